@@ -1,0 +1,269 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+Each check ties one oracle layer to the paper or to mathematics: the printed
+merging table (Tbl. S1), the structural properties of words (Methods,
+properties 1-3 and the 1/2^m rule), dense Kronecker products, second
+quantisation, Hermiticity, closed-form ground energies and library eigen
+solvers.  All run on the CPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import brute, fermion
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _sorted_keys(words):
+    return oracle.sort_unique(words)
+
+
+# ------------------------------------------------------- Tbl. S1 (paper) --
+def test_merge_rules_match_table_s1():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "merge_rules_tbl_s1.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 16
+    for a, b, res in rows:
+        assert wl.merge_pair(a, b) == res, (a, b, res)
+
+
+# ------------------------------------------- Methods, properties 1-3, 1/2^m --
+@pytest.mark.parametrize("seed", range(6))
+def test_pauli_word_properties(seed):
+    rng = np.random.default_rng(seed)
+    n = 7
+    F_of = {}
+    for _ in range(8):
+        qs = rng.choice(n, size=int(rng.integers(1, n + 1)), replace=False)
+        word = [(int(q), int(rng.choice([wl.Z, wl.X, wl.Y]))) for q in qs]
+        M = brute.word_matrix(n, word)
+        nz = np.abs(M) > 0
+        # property 1: exactly one nonzero per row (and per column)
+        assert np.all(nz.sum(axis=1) == 1) and np.all(nz.sum(axis=0) == 1)
+        # property 2: column = row XOR (bits under X / Y)
+        f = sum(1 << q for q, c in word if c in (wl.X, wl.Y))
+        rows, cols = np.nonzero(nz)
+        assert np.all(cols == (rows ^ f))
+        F_of.setdefault(f, []).append(nz)
+    # property 3: words with the same off-diagonal structure share positions
+    for f, mats in F_of.items():
+        for m in mats[1:]:
+            assert np.array_equal(m, mats[0])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_projector_ladder_fraction(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 8
+    qs = rng.choice(n, size=int(rng.integers(1, n + 1)), replace=False)
+    word = [(int(q), int(rng.integers(0, 7))) for q in qs]
+    m = sum(1 for _, c in word if c in (wl.P0, wl.P1, wl.LOWER, wl.RAISE))
+    M = brute.word_matrix(n, word)
+    nonzero_rows = int(np.count_nonzero(np.abs(M).sum(axis=1)))
+    assert nonzero_rows * (1 << m) == (1 << n)
+
+
+# ----------------------------------------------- oracle vs dense Kronecker --
+@pytest.mark.parametrize("n,T,D,k,seed", [(5, 12, 20, 1, 0), (8, 30, 150, 3, 1),
+                                          (10, 40, 400, 2, 2), (6, 25, 64, 1, 3)])
+def test_oracle_apply_matches_kronecker(n, T, D, k, seed):
+    op = wl.random_extended(n, T, max_weight=n, seed=seed, hermitian=False, real=False)
+    keys = _sorted_keys(wl.random_subspace(n, D, seed + 10, duplicates=5))
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(keys.shape[0], k)) + 1j * rng.normal(size=(keys.shape[0], k))
+    H = brute.restricted(op, keys)
+    assert _rel(oracle.apply(op, keys, x), H @ x) < 1e-13
+    assert _rel(oracle.diagonal(op, keys), np.diag(H)) < 1e-13 or np.allclose(np.diag(H), 0)
+    assert np.allclose(oracle.dense(op, keys), H, atol=1e-13)
+
+
+def test_oracle_identity_term_and_empty_subspace():
+    op = wl.QubitOperator.from_terms(3, [(2.5, []), (1.0, [(0, "X")])])
+    keys = _sorted_keys(wl.full_space(3))
+    x = np.arange(8, dtype=float)
+    H = brute.restricted(op, keys)
+    assert _rel(oracle.apply(op, keys, x), H @ x) < 1e-15
+    empty = np.zeros((0, 1), np.uint64)
+    assert oracle.apply(op, empty, np.zeros(0)).shape == (0,)
+
+
+def test_term_and_target_tables_match_kronecker():
+    n = 8
+    op = wl.random_extended(n, 20, max_weight=5, seed=7, hermitian=True, real=True)
+    keys = _sorted_keys(wl.random_subspace(n, 120, 8))
+    D = keys.shape[0]
+    rows = keys[:, 0].astype(np.int64)
+    pos = {int(r): i for i, r in enumerate(rows)}
+    tt = oracle.term_table(op, keys)
+    words = list(op.terms())
+    factor = {1: 1, 2: 1j, 3: -1, 4: -1j}
+    mats = [brute.word_matrix(n, w) for _, w in words]
+    for t, M in enumerate(mats):
+        for a, r in enumerate(rows):
+            nzc = np.nonzero(M[r])[0]
+            if tt[a, t] == 0:
+                assert nzc.size == 0
+            else:
+                assert nzc.size == 1 and M[r, nzc[0]] == factor[int(tt[a, t])]
+    # groups: distinct nonzero column offsets (row XOR column) of the words
+    G = oracle.groups(op)
+    fsets = {}
+    for t, M in enumerate(mats):
+        r_, c_ = np.nonzero(M)
+        offs = set((r_ ^ c_).tolist())
+        assert len(offs) <= 1
+        if offs and offs != {0}:
+            fsets.setdefault(offs.pop(), []).append(t)
+    expected = sorted(fsets, key=lambda f: (bin(f).count("1"), f))
+    assert G[:, 0].tolist() == expected
+    tg = oracle.target_table(op, keys)
+    for g, f in enumerate(expected):
+        for a, r in enumerate(rows):
+            hit = [t for t in fsets[f] if np.any(mats[t][r])]
+            want = -2 if not hit else pos.get(int(r) ^ f, -1)
+            assert tg[a, g] == want
+
+
+# ------------------------------------------------------------ Hermiticity --
+def test_hermitian_csr_invariant():
+    n = 9
+    op = wl.random_extended(n, 40, max_weight=6, seed=11, hermitian=True, real=False)
+    keys = _sorted_keys(wl.random_subspace(n, 300, 12))
+    indptr, indices, data = oracle.csr(op, keys)
+    D = keys.shape[0]
+    entries = {}
+    for a in range(D):
+        cols = indices[indptr[a]:indptr[a + 1]]
+        assert np.all(np.diff(cols) > 0) and a in cols
+        for c, v in zip(cols, data[indptr[a]:indptr[a + 1]]):
+            entries[(a, int(c))] = v
+    for (a, c), v in entries.items():
+        assert (c, a) in entries
+        assert abs(entries[(c, a)] - np.conj(v)) <= 1e-15 * max(1.0, abs(v))
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=D) + 1j * rng.normal(size=D)
+    y = rng.normal(size=D) + 1j * rng.normal(size=D)
+    lhs = np.vdot(x, oracle.apply(op, keys, y))
+    rhs = np.vdot(oracle.apply(op, keys, x), y)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------- closed forms / solvers --
+def tfim_closed_form(N, g):
+    """Ground energy of the periodic chain H = -sum ZZ - g sum X, N even:
+    -sum_n sqrt(1 + g^2 - 2 g cos(pi (2n+1)/N)) (free-fermion solution)."""
+    return -sum(math.sqrt(1 + g * g - 2 * g * math.cos(math.pi * (2 * m + 1) / N)) for m in range(N))
+
+
+@pytest.mark.parametrize("g", [1.0, 0.5, 2.0])
+def test_tfim_closed_form(g):
+    op = wl.tfim_chain(12, g=g)
+    keys = _sorted_keys(wl.full_space(12))
+    e_ref = tfim_closed_form(12, g)
+    if g == 1.0:
+        assert abs(e_ref + 2.0 / math.sin(math.pi / 24)) < 1e-12
+    assert abs(oracle.ground_energy(op, keys) - e_ref) <= 1e-10 * abs(e_ref)
+    e, steps = oracle.lanczos(op, keys, m_max=200, tol=1e-14, seed=1)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+
+
+def test_dense_full_space_small():
+    op = wl.xxz_square(3, 3, 0.5, 1.0)
+    keys = _sorted_keys(wl.full_space(9))
+    e_full = np.linalg.eigvalsh(brute.full_matrix(op).real)[0]
+    assert abs(oracle.ground_energy(op, keys) - e_full) < 1e-11
+    e, _ = oracle.lanczos(op, keys, m_max=300, tol=1e-14, seed=2)
+    assert abs(e - e_full) < 1e-10 * abs(e_full)
+
+
+def test_lanczos_on_subspace_matches_eigh():
+    op = wl.xxz_square(4, 4, 0.5, 1.0)
+    keys = _sorted_keys(wl.xxz_walk_subspace(4, 4, count=1500, max_len=8, seed=5))
+    H = brute.restricted(op, keys) if op.n_qubits <= 12 else oracle.dense(op, keys)
+    e_ref = np.linalg.eigvalsh(H.real)[0]
+    e, _ = oracle.lanczos(op, keys, m_max=300, tol=1e-14, seed=3)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+
+
+def test_tridiag_min_matches_eigvalsh():
+    rng = np.random.default_rng(4)
+    for m in (1, 2, 7, 60):
+        a, b = rng.normal(size=m), rng.normal(size=m)
+        T = np.diag(a) + np.diag(b[1:], 1) + np.diag(b[1:], -1)
+        assert abs(oracle.tridiag_min(a, b) - np.linalg.eigvalsh(T)[0]) < 1e-13
+
+
+# ------------------------------------------------------ fermionic layer --
+def _random_fermionic(n_modes, n_terms, seed):
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(n_terms):
+        L = int(rng.integers(1, 5))
+        ops = [(int(rng.integers(0, n_modes)), bool(rng.integers(0, 2))) for _ in range(L)]
+        terms.append((complex(rng.normal(), rng.normal()), ops))
+    return wl.FermionicOperator(n_modes, terms)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_jordan_wigner_matches_second_quantisation(seed):
+    fop = _random_fermionic(6, 25, seed)
+    qop = wl.jordan_wigner(fop)
+    assert set(np.unique(qop.op_code).tolist()) <= {wl.Z, wl.P0, wl.P1, wl.LOWER, wl.RAISE}
+    np.testing.assert_allclose(brute.full_matrix(qop), fermion.dense(fop), atol=1e-13)
+
+
+def test_hubbard_dimer_closed_form():
+    t, U = 1.0, 3.0
+    h = np.array([[0.0, -t], [-t, 0.0]])
+    eri = np.zeros((2, 2, 2, 2))
+    eri[0, 0, 0, 0] = eri[1, 1, 1, 1] = U
+    op = wl.jordan_wigner(wl.molecular_fermionic(h, eri))
+    keys = _sorted_keys(wl.product_subspace([1, 2], [1, 2], 2))
+    e = oracle.ground_energy(op, keys)
+    assert abs(e - (U - math.sqrt(U * U + 16 * t * t)) / 2) < 1e-12
+
+
+def test_one_body_slater_closed_form():
+    rng = np.random.default_rng(9)
+    n_orb, na, nb = 4, 2, 1
+    A = rng.normal(size=(n_orb, n_orb))
+    h = (A + A.T) / 2
+    op = wl.jordan_wigner(wl.molecular_fermionic(h, np.zeros((n_orb,) * 4)))
+    alpha = [v for v in range(1 << n_orb) if bin(v).count("1") == na]
+    beta = [v for v in range(1 << n_orb) if bin(v).count("1") == nb]
+    keys = _sorted_keys(wl.product_subspace(alpha, beta, n_orb))
+    eps = np.linalg.eigvalsh(h)
+    assert abs(oracle.ground_energy(op, keys) - (eps[:na].sum() + eps[:nb].sum())) < 1e-12
+
+
+# ------------------------------------------------------- bit-string layer --
+@pytest.mark.parametrize("n", [36, 64, 130, 200])
+def test_sort_unique_and_find(n):
+    words = wl.random_subspace(n, 500, n, duplicates=100)
+    keys = oracle.sort_unique(words)
+    ints = sorted(set(wl.words_to_ints(words)))
+    assert wl.words_to_ints(keys) == ints
+    probe = np.concatenate([words[:50], wl.random_subspace(n, 50, n + 1)])
+    got = oracle.find(keys, probe)
+    pos = {v: i for i, v in enumerate(ints)}
+    assert got.tolist() == [pos.get(v, -1) for v in wl.words_to_ints(probe)]
+
+
+def test_operator_errors():
+    keys = _sorted_keys(wl.full_space(3))
+    bad_repeat = wl.QubitOperator.from_terms(3, [(1.0, [(0, "X"), (0, "Z")])])
+    bad_range = wl.QubitOperator.from_terms(3, [(1.0, [(3, "X")])])
+    with pytest.raises(oracle.OracleError):
+        oracle.apply(bad_repeat, keys, np.zeros(8))
+    with pytest.raises(oracle.OracleError):
+        oracle.apply(bad_range, keys, np.zeros(8))
