@@ -1,0 +1,372 @@
+"""Benchmark of the subspace Hamiltonian-vector product on one GB300 (or N
+replicas under torchrun).
+
+Workload (default): the 2D XXZ model on the 6x6 periodic square lattice
+(36 qubits), H = sum_<ij> 0.5 (s+_i s-_j + s-_i s+_j) + Z_i Z_j, over 300,000
+distinct weight-18 bit-strings from seeded bond-swap walks (length 1-12) from
+the Neel state.  One step = one FP64 product y = H_S x over the whole
+subspace (k = 1).  Throughput is Gelem/s = D * (groups + 1) * k / t (the
+paper's count of matrix-element evaluations: subspace dimension times the
+number of groups, diagonal group included).
+
+Extra objects on the same JSON line: the FP32-mixed and block (k = 16)
+variants timed the same way, a full ground-state solve, the roofline of the
+product kernel, the CPU oracle baseline, clocks sampled during the timed
+region, and the end-to-end number through the host-buffer ABI call.
+
+  python bench.py [--steps K] [--warmup W] [--workload xxz|tfim|ising]
+  python bench.py --impl reference      # the CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+if "OMP_NUM_THREADS" not in os.environ:
+    os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "apply_H Gelem/s FP64 vs FP32-mixed block; served eigensolves/s, p50/p99 latency"
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str):
+    if name == "xxz":
+        op = wl.xxz_square(6, 6, 0.5, 1.0)
+        words = wl.xxz_walk_subspace(6, 6, count=300_000, max_len=12, seed=2)
+        desc = ("2D XXZ 6x6 periodic (36 qubits), 300k distinct weight-18 strings from bond-swap walks "
+                "(len 1-12) from Neel, seed 2")
+    elif name == "tfim":
+        op = wl.tfim_chain(12, g=1.0)
+        words = wl.full_space(12)
+        desc = "1D TFIM 12 qubits periodic, full 4096-string space"
+    elif name == "ising":
+        op = wl.ising_heavy_hex(200, seed=4)
+        words = wl.flip_subspace(200, 1_000_000, max_flips=20, seed=4)
+        desc = "Ising 200 qubits heavy-hex-like graph, 1M strings = seeded reference with 1-20 bits flipped"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return op, words, desc
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_profile_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes of the product kernel from the committed ncu
+    summary (profiles/<tag>.md, line 'traffic_bytes_per_launch: N'), or None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            v = line.split(":", 1)[1].strip()
+            return None if v in ("", "null", "None") else float(v)
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import paper_2603_18731_gb300 as q
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    op, words, desc = make_workload(args.workload)
+    ctx = q.create(local)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(op.n_qubits, words)
+    info = h.info()
+    D, G, W = sub.dim, info["n_groups"], sub.W
+    dev = ctx.device
+    s = ctx.stream
+    rng = np.random.default_rng(0)
+    with torch.cuda.stream(s):
+        x64 = torch.as_tensor(rng.normal(size=D), device=dev)
+        x32 = x64.float()
+        xb64 = torch.as_tensor(rng.normal(size=(D, 16)), device=dev)
+        xb32 = xb64.float()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # lookups / hits per product (integer target table, not timed)
+    lookups = hits = 0
+    chunk = max(1, (1 << 27) // max(G, 1))
+    for r0 in range(0, D, chunk):
+        n = min(chunk, D - r0)
+        tt = ctx.target_table(h, sub, r0, n)
+        ctx.synchronize()
+        lookups += int((tt != -2).sum().item())
+        hits += int((tt >= 0).sum().item())
+        del tt
+    ctx.synchronize()
+
+    def time_variant(x, precision, steps, warmup):
+        y = ctx.empty(tuple(x.shape), x.dtype)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for _ in range(warmup):
+            ctx.apply_H(h, sub, x, y, precision)
+        ctx.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            with torch.cuda.stream(s):
+                flush.zero_()
+            ev[i][0].record(s)
+            ctx.apply_H(h, sub, x, y, precision)
+            ev[i][1].record(s)
+        ctx.synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return float(np.mean(ms)), ms, wall
+
+    k1 = 1
+    elems = D * (G + 1)
+    # headline: FP64, k = 1
+    with ClockSampler(local) as clk:
+        ms64, all64, wall64 = time_variant(x64, q.QSD_FP64, args.steps, args.warmup)
+    t_max = ms64
+    if dist:
+        t = torch.tensor([ms64], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * elems * k1 / (t_max * 1e-3) / 1e9
+    variants = {}
+    vsteps = max(3, min(args.steps, 20))
+    for name, x, prec, k in (("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp64_k16", xb64, q.QSD_FP64, 16),
+                             ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16)):
+        m, _, _ = time_variant(x, prec, vsteps, 3)
+        variants[name] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
+    variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / value * world if value else None
+
+    # roofline of the product kernel (FP64, k = 1): algorithmic bytes
+    s_x = 8
+    b_alg = D * (W * 8 + 8 + s_x + s_x) + lookups * 8 + hits * (W * 8 + s_x)
+    b_alg += info["n_terms"] * (3 * W * 8 + 8 + 1) + G * (W * 8 + 8 + 4 + 1 + 8 + 68)
+    peak, peak_kind = load_peaks()
+    achieved = b_alg / (ms64 * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} hbm_gbs (burst, kernel timed alone)",
+            "traffic": read_profile_traffic(f"apply_H_{args.workload}"),
+            "algorithmic_bytes_per_launch": b_alg, "lookups_per_launch": lookups, "hits_per_launch": hits}
+
+    # end to end through the host-buffer ABI call (pinned host memory)
+    xh = torch.empty(D, dtype=torch.float64, pin_memory=True).numpy()
+    xh[:] = x64.cpu().numpy()
+    yh = torch.empty(D, dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(args.warmup):
+        ctx.apply_H_host(h, sub, xh, q.QSD_FP64, out=yh)
+    et = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.apply_H_host(h, sub, xh, q.QSD_FP64, out=yh)
+        et.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(et))
+    e2e = {"value": world * elems / e2e_s / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": D * 8,
+           "d2h_bytes_per_step": D * 8, "ms_per_step": e2e_s * 1e3}
+
+    # one full ground-state solve per precision (not part of the timed steps)
+    solve = {}
+    if not args.no_solve:
+        for name, prec in (("fp64", q.QSD_FP64), ("fp32_mixed", q.QSD_FP32_MIXED)):
+            ctx.synchronize()
+            t0 = time.perf_counter()
+            e, inf = ctx.lanczos_ground_state(h, sub, check=False, precision=prec, max_steps=args.solve_steps,
+                                              tol=1e-9)
+            ctx.synchronize()
+            solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "steps": inf["steps"],
+                           "applies": inf["applies"], "residual": inf["residual"], "status": inf["status"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(op, words, G, target_seconds=args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "dim": D, "groups": G, "qubits": op.n_qubits,
+                       "k": 1, "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "variants": variants, "solve": solve,
+            "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU arm
+def cpu_baseline(op, words, G, target_seconds=12.0, sample_rows=None):
+    """The plain oracle product on a bounded sample of rows, timed on the host
+    cores; returns Gelem/s on the same count (rows * (groups + 1))."""
+    import oracle
+    keys = oracle.sort_unique(words)
+    D = keys.shape[0]
+    x = np.random.default_rng(0).normal(size=D)
+    rng = np.random.default_rng(1)
+    n = min(D, 512)
+    rows = np.sort(rng.choice(D, size=n, replace=False))
+    t0 = time.perf_counter()
+    oracle.apply_rows(op, keys, x, rows)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    if sample_rows is None:
+        sample_rows = int(min(D, max(n, n * target_seconds / dt)))
+    rows = np.sort(rng.choice(D, size=sample_rows, replace=False))
+    t0 = time.perf_counter()
+    oracle.apply_rows(op, keys, x, rows)
+    dt = time.perf_counter() - t0
+    return {"value": sample_rows * (G + 1) / dt / 1e9, "unit": "Gelem/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{sample_rows} of {D} rows (uniform sample), FP64 product, OpenMP over rows"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    op, words, desc = make_workload(args.workload)
+    keys = oracle.sort_unique(words)
+    # group count by the oracle's own definition (distinct flip sets)
+    G = oracle.groups(op).shape[0]
+    D = keys.shape[0]
+    x = np.random.default_rng(0).normal(size=D)
+    rng = np.random.default_rng(2)
+    probe = np.sort(rng.choice(D, size=min(D, 512), replace=False))
+    t0 = time.perf_counter()
+    oracle.apply_rows(op, keys, x, probe)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    per_step = args.ref_step_seconds
+    n = int(min(D, max(64, len(probe) * per_step / dt)))
+    rows = np.sort(rng.choice(D, size=n, replace=False))
+    for _ in range(args.warmup):
+        oracle.apply_rows(op, keys, x, rows)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.apply_rows(op, keys, x, rows)
+        ts.append(time.perf_counter() - t0)
+    ms = float(np.mean(ts)) * 1e3
+    value = n * (G + 1) / (ms * 1e-3) / 1e9
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    sample = f"{n} of {D} rows per step (uniform sample), FP64 product, OpenMP over rows"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "dim": D, "groups": G, "k": 1,
+                   "precision": "fp64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="xxz", choices=["xxz", "tfim", "ising"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solve-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=2.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

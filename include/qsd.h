@@ -1,0 +1,230 @@
+/*
+ * qsd.h -- C ABI of the GB300 subspace Hamiltonian library.
+ *
+ * The library evaluates the matrix-free product y = H_S x of a Hamiltonian
+ * written in the extended alphabet [Z, 0, 1, X, Y, -, +] over a subspace S
+ * of sampled bit-strings, and finds the ground state of H_S with a Lanczos
+ * solver on the device (arXiv 2603.18731, "A generalized framework for
+ * quantum subspace diagonalization": Methods "Qubit Hamiltonians",
+ * "Subspace data structure" and "Matrix evaluation").
+ *
+ * Conventions that hold for every call:
+ *  - Bit-strings over n qubits are W = ceil(n/64) little-endian uint64 words;
+ *    qubit q is bit q%64 of word q/64.  Arrays of bit-strings are row-major
+ *    [count][W].  There is no upper limit on n other than memory.
+ *  - Letters are coded [Z, 0, 1, X, Y, -, +] -> 0..6 as in the paper
+ *    (Methods, "Qubit Hamiltonians"): 0 = |0><0|, 1 = |1><1|,
+ *    + = |1><0| (raising), - = |0><1| (lowering).
+ *  - Subspace index of a bit-string = its rank in ascending integer order
+ *    (word W-1 most significant) after duplicates are dropped (Methods,
+ *    "Lower / upper triangle evaluation" sorts the subspace by integer value).
+ *  - Every call returns a status code (QSD_OK = 0).  On error the context's
+ *    message is set (qsd_last_error) and no output is written unless stated.
+ *  - Input arrays are read during the call and stay owned by the caller.
+ *    Handles are owned by the library until freed.
+ *  - Device pointers must be device memory of the context's device.  Device
+ *    work is enqueued on the context's stream; calls that return a host
+ *    value (dimensions, energies) synchronise that stream.
+ *  - A handle must not be used from two threads at once; distinct contexts
+ *    may be used concurrently.
+ */
+#ifndef QSD_H
+#define QSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------- status codes */
+#define QSD_OK                      0
+#define QSD_ERR_INVALID_ARG         1  /* bad pointer, size, enum or handle */
+#define QSD_ERR_QUBIT_RANGE         2  /* qubit index < 0 or >= n, or letter code > 6 */
+#define QSD_ERR_REPEATED_INDEX      3  /* a qubit appears twice in one word */
+#define QSD_ERR_NOT_HERMITIAN       4  /* operator is not Hermitian (eigensolvers only) */
+#define QSD_ERR_COMPLEX_UNSUPPORTED 5  /* operator has complex matrix elements */
+#define QSD_ERR_OOM                 6  /* device or host allocation failed */
+#define QSD_ERR_NOT_CONVERGED       7  /* eigensolver hit max_steps; best estimate returned */
+#define QSD_ERR_TIMEOUT             8  /* a bounded device or host wait ran out */
+#define QSD_ERR_CUDA                9  /* a CUDA runtime call failed */
+#define QSD_ERR_CAPACITY           10  /* subspace larger than 2^32 - 2 rows */
+#define QSD_ERR_CANCELLED          11  /* request cancelled before completion */
+#define QSD_PENDING                12  /* server request still running */
+#define QSD_ERR_INTERNAL           13  /* a device-side consistency check failed */
+
+/* ------------------------------------------------------------- precision */
+#define QSD_FP64        0  /* x, y stored as double; FP64 accumulation */
+#define QSD_FP32_MIXED  1  /* x, y stored as float; each row accumulated in FP64 */
+
+typedef struct qsd_ctx_s *qsd_ctx;
+typedef struct qsd_op_s *qsd_op;
+typedef struct qsd_sub_s *qsd_sub;
+
+/* ------------------------------------------------------------- contexts */
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to enqueue on (e.g. a PyTorch stream), or NULL for a stream owned by the
+ * context.  *out receives the handle. */
+int qsd_create(int device, void *cuda_stream, qsd_ctx *out);
+
+/* Destroy a context.  Operators and subspaces made on it must be freed first. */
+int qsd_destroy(qsd_ctx ctx);
+
+/* Message of the last failed call on `ctx` (or of the calling thread's last
+ * failed qsd_create when ctx is NULL).  Valid until the next call. */
+const char *qsd_last_error(qsd_ctx ctx);
+
+/* --------------------------------------------------------------- operators */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_words;          /* W */
+    int64_t n_terms_in;       /* terms passed to qsd_load_operator */
+    int64_t n_terms;          /* off-diagonal terms after combining equal words */
+    int64_t n_diag_terms;     /* diagonal terms (no flipped qubit) after combining */
+    int64_t n_groups;         /* off-diagonal groups (distinct flip sets) */
+    int64_t n_ladder_groups;  /* groups that use the ladder-integer table */
+    int64_t max_group_terms;
+    int32_t is_real;          /* every matrix element is real */
+    int32_t is_hermitian;     /* term set closed under adjoint (rel. 1e-14) */
+    double identity_coef;     /* real part of the constant (empty-word) term */
+} qsd_op_info;
+
+/* Load H = sum_t c_t W_t (Methods, "Qubit Hamiltonians": a term is a
+ * coefficient, the sorted qubit indices of its non-identity factors and
+ * their letters).  Term t owns factors term_ptr[t] .. term_ptr[t+1]-1 of
+ * op_qubit (int32) and op_code (uint8, 0..6).  coef_im may be NULL (real
+ * coefficients).  An empty word is the identity and adds its coefficient to
+ * the diagonal.  Terms with a zero coefficient are dropped.  All arrays are
+ * host memory.
+ *
+ * The call converts every word to masks over the row bits (flip F, test P
+ * and V, sign Z), combines equal words, and groups the off-diagonal terms on
+ * the device by their off-diagonal structure F ordered by (popcount F, F)
+ * (Methods, "Qubit Hamiltonians", properties 1-3 and Fig. 3a); inside a group
+ * terms are ordered by their ladder integer, and groups whose flipped qubits
+ * all carry ladder letters get the int_ptrs table of the ladder integer
+ * (Methods, "Fermionic Hamiltonians", Fig. 3b).
+ * Errors: QSD_ERR_QUBIT_RANGE, QSD_ERR_REPEATED_INDEX, QSD_ERR_INVALID_ARG. */
+int qsd_load_operator(qsd_ctx ctx, int32_t n_qubits, int64_t n_terms,
+                      const int64_t *term_ptr, const int32_t *op_qubit,
+                      const uint8_t *op_code, const double *coef_re,
+                      const double *coef_im, qsd_op *out);
+
+int qsd_op_get_info(qsd_op op, qsd_op_info *info);
+
+/* Group flip sets in the library's group order, row-major [n_groups][W]
+ * (host output). */
+int qsd_op_groups(qsd_op op, uint64_t *groups_out);
+
+int qsd_free_op(qsd_op op);
+
+/* --------------------------------------------------------------- subspaces */
+/* Build the subspace from n_in bit-strings (row-major [n_in][W], host memory
+ * when words_on_device == 0, else device memory), any order, duplicates
+ * allowed (Methods, "Subspace data structure").  The strings are sorted by
+ * integer value on the device, duplicates dropped, and an open-addressing
+ * hash table (load factor <= 1/2, 4-slot buckets of (32-bit tag, 32-bit
+ * index)) is built for lookups.  *dim_out receives D.  Synchronises.
+ * Errors: QSD_ERR_CAPACITY when D would exceed 2^32 - 2. */
+int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,
+                       const uint64_t *words, int words_on_device,
+                       qsd_sub *out, int64_t *dim_out);
+
+/* Dimension, qubit count and hash capacity (slots) of a subspace. */
+int qsd_subspace_info(qsd_sub sub, int64_t *dim, int32_t *n_qubits, int64_t *capacity);
+
+/* Copy the sorted bit-strings, row-major [D][W], to `out` (device memory when
+ * out_on_device != 0, else host memory; host copies synchronise). */
+int qsd_subspace_keys(qsd_ctx ctx, qsd_sub sub, uint64_t *out, int out_on_device);
+
+/* Index of each of n query strings (device, row-major [n][W]) in the
+ * subspace, or -1 when absent; idx_out is device int64 [n]. */
+int qsd_subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n,
+                       const uint64_t *keys, int64_t *idx_out);
+
+int qsd_free_sub(qsd_sub sub);
+
+/* --------------------------------------------------------------- products */
+/* y = H_S x for k right-hand sides (Methods, "Matrix evaluation": the
+ * matrix-free product recomputes each element per call, in parallel over
+ * row bit-strings; each row gathers from the columns its groups reach).
+ * x and y are device arrays [D][k] row-major, of double (QSD_FP64) or float
+ * (QSD_FP32_MIXED, where each row is accumulated in FP64 and rounded once).
+ * x and y must not overlap.  Per row the diagonal is applied first, then the
+ * groups in group order, and the terms of a group in term order, so results
+ * are deterministic.  Asynchronous on the context stream.  The first product
+ * of an (operator, subspace) pair computes and caches the diagonal of H_S
+ * (Methods, "Matrix evaluation": the diagonal is computed once and cached).
+ * Errors: QSD_ERR_COMPLEX_UNSUPPORTED when the operator has complex matrix
+ * elements; QSD_ERR_INVALID_ARG on qubit-count mismatch or k < 1. */
+int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k,
+                const void *x, void *y);
+
+/* As qsd_apply_H with x and y in HOST memory: copies x to the device, applies,
+ * copies y back and synchronises.  Pinned host buffers copy fastest. */
+int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision,
+                     int32_t k, const void *x_host, void *y_host);
+
+/* Diagonal of H_S into device double [D] (real part). */
+int qsd_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d_out);
+
+/* Target table of rows row0 .. row0+nrows-1: out is device int64
+ * [nrows][n_groups] in group order; entry = -2 when no term of the group is
+ * nonzero at the row (the group is skipped with no lookup, Methods "Matrix
+ * evaluation"), -1 when the column is not in the subspace, else the column
+ * index. */
+int qsd_target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
+                     int64_t nrows, int64_t *out);
+
+/* Term table of rows row0 .. row0+nrows-1 for the terms as passed to
+ * qsd_load_operator: out is device int8 [nrows][n_terms_in]; entry 0 when
+ * <r|W_t|r xor F_t> is zero, else 1 + p where the element is i^p. */
+int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
+                   int64_t nrows, int8_t *out);
+
+/* ------------------------------------------------------------- eigensolver */
+typedef struct {
+    int32_t precision;     /* QSD_FP64, or QSD_FP32_MIXED: FP32 Krylov basis and
+                              products, FP64 dots and tridiagonal, then FP64
+                              refinement of the Ritz value */
+    int32_t max_steps;     /* Krylov dimension limit (>= 1) */
+    double tol;            /* stop when |H u - theta u| / |theta| <= tol */
+    double refine_tol;     /* mixed only: stop refining when the relative change
+                              of the FP64 Rayleigh quotient is <= refine_tol */
+    int32_t check_every;   /* solve the tridiagonal problem every this many steps */
+    int32_t refine_steps;  /* mixed only: Krylov steps per FP64 refinement restart */
+    int32_t max_refine;    /* mixed only: refinement restarts limit */
+    int32_t use_graphs;    /* capture each block of check_every steps in a CUDA graph */
+    uint64_t seed;         /* start vector entries U(-1,1) from SplitMix64(seed ^ i) */
+    const double *v0;      /* optional device start vector [D] (overrides seed) */
+    double time_limit_s;   /* 0 = none; else QSD_ERR_TIMEOUT after this wall time */
+} qsd_lanczos_params;
+
+typedef struct {
+    int32_t steps;         /* Krylov steps taken (all phases) */
+    int32_t refine_restarts;
+    double residual;       /* |H u - theta u| / |theta| of the returned vector (FP64) */
+    double energy_unrefined; /* Ritz value before FP64 refinement */
+    int32_t status;        /* copy of the return code */
+    int32_t applies;       /* number of H_S products */
+} qsd_lanczos_info;
+
+/* Fill *p with defaults: FP64, max_steps 300, tol 1e-9, refine_tol 1e-10,
+ * check_every 10, refine_steps 30, max_refine 5, graphs on, seed 1. */
+void qsd_lanczos_default_params(qsd_lanczos_params *p);
+
+/* Lowest eigenvalue of the real symmetric H_S with a Lanczos solver on the
+ * device, fully reorthogonalised (classical Gram-Schmidt twice per step).
+ * *energy receives the Ritz value (FP64).  vec_out (optional, device double
+ * [D]) receives the normalised Ritz vector.  info is optional.
+ * Errors: QSD_ERR_NOT_HERMITIAN, QSD_ERR_COMPLEX_UNSUPPORTED,
+ * QSD_ERR_NOT_CONVERGED (best estimate still written), QSD_ERR_TIMEOUT. */
+int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub,
+                             const qsd_lanczos_params *p, double *energy,
+                             double *vec_out, qsd_lanczos_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSD_H */

@@ -59,6 +59,7 @@ def lib():
             L.orc_find.argtypes = [i32, i64, p, p]
             L.orc_check_operator.argtypes = [i32, i64, p, p, p]
             L.orc_apply.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, i32, p, p, p, p]
+            L.orc_apply_rows.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, i32, p, i64, p, p, p]
             L.orc_diagonal.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, p, p]
             L.orc_term_table.argtypes = [i32, i32, i64, p, p, p, i64, p, i64, i64, p]
             L.orc_groups.restype = i64
@@ -139,6 +140,23 @@ def apply(op, keys: np.ndarray, x: np.ndarray) -> np.ndarray:
     _check(lib().orc_apply(op.n_qubits, W, op.n_terms, _ptr(tp), _ptr(oq), _ptr(oc), _ptr(cr), _ptr(ci),
                            D, _ptr(keys), k, _ptr(xr), _ptr(xi), _ptr(yr), _ptr(yi)))
     return (yr + 1j * yi).reshape(shape)
+
+
+def apply_rows(op, keys: np.ndarray, x: np.ndarray, rows) -> np.ndarray:
+    """(H_S x)[rows] for a real ``x`` ([D] or [D, k]); complex result."""
+    keys = np.ascontiguousarray(keys, np.uint64)
+    D, W = keys.shape
+    x = np.asarray(x, np.float64)
+    x2 = np.ascontiguousarray(x.reshape(D, 1) if x.ndim == 1 else x)
+    k = x2.shape[1]
+    rows = np.ascontiguousarray(rows, np.int64)
+    yr = np.zeros((rows.shape[0], k))
+    yi = np.zeros((rows.shape[0], k))
+    tp, oq, oc, cr, ci = _op_arrays(op)
+    _check(lib().orc_apply_rows(op.n_qubits, W, op.n_terms, _ptr(tp), _ptr(oq), _ptr(oc), _ptr(cr), _ptr(ci),
+                                D, _ptr(keys), k, _ptr(x2), rows.shape[0], _ptr(rows), _ptr(yr), _ptr(yi)))
+    y = yr + 1j * yi
+    return y[:, 0] if x.ndim == 1 else y
 
 
 def diagonal(op, keys: np.ndarray) -> np.ndarray:

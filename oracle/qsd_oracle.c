@@ -200,6 +200,51 @@ int orc_apply(int n, int W, int64_t T, const int64_t *term_ptr,
     return ORC_OK;
 }
 
+/* y[i] = (H_S x)[rows[i]] for a list of rows only (sampled checks at sizes
+ * where the full product is too slow); y is [n_rows][k]. */
+int orc_apply_rows(int n, int W, int64_t T, const int64_t *term_ptr,
+                   const int32_t *op_qubit, const uint8_t *op_code,
+                   const double *coef_re, const double *coef_im,
+                   int64_t D, const uint64_t *keys, int k, const double *x_re,
+                   int64_t n_rows, const int64_t *rows, double *y_re, double *y_im)
+{
+    int rc = orc_check_operator(n, T, term_ptr, op_qubit, op_code);
+    if (rc) return rc;
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (rows[i] < 0 || rows[i] >= D) return ORC_ERR_ARG;
+    #pragma omp parallel
+    {
+        uint64_t *col = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+        double *acc = (double *)malloc(sizeof(double) * 2 * (size_t)(k > 0 ? k : 1));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n_rows; ++i) {
+            const uint64_t *row = keys + rows[i] * W;
+            for (int j = 0; j < 2 * k; ++j) acc[j] = 0.0;
+            for (int64_t t = 0; t < T; ++t) {
+                int p;
+                if (!word_element(op_qubit + term_ptr[t], op_code + term_ptr[t],
+                                  term_ptr[t + 1] - term_ptr[t], row, col, W, &p))
+                    continue;
+                int64_t b = orc_find(W, D, keys, col);
+                if (b < 0) continue;
+                double hre, him;
+                mul_ipow(coef_re[t], coef_im ? coef_im[t] : 0.0, p, &hre, &him);
+                for (int j = 0; j < k; ++j) {
+                    acc[2 * j] += hre * x_re[b * k + j];
+                    acc[2 * j + 1] += him * x_re[b * k + j];
+                }
+            }
+            for (int j = 0; j < k; ++j) {
+                y_re[i * k + j] = acc[2 * j];
+                if (y_im) y_im[i * k + j] = acc[2 * j + 1];
+            }
+        }
+        free(col);
+        free(acc);
+    }
+    return ORC_OK;
+}
+
 /* Diagonal of H_S: the sum over terms whose candidate column is the row. */
 int orc_diagonal(int n, int W, int64_t T, const int64_t *term_ptr,
                  const int32_t *op_qubit, const uint8_t *op_code,

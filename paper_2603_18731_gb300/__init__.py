@@ -1,0 +1,301 @@
+"""Python binding of the GB300 subspace Hamiltonian library (``libqsd.so``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI declared in ``include/qsd.h``; the names here are the
+ABI's names without the ``qsd_`` prefix.  PyTorch supplies device memory and
+streams.  There is no CPU fallback: when the library is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsd.so")
+
+QSD_OK = 0
+QSD_FP64 = 0
+QSD_FP32_MIXED = 1
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "QUBIT_RANGE", 3: "REPEATED_INDEX", 4: "NOT_HERMITIAN",
+    5: "COMPLEX_UNSUPPORTED", 6: "OOM", 7: "NOT_CONVERGED", 8: "TIMEOUT", 9: "CUDA", 10: "CAPACITY",
+    11: "CANCELLED", 12: "PENDING", 13: "INTERNAL",
+}
+
+
+class QsdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class OpInfo(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_words", C.c_int32), ("n_terms_in", C.c_int64),
+                ("n_terms", C.c_int64), ("n_diag_terms", C.c_int64), ("n_groups", C.c_int64),
+                ("n_ladder_groups", C.c_int64), ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
+                ("is_hermitian", C.c_int32), ("identity_coef", C.c_double)]
+
+
+class LanczosParams(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_steps", C.c_int32), ("tol", C.c_double),
+                ("refine_tol", C.c_double), ("check_every", C.c_int32), ("refine_steps", C.c_int32),
+                ("max_refine", C.c_int32), ("use_graphs", C.c_int32), ("seed", C.c_uint64),
+                ("v0", C.c_void_p), ("time_limit_s", C.c_double)]
+
+
+class LanczosInfo(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("refine_restarts", C.c_int32), ("residual", C.c_double),
+                ("energy_unrefined", C.c_double), ("status", C.c_int32), ("applies", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every exported entry point
+_P, _I32, _I64, _U64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+SIGNATURES = [
+    ("qsd_create", C.c_int, [C.c_int, _P, C.POINTER(_P)]),
+    ("qsd_destroy", C.c_int, [_P]),
+    ("qsd_last_error", C.c_char_p, [_P]),
+    ("qsd_load_operator", C.c_int, [_P, _I32, _I64, _P, _P, _P, _P, _P, C.POINTER(_P)]),
+    ("qsd_op_get_info", C.c_int, [_P, C.POINTER(OpInfo)]),
+    ("qsd_op_groups", C.c_int, [_P, _P]),
+    ("qsd_free_op", C.c_int, [_P]),
+    ("qsd_build_subspace", C.c_int, [_P, _I32, _I64, _P, C.c_int, C.POINTER(_P), C.POINTER(_I64)]),
+    ("qsd_subspace_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
+    ("qsd_subspace_keys", C.c_int, [_P, _P, _P, C.c_int]),
+    ("qsd_subspace_index", C.c_int, [_P, _P, _I64, _P, _P]),
+    ("qsd_free_sub", C.c_int, [_P]),
+    ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
+    ("qsd_apply_H_host", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
+    ("qsd_diagonal", C.c_int, [_P, _P, _P, _P]),
+    ("qsd_target_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
+    ("qsd_term_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
+    ("qsd_lanczos_default_params", None, [C.POINTER(LanczosParams)]),
+    ("qsd_lanczos_ground_state", C.c_int, [_P, _P, _P, C.POINTER(LanczosParams), C.POINTER(_D), _P,
+                                          C.POINTER(LanczosInfo)]),
+]
+
+
+def lib(build_if_missing: bool = True):
+    """Load ``libqsd.so`` (building it first when absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                if not build_if_missing:
+                    raise ImportError(f"{LIB_PATH} is not built")
+                from . import build as _build
+                _build.build()
+            L = C.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _t_ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def W_of(n_qubits: int) -> int:
+    return 1 if n_qubits <= 64 else (n_qubits + 63) // 64
+
+
+class Operator:
+    def __init__(self, ctx: "Context", handle, n_qubits: int):
+        self.ctx, self.handle, self.n_qubits = ctx, handle, n_qubits
+
+    def info(self) -> dict:
+        i = OpInfo()
+        self.ctx._check(lib().qsd_op_get_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in OpInfo._fields_}
+
+    def groups(self) -> np.ndarray:
+        g = self.info()["n_groups"]
+        out = np.zeros((max(g, 1), W_of(self.n_qubits)), np.uint64)
+        self.ctx._check(lib().qsd_op_groups(self.handle, _np_ptr(out)))
+        return out[:g]
+
+    def free(self):
+        if self.handle:
+            lib().qsd_free_op(self.handle)
+            self.handle = None
+
+
+class Subspace:
+    def __init__(self, ctx: "Context", handle, n_qubits: int, dim: int):
+        self.ctx, self.handle, self.n_qubits, self.dim = ctx, handle, n_qubits, dim
+
+    @property
+    def W(self) -> int:
+        return W_of(self.n_qubits)
+
+    def capacity(self) -> int:
+        d, n, cap = C.c_int64(), C.c_int32(), C.c_int64()
+        self.ctx._check(lib().qsd_subspace_info(self.handle, C.byref(d), C.byref(n), C.byref(cap)))
+        return cap.value
+
+    def free(self):
+        if self.handle:
+            lib().qsd_free_sub(self.handle)
+            self.handle = None
+
+
+class Context:
+    """A library context on one CUDA device and one CUDA stream (a dedicated
+    ``torch.cuda.Stream`` unless one is given)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2603_18731_gb300 needs a CUDA GPU; none is visible")
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = C.c_void_p()
+        rc = lib().qsd_create(device, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != QSD_OK:
+            raise QsdError(rc, lib().qsd_last_error(None).decode())
+        self.handle = h
+
+    # -- plumbing
+    def _check(self, rc: int):
+        if rc != QSD_OK:
+            raise QsdError(rc, lib().qsd_last_error(self.handle).decode())
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def empty(self, shape, dtype):
+        with self.torch.cuda.stream(self.stream):
+            return self.torch.empty(shape, dtype=dtype, device=self.device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qsd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- ABI calls
+    def load_operator(self, op) -> Operator:
+        """``op``: any object with n_qubits, term_ptr, op_qubit, op_code, coef
+        (complex) as numpy arrays (e.g. ``workloads.QubitOperator``)."""
+        tp = np.ascontiguousarray(op.term_ptr, np.int64)
+        oq = np.ascontiguousarray(op.op_qubit, np.int32)
+        oc = np.ascontiguousarray(op.op_code, np.uint8)
+        cr = np.ascontiguousarray(np.real(op.coef), np.float64)
+        ci = np.ascontiguousarray(np.imag(op.coef), np.float64)
+        h = C.c_void_p()
+        self._check(lib().qsd_load_operator(self.handle, int(op.n_qubits), int(cr.shape[0]), _np_ptr(tp),
+                                            _np_ptr(oq), _np_ptr(oc), _np_ptr(cr), _np_ptr(ci), C.byref(h)))
+        return Operator(self, h, int(op.n_qubits))
+
+    def build_subspace(self, n_qubits: int, words) -> Subspace:
+        """``words``: [n, W] uint64 numpy array (host) or int64/uint64 CUDA tensor."""
+        h = C.c_void_p()
+        dim = C.c_int64()
+        if isinstance(words, np.ndarray):
+            w = np.ascontiguousarray(words, np.uint64)
+            self._check(lib().qsd_build_subspace(self.handle, n_qubits, int(w.shape[0]), _np_ptr(w), 0,
+                                                 C.byref(h), C.byref(dim)))
+        else:
+            w = words.contiguous()
+            self._check(lib().qsd_build_subspace(self.handle, n_qubits, int(w.shape[0]), _t_ptr(w), 1,
+                                                 C.byref(h), C.byref(dim)))
+        return Subspace(self, h, n_qubits, dim.value)
+
+    def subspace_keys(self, sub: Subspace) -> np.ndarray:
+        out = np.zeros((max(sub.dim, 1), sub.W), np.uint64)
+        self._check(lib().qsd_subspace_keys(self.handle, sub.handle, _np_ptr(out), 0))
+        return out[:sub.dim]
+
+    def subspace_index(self, sub: Subspace, keys):
+        """``keys``: CUDA int64 tensor [n, W] (bit patterns); returns int64 [n]."""
+        keys = keys.contiguous()
+        out = self.empty((keys.shape[0],), self.torch.int64)
+        self._check(lib().qsd_subspace_index(self.handle, sub.handle, int(keys.shape[0]), _t_ptr(keys),
+                                             _t_ptr(out)))
+        return out
+
+    def apply_H(self, op: Operator, sub: Subspace, x, y=None, precision: int = QSD_FP64):
+        """y = H_S x for CUDA tensors x of shape [D] or [D, k]."""
+        dt = self.torch.float64 if precision == QSD_FP64 else self.torch.float32
+        if x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {dt} tensor")
+        k = 1 if x.dim() == 1 else int(x.shape[1])
+        if y is None:
+            y = self.empty(tuple(x.shape), dt)
+        self._check(lib().qsd_apply_H(self.handle, op.handle, sub.handle, precision, k, _t_ptr(x), _t_ptr(y)))
+        return y
+
+    def apply_H_host(self, op: Operator, sub: Subspace, x: np.ndarray, precision: int = QSD_FP64,
+                     out: np.ndarray | None = None) -> np.ndarray:
+        dt = np.float64 if precision == QSD_FP64 else np.float32
+        if x.dtype != dt or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"x must be a contiguous {dt} array")
+        k = 1 if x.ndim == 1 else int(x.shape[1])
+        y = np.empty_like(x) if out is None else out
+        self._check(lib().qsd_apply_H_host(self.handle, op.handle, sub.handle, precision, k, _np_ptr(x),
+                                           _np_ptr(y)))
+        return y
+
+    def diagonal(self, op: Operator, sub: Subspace):
+        out = self.empty((sub.dim,), self.torch.float64)
+        self._check(lib().qsd_diagonal(self.handle, op.handle, sub.handle, _t_ptr(out)))
+        return out
+
+    def target_table(self, op: Operator, sub: Subspace, row0: int = 0, nrows: int | None = None):
+        nrows = sub.dim - row0 if nrows is None else nrows
+        G = op.info()["n_groups"]
+        out = self.empty((nrows, G), self.torch.int64)
+        self._check(lib().qsd_target_table(self.handle, op.handle, sub.handle, row0, nrows, _t_ptr(out)))
+        return out
+
+    def term_table(self, op: Operator, sub: Subspace, row0: int = 0, nrows: int | None = None):
+        nrows = sub.dim - row0 if nrows is None else nrows
+        T = op.info()["n_terms_in"]
+        out = self.empty((nrows, T), self.torch.int8)
+        self._check(lib().qsd_term_table(self.handle, op.handle, sub.handle, row0, nrows, _t_ptr(out)))
+        return out
+
+    def lanczos_ground_state(self, op: Operator, sub: Subspace, want_vector: bool = False,
+                             check: bool = True, **params):
+        """Returns (energy, info dict[, vector tensor]).  Keyword arguments set
+        fields of qsd_lanczos_params (precision, max_steps, tol, ...)."""
+        p = LanczosParams()
+        lib().qsd_lanczos_default_params(C.byref(p))
+        v0 = params.pop("v0", None)
+        for k, v in params.items():
+            setattr(p, k, v)
+        if v0 is not None:
+            p.v0 = C.c_void_p(v0.data_ptr())
+        e = C.c_double()
+        info = LanczosInfo()
+        vec = self.empty((sub.dim,), self.torch.float64) if want_vector else None
+        rc = lib().qsd_lanczos_ground_state(self.handle, op.handle, sub.handle, C.byref(p), C.byref(e),
+                                            _t_ptr(vec) if vec is not None else None, C.byref(info))
+        d = {f: getattr(info, f) for f, _ in LanczosInfo._fields_}
+        if check and rc not in (QSD_OK,):
+            raise QsdError(rc, lib().qsd_last_error(self.handle).decode())
+        return (e.value, d, vec) if want_vector else (e.value, d)
+
+
+def create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)

@@ -1,0 +1,511 @@
+// C ABI entry points (include/qsd.h): argument checks, handle management,
+// error translation, and the host side of the product dispatch.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "apply_kernel.cuh"
+#include "qsd_internal.cuh"
+
+namespace qsd {
+
+thread_local std::string g_thread_error;
+
+void fail(int code, const std::string &msg) { throw Error(code, msg); }
+
+void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    const int code = (e == cudaErrorMemoryAllocation) ? QSD_ERR_OOM : QSD_ERR_CUDA;
+    const char *f = std::strrchr(file, '/');
+    throw Error(code, std::string(what) + ": " + cudaGetErrorString(e) + " (" + (f ? f + 1 : file) + ":" +
+                          std::to_string(line) + ")");
+}
+
+void DevBuf::alloc(size_t n) {
+    release();
+    if (n == 0) return;
+    const cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        throw Error(QSD_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = n;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+// ------------------------------------------------------------ hash tables
+namespace {
+uint64_t splitmix_next(uint64_t &state) {
+    state += 0x9E3779B97F4A7C15ull;
+    return fmix64(state);
+}
+std::mutex g_nib_mu;
+std::vector<uint64_t> g_nib;  // [(W-1)*256]
+int g_nib_words = 1;
+}  // namespace
+
+const std::vector<uint64_t> &host_nibble_tables(int W) {
+    std::lock_guard<std::mutex> lk(g_nib_mu);
+    if (W > g_nib_words) {
+        // random GF(2) columns Q[q] for qubits 64..64W-1, fixed seed
+        uint64_t st = 0x5153445F48415348ull;  // "QSD_HASH"
+        std::vector<uint64_t> Q((size_t)64 * W);
+        for (auto &v : Q) v = splitmix_next(st);
+        g_nib.assign((size_t)(W - 1) * 256, 0);
+        for (int w = 1; w < W; ++w)
+            for (int j = 0; j < 16; ++j)
+                for (int v = 0; v < 16; ++v) {
+                    uint64_t h = 0;
+                    for (int b = 0; b < 4; ++b)
+                        if ((v >> b) & 1) h ^= Q[(size_t)64 * w + 4 * j + b];
+                    g_nib[(size_t)(w - 1) * 256 + j * 16 + v] = h;
+                }
+        g_nib_words = W;
+    }
+    return g_nib;
+}
+
+uint64_t host_prehash(const uint64_t *x, int W) {
+    const auto &t = host_nibble_tables(W);
+    uint64_t h = x[0];
+    for (int w = 1; w < W; ++w)
+        for (int j = 0; j < 16; ++j) h ^= t[(size_t)(w - 1) * 256 + j * 16 + ((x[w] >> (4 * j)) & 15)];
+    return h;
+}
+
+void ensure_nibble_tables(qsd_ctx ctx, int W) {
+    const int want = std::max(W, 8);
+    if (ctx->nib_words >= want) return;
+    const auto &t = host_nibble_tables(want);
+    QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->nib.alloc(t.size() * 8);
+    QSD_CUDA(cudaMemcpy(ctx->nib.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
+    ctx->nib_words = want;
+}
+
+uint32_t take_device_error(qsd_ctx ctx) {
+    QSD_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    const uint32_t e = *ctx->h_err;
+    if (e) QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    return e;
+}
+
+// ------------------------------------------------------------ bindings
+Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    auto key = std::make_pair((const void *)op, (const void *)sub);
+    auto it = ctx->bindings.find(key);
+    if (it != ctx->bindings.end()) return it->second;
+    auto *b = new Binding();
+    try {
+        b->diag.alloc((size_t)std::max<int64_t>(sub->D, 1) * 8);
+        compute_diagonal(ctx, op, sub, b->diag.as<double>());
+        QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        delete b;
+        throw;
+    }
+    ctx->bindings[key] = b;
+    return b;
+}
+
+void drop_bindings(qsd_ctx ctx, const void *handle) {
+    for (auto it = ctx->bindings.begin(); it != ctx->bindings.end();) {
+        if (it->first.first == handle || it->first.second == handle) {
+            delete it->second;
+            it = ctx->bindings.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// ------------------------------------------------------------ product
+// Lanes per row: a lane per row once there are enough rows to fill the GPU
+// twice over; otherwise more lanes per row (never more than the groups).
+static int choose_lanes(qsd_ctx ctx, int64_t D, int64_t G) {
+    const int64_t full = (int64_t)ctx->num_sms * 2048 * 2;
+    int R = 1;
+    if (D > 0 && D < full) {
+        const int64_t want = (full + D - 1) / D;
+        R = want >= 32 ? 32 : (want >= 4 ? 4 : 1);
+    }
+    while (R > 1 && R / 2 >= G) R = R == 32 ? 4 : 1;
+    return R;
+}
+
+void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
+             cudaStream_t stream) {
+    ApplyParams p{};
+    p.keys = sub->keys.as<uint64_t>();
+    p.D = sub->D;
+    p.slots = sub->slots.as<uint64_t>();
+    p.bmask = (uint64_t)sub->n_buckets - 1;
+    p.nib = ctx->nib.as<uint64_t>();
+    p.G = op->G;
+    p.gF = op->gF.as<uint64_t>();
+    p.ghash = op->ghash.as<uint64_t>();
+    p.grange = op->grange.as<int32_t>();
+    p.gL = op->gL.as<uint8_t>();
+    p.gpos = op->gpos.as<uint64_t>();
+    p.gptr = op->gptr.as<int32_t>();
+    p.T = op->T;
+    p.tP = op->tP.as<uint64_t>();
+    p.tV = op->tV.as<uint64_t>();
+    p.tZ = op->tZ.as<uint64_t>();
+    p.tphi = op->tphi.as<double>();
+    p.tflag = op->tflag.as<uint8_t>();
+    p.diag = diag;
+    p.x = x;
+    p.y = y;
+    p.ld = k;
+    p.err = ctx->d_err;
+    const int R = choose_lanes(ctx, sub->D, op->G);
+    int64_t c = 0;
+    while (c < k) {
+        const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
+        p.col0 = c;
+        if (precision == QSD_FP64) launch_apply<double>(p, op->W, R, KB, stream);
+        else launch_apply<float>(p, op->W, R, KB, stream);
+        c += KB;
+    }
+}
+
+}  // namespace qsd
+
+using namespace qsd;
+
+// ------------------------------------------------------------ ABI helpers
+#define QSD_GUARD(ctxp, ...)                                           \
+    do {                                                               \
+        try {                                                          \
+            __VA_ARGS__;                                               \
+            return QSD_OK;                                             \
+        } catch (const qsd::Error &e) {                                \
+            if (ctxp) (ctxp)->last_error = e.what();                   \
+            else qsd::g_thread_error = e.what();                       \
+            return e.code;                                             \
+        } catch (const std::bad_alloc &) {                             \
+            if (ctxp) (ctxp)->last_error = "host allocation failed";   \
+            return QSD_ERR_OOM;                                        \
+        } catch (const std::exception &e) {                            \
+            if (ctxp) (ctxp)->last_error = e.what();                   \
+            return QSD_ERR_INTERNAL;                                   \
+        }                                                              \
+    } while (0)
+
+static void set_device(qsd_ctx ctx) { QSD_CUDA(cudaSetDevice(ctx->device)); }
+
+static int W_of(int32_t n) { return n <= 64 ? 1 : (n + 63) / 64; }
+
+extern "C" {
+
+int qsd_create(int device, void *cuda_stream, qsd_ctx *out) {
+    qsd_ctx ctx = nullptr;
+    try {
+        if (!out) fail(QSD_ERR_INVALID_ARG, "qsd_create: out is NULL");
+        int n = 0;
+        QSD_CUDA(cudaGetDeviceCount(&n));
+        if (device < 0 || device >= n) fail(QSD_ERR_INVALID_ARG, "qsd_create: no such device");
+        ctx = new qsd_ctx_s();
+        ctx->device = device;
+        QSD_CUDA(cudaSetDevice(device));
+        QSD_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            QSD_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        QSD_CUDA(cudaMalloc(&ctx->d_err, 4));
+        QSD_CUDA(cudaMemset(ctx->d_err, 0, 4));
+        QSD_CUDA(cudaMallocHost(&ctx->h_err, 4));
+        ensure_nibble_tables(ctx, 8);
+        *out = ctx;
+        return QSD_OK;
+    } catch (const qsd::Error &e) {
+        g_thread_error = e.what();
+        if (ctx) qsd_destroy(ctx);
+        return e.code;
+    } catch (const std::exception &e) {
+        g_thread_error = e.what();
+        if (ctx) qsd_destroy(ctx);
+        return QSD_ERR_INTERNAL;
+    }
+}
+
+int qsd_destroy(qsd_ctx ctx) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->bindings) delete kv.second;
+    ctx->bindings.clear();
+    ctx->nib.release();
+    for (auto &s : ctx->scratch) s.buf.release();
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return QSD_OK;
+}
+
+const char *qsd_last_error(qsd_ctx ctx) { return ctx ? ctx->last_error.c_str() : g_thread_error.c_str(); }
+
+int qsd_load_operator(qsd_ctx ctx, int32_t n_qubits, int64_t n_terms, const int64_t *term_ptr,
+                      const int32_t *op_qubit, const uint8_t *op_code, const double *coef_re,
+                      const double *coef_im, qsd_op *out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        if (!out || n_qubits < 1) fail(QSD_ERR_INVALID_ARG, "qsd_load_operator: bad arguments");
+        set_device(ctx);
+        auto *op = new qsd_op_s();
+        op->ctx = ctx;
+        op->n_qubits = n_qubits;
+        op->W = W_of(n_qubits);
+        if (op->W > kMaxWordsDyn) {
+            delete op;
+            fail(QSD_ERR_INVALID_ARG, "qsd_load_operator: more than 4096 qubits");
+        }
+        try {
+            load_operator(ctx, op, n_terms, term_ptr, op_qubit, op_code, coef_re, coef_im);
+        } catch (...) {
+            delete op;
+            throw;
+        }
+        *out = op;
+    });
+}
+
+int qsd_op_get_info(qsd_op op, qsd_op_info *info) {
+    if (!op || !info) return QSD_ERR_INVALID_ARG;
+    *info = op->info;
+    return QSD_OK;
+}
+
+int qsd_op_groups(qsd_op op, uint64_t *groups_out) {
+    if (!op || (!groups_out && op->G > 0)) return QSD_ERR_INVALID_ARG;
+    if (op->G > 0) std::memcpy(groups_out, op->host_groups.data(), op->host_groups.size() * 8);
+    return QSD_OK;
+}
+
+int qsd_free_op(qsd_op op) {
+    if (!op) return QSD_ERR_INVALID_ARG;
+    qsd_ctx ctx = op->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_bindings(ctx, op);
+    delete op;
+    return QSD_OK;
+}
+
+int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in, const uint64_t *words, int words_on_device,
+                       qsd_sub *out, int64_t *dim_out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        if (!out || n_qubits < 1 || n_in < 0 || (n_in > 0 && !words))
+            fail(QSD_ERR_INVALID_ARG, "qsd_build_subspace: bad arguments");
+        set_device(ctx);
+        auto *sub = new qsd_sub_s();
+        sub->ctx = ctx;
+        sub->n_qubits = n_qubits;
+        sub->W = W_of(n_qubits);
+        if (sub->W > kMaxWordsDyn) {
+            delete sub;
+            fail(QSD_ERR_INVALID_ARG, "qsd_build_subspace: more than 4096 qubits");
+        }
+        try {
+            build_subspace(ctx, sub, words, n_in, words_on_device != 0);
+        } catch (...) {
+            delete sub;
+            throw;
+        }
+        *out = sub;
+        if (dim_out) *dim_out = sub->D;
+    });
+}
+
+int qsd_subspace_info(qsd_sub sub, int64_t *dim, int32_t *n_qubits, int64_t *capacity) {
+    if (!sub) return QSD_ERR_INVALID_ARG;
+    if (dim) *dim = sub->D;
+    if (n_qubits) *n_qubits = sub->n_qubits;
+    if (capacity) *capacity = sub->n_buckets * kBucketSlots;
+    return QSD_OK;
+}
+
+int qsd_subspace_keys(qsd_ctx ctx, qsd_sub sub, uint64_t *out, int out_on_device) {
+    if (!ctx || !sub) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        if (sub->D > 0 && !out) fail(QSD_ERR_INVALID_ARG, "qsd_subspace_keys: out is NULL");
+        set_device(ctx);
+        if (sub->D == 0) return QSD_OK;
+        if (out_on_device) {
+            subspace_keys_aos(ctx, sub, out);
+        } else {
+            DevBuf tmp((size_t)sub->D * sub->W * 8);
+            subspace_keys_aos(ctx, sub, tmp.as<uint64_t>());
+            QSD_CUDA(cudaMemcpyAsync(out, tmp.p, tmp.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
+    });
+}
+
+int qsd_subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *keys, int64_t *idx_out) {
+    if (!ctx || !sub) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        if (n < 0 || (n > 0 && (!keys || !idx_out))) fail(QSD_ERR_INVALID_ARG, "qsd_subspace_index: bad arguments");
+        set_device(ctx);
+        subspace_index(ctx, sub, n, keys, idx_out);
+    });
+}
+
+int qsd_free_sub(qsd_sub sub) {
+    if (!sub) return QSD_ERR_INVALID_ARG;
+    qsd_ctx ctx = sub->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_bindings(ctx, sub);
+    delete sub;
+    return QSD_OK;
+}
+
+static void check_pair(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    if (!op || !sub) fail(QSD_ERR_INVALID_ARG, "NULL operator or subspace");
+    if (op->ctx != ctx || sub->ctx != ctx) fail(QSD_ERR_INVALID_ARG, "handles belong to another context");
+    if (op->n_qubits != sub->n_qubits)
+        fail(QSD_ERR_INVALID_ARG, "operator has " + std::to_string(op->n_qubits) + " qubits, subspace " +
+                                      std::to_string(sub->n_qubits));
+}
+
+int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, const void *x, void *y) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (k < 1 || (precision != QSD_FP64 && precision != QSD_FP32_MIXED))
+            fail(QSD_ERR_INVALID_ARG, "qsd_apply_H: bad k or precision");
+        if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_apply_H: operator has complex matrix elements");
+        if (sub->D == 0) return QSD_OK;
+        if (!x || !y) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H: NULL vector");
+        set_device(ctx);
+        Binding *b = get_binding(ctx, op, sub);
+        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, x, y, ctx->stream);
+    });
+}
+
+int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, const void *x_host,
+                     void *y_host) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (k < 1 || (precision != QSD_FP64 && precision != QSD_FP32_MIXED))
+            fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_host: bad k or precision");
+        if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_apply_H_host: complex operator");
+        if (sub->D == 0) return QSD_OK;
+        if (!x_host || !y_host) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_host: NULL vector");
+        set_device(ctx);
+        Binding *b = get_binding(ctx, op, sub);
+        const size_t bytes = (size_t)sub->D * k * (precision == QSD_FP64 ? 8 : 4);
+        Scratch &sx = ctx->scratch[0], &sy = ctx->scratch[1];
+        void *dx = sx.get(bytes), *dy = sy.get(bytes);
+        QSD_CUDA(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, dx, dy, ctx->stream);
+        QSD_CUDA(cudaMemcpyAsync(y_host, dy, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+int qsd_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d_out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (sub->D == 0) return QSD_OK;
+        if (!d_out) fail(QSD_ERR_INVALID_ARG, "qsd_diagonal: NULL output");
+        set_device(ctx);
+        Binding *b = get_binding(ctx, op, sub);
+        QSD_CUDA(cudaMemcpyAsync(d_out, b->diag.p, (size_t)sub->D * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    });
+}
+
+int qsd_target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (row0 < 0 || nrows < 0 || row0 + nrows > sub->D) fail(QSD_ERR_INVALID_ARG, "qsd_target_table: bad row range");
+        if (nrows > 0 && op->G > 0 && !out) fail(QSD_ERR_INVALID_ARG, "qsd_target_table: NULL output");
+        set_device(ctx);
+        target_table(ctx, op, sub, row0, nrows, out);
+    });
+}
+
+int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int8_t *out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (row0 < 0 || nrows < 0 || row0 + nrows > sub->D) fail(QSD_ERR_INVALID_ARG, "qsd_term_table: bad row range");
+        if (nrows > 0 && op->T_in > 0 && !out) fail(QSD_ERR_INVALID_ARG, "qsd_term_table: NULL output");
+        set_device(ctx);
+        term_table(ctx, op, sub, row0, nrows, out);
+    });
+}
+
+void qsd_lanczos_default_params(qsd_lanczos_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->precision = QSD_FP64;
+    p->max_steps = 300;
+    p->tol = 1e-9;
+    p->refine_tol = 1e-10;
+    p->check_every = 10;
+    p->refine_steps = 30;
+    p->max_refine = 5;
+    p->use_graphs = 1;
+    p->seed = 1;
+    p->v0 = nullptr;
+    p->time_limit_s = 0.0;
+}
+
+int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_params *p, double *energy,
+                             double *vec_out, qsd_lanczos_info *info) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int rc = QSD_OK;
+    try {
+        check_pair(ctx, op, sub);
+        if (!p || !energy || p->max_steps < 1 || p->check_every < 1 ||
+            (p->precision != QSD_FP64 && p->precision != QSD_FP32_MIXED))
+            fail(QSD_ERR_INVALID_ARG, "qsd_lanczos_ground_state: bad arguments");
+        if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_lanczos_ground_state: complex operator");
+        if (!op->info.is_hermitian) fail(QSD_ERR_NOT_HERMITIAN, "qsd_lanczos_ground_state: operator is not Hermitian");
+        if (sub->D == 0) fail(QSD_ERR_INVALID_ARG, "qsd_lanczos_ground_state: empty subspace");
+        set_device(ctx);
+        rc = lanczos_ground_state(ctx, op, sub, *p, energy, vec_out, info);
+        if (rc != QSD_OK && rc != QSD_ERR_NOT_CONVERGED) ctx->last_error = "lanczos: status " + std::to_string(rc);
+        if (rc == QSD_ERR_NOT_CONVERGED) ctx->last_error = "lanczos: max_steps reached before tol";
+    } catch (const qsd::Error &e) {
+        ctx->last_error = e.what();
+        rc = e.code;
+    } catch (const std::exception &e) {
+        ctx->last_error = e.what();
+        rc = QSD_ERR_INTERNAL;
+    }
+    if (info) info->status = rc;
+    return rc;
+}
+
+}  // extern "C"

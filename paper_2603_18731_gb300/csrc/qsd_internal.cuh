@@ -1,0 +1,283 @@
+// Internal declarations of the GB300 subspace Hamiltonian library.
+//
+// Layout in device memory (all arrays are plain cudaMalloc allocations owned
+// by the handles):
+//   subspace  keys   uint64 [W][D]   SoA, sorted ascending (word W-1 most
+//                                    significant); row index = rank
+//             slots  uint64 [cap]    4-slot buckets, slot = tag<<32 | index,
+//                                    empty = all ones; load factor <= 1/2
+//   operator  off-diagonal terms grouped by flip mask F (Methods, properties
+//             1-3): per group F[W][G], hash of F, term range, ladder table;
+//             per term P/V/Z masks [W][T] and the real phase phi[T]
+//             diagonal terms separately (the cached diagonal, Methods
+//             "Matrix evaluation")
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/qsd.h"
+
+namespace qsd {
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+#define QSD_CUDA(call) ::qsd::cuda_check((call), #call, __FILE__, __LINE__)
+#define QSD_LAUNCH_CHECK() ::qsd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// ------------------------------------------------------------------ memory
+// Owning device allocation.  Allocation failure throws QSD_ERR_OOM.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t n) { alloc(n); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t n);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Grow-only scratch buffer (reused between calls on one context).
+struct Scratch {
+    DevBuf buf;
+    void *get(size_t bytes) {
+        if (buf.bytes < bytes) { buf.release(); buf.alloc(bytes + bytes / 4); }
+        return buf.p;
+    }
+};
+
+// ------------------------------------------------------------------ handles
+struct Binding;
+
+}  // namespace qsd
+
+struct qsd_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string last_error;
+    std::mutex mu;
+    qsd::Scratch scratch[4];
+    // (operator, subspace) -> cached diagonal; dropped when either is freed
+    std::map<std::pair<const void *, const void *>, qsd::Binding *> bindings;
+    // device copy of the nibble tables of the prehash (see hash_prehash)
+    qsd::DevBuf nib;
+    int nib_words = 0;
+    uint32_t *d_err = nullptr;   // device error word of the last kernels
+    uint32_t *h_err = nullptr;   // pinned mirror
+};
+
+struct qsd_sub_s {
+    qsd_ctx ctx = nullptr;
+    int32_t n_qubits = 0;
+    int W = 1;
+    int64_t D = 0;
+    int64_t n_buckets = 0;  // power of two; capacity = 4 * n_buckets slots
+    qsd::DevBuf keys;   // uint64 [W][D]
+    qsd::DevBuf slots;  // uint64 [4 * n_buckets]
+};
+
+struct qsd_op_s {
+    qsd_ctx ctx = nullptr;
+    int32_t n_qubits = 0;
+    int W = 1;
+    qsd_op_info info{};
+    double identity = 0.0;
+    // off-diagonal groups (G) and terms (T), group order
+    int64_t G = 0, T = 0;
+    qsd::DevBuf gF;      // uint64 [W][G]
+    qsd::DevBuf ghash;   // uint64 [G]  prehash of F
+    qsd::DevBuf grange;  // int32  [G+1] term offsets
+    qsd::DevBuf gL;      // uint8  [G]  ladder bits with a table (0: scan the group)
+    qsd::DevBuf gpos;    // uint64 [G]  4 x 16-bit flipped-qubit positions, ascending
+    qsd::DevBuf gptr;    // int32  [G][17] ladder-integer term offsets (absolute)
+    qsd::DevBuf tP, tV, tZ;  // uint64 [W][T]
+    qsd::DevBuf tphi;    // double [T] real phase * coefficient
+    qsd::DevBuf tphi_im; // double [T]
+    qsd::DevBuf tflag;   // uint8  [T] bit0: P != 0, bit1: Z != 0
+    // diagonal terms (Td)
+    int64_t Td = 0;
+    qsd::DevBuf dP, dV, dZ;  // uint64 [W][Td]
+    qsd::DevBuf dphi;        // double [Td]
+    // input terms as masks, for the term table
+    int64_t T_in = 0;
+    qsd::DevBuf iF, iP, iV, iZ;  // uint64 [W][T_in]
+    qsd::DevBuf iY;              // uint8 [T_in] number of Y letters mod 4
+    std::vector<uint64_t> host_groups;  // [G][W]
+};
+
+namespace qsd {
+
+struct Binding {
+    DevBuf diag;  // double [D]
+};
+
+// ------------------------------------------------------------ device hash
+// Keys are hashed in two steps.  (1) A GF(2)-linear prehash h(x) = x_0 xor
+// L_1(x_1) xor ... where L_w is a random linear map of word w given by 16
+// nibble tables of 16 entries (one 128-byte line each).  Linearity gives
+// h(r xor F) = h(r) xor h(F): a row's prehash is computed once and each
+// group costs one xor.  (2) The SplitMix64 finaliser (Steele, Lea & Flood,
+// OOPSLA 2014) mixes h into the bucket (low bits) and the 32-bit tag (high
+// bits).  Collisions of h only cost probes; every hit is verified against
+// the full key.
+constexpr uint64_t kEmptySlot = ~0ull;
+constexpr int kBucketSlots = 4;
+
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// nib: tables for words 1..W-1, [(w-1)][16 nibble positions][16 values]
+template <int W>
+__device__ __forceinline__ uint64_t prehash(const uint64_t (&x)[W], const uint64_t *__restrict__ nib) {
+    uint64_t h = x[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+        const uint64_t *t = nib + (size_t)(w - 1) * 256;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h ^= __ldg(t + j * 16 + ((x[w] >> (4 * j)) & 15));
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint64_t prehash_dyn(const uint64_t *x, int W, const uint64_t *__restrict__ nib) {
+    uint64_t h = x[0];
+    for (int w = 1; w < W; ++w) {
+        const uint64_t *t = nib + (size_t)(w - 1) * 256;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h ^= __ldg(t + j * 16 + ((x[w] >> (4 * j)) & 15));
+    }
+    return h;
+}
+
+// Host prehash of a W-word key (same tables as the device copy).
+uint64_t host_prehash(const uint64_t *x, int W);
+// Nibble tables for words 1..W-1 (host copy), [(W-1)*256].
+const std::vector<uint64_t> &host_nibble_tables(int W);
+void ensure_nibble_tables(qsd_ctx ctx, int W);
+
+// Lookup of column key c (W words, prehash hc) in the subspace; returns the
+// row index or -1.  Probing ends at the first bucket with an empty slot; at
+// most n_buckets buckets are visited (a full table yields -1 and sets *err).
+template <int W>
+__device__ __forceinline__ int64_t probe(const uint64_t (&c)[W], uint64_t hc,
+                                         const uint64_t *__restrict__ slots,
+                                         const uint64_t *__restrict__ keys, int64_t D,
+                                         uint64_t bucket_mask, uint32_t *err) {
+    const uint64_t m = fmix64(hc);
+    const uint32_t tag = (uint32_t)(m >> 32);
+    uint64_t b = m & bucket_mask;
+    for (uint64_t step = 0; step <= bucket_mask; ++step) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(slots + b * kBucketSlots);
+        const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1);
+        const uint64_t s[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (s[i] == kEmptySlot) return -1;
+            if ((uint32_t)(s[i] >> 32) == tag) {
+                const uint64_t idx = (uint32_t)s[i];
+                bool eq = true;
+#pragma unroll
+                for (int w = 0; w < W; ++w) eq &= (__ldg(keys + (size_t)w * D + idx) == c[w]);
+                if (eq) return (int64_t)idx;
+            }
+        }
+        b = (b + 1) & bucket_mask;
+    }
+    if (err) atomicOr(err, 1u);
+    return -1;
+}
+
+__device__ __forceinline__ int64_t probe_dyn(const uint64_t *c, int W, uint64_t hc,
+                                             const uint64_t *__restrict__ slots,
+                                             const uint64_t *__restrict__ keys, int64_t D,
+                                             uint64_t bucket_mask, uint32_t *err) {
+    const uint64_t m = fmix64(hc);
+    const uint32_t tag = (uint32_t)(m >> 32);
+    uint64_t b = m & bucket_mask;
+    for (uint64_t step = 0; step <= bucket_mask; ++step) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(slots + b * kBucketSlots);
+        const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1);
+        const uint64_t s[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (s[i] == kEmptySlot) return -1;
+            if ((uint32_t)(s[i] >> 32) == tag) {
+                const uint64_t idx = (uint32_t)s[i];
+                bool eq = true;
+                for (int w = 0; w < W; ++w) eq &= (__ldg(keys + (size_t)w * D + idx) == c[w]);
+                if (eq) return (int64_t)idx;
+            }
+        }
+        b = (b + 1) & bucket_mask;
+    }
+    if (err) atomicOr(err, 1u);
+    return -1;
+}
+
+// Largest W handled by the unrolled (template) kernels; larger W use the
+// run-time-W kernels with keys in local memory up to kMaxWordsDyn.
+constexpr int kMaxWordsStatic = 4;
+constexpr int kMaxWordsDyn = 64;  // 4096 qubits
+
+// ----------------------------------------------------------- primitives
+// Exclusive prefix sum of n uint32 (in place allowed); returns the total.
+uint64_t exclusive_scan_u32(qsd_ctx ctx, const uint32_t *in, uint32_t *out, int64_t n, bool want_total);
+// Stable LSD radix sort of n items by K-word keys (SoA, keys[w*n+i], word
+// K-1 most significant) with an optional uint32 payload, 8-bit digits;
+// digits that are equal for every item are skipped.
+void radix_sort(qsd_ctx ctx, uint64_t *keys, int K, int64_t n, uint32_t *payload);
+// flags[i] = 1 when item i of the sorted SoA keys starts a run of equal keys.
+void diff_flags(qsd_ctx ctx, const uint64_t *keys, int K, int64_t n, uint32_t *flags);
+// Keep the first of each run of equal K-word keys in the sorted SoA array;
+// writes the unique keys (SoA with stride n_out) to out and returns n_out.
+int64_t unique_sorted(qsd_ctx ctx, const uint64_t *keys, int K, int64_t n, uint64_t *out, int64_t out_cap);
+
+// ----------------------------------------------------------- operations
+void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_in, bool on_device);
+void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out);
+void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev);
+void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_ptr,
+                   const int32_t *op_qubit, const uint8_t *op_code, const double *coef_re,
+                   const double *coef_im);
+Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub);
+void drop_bindings(qsd_ctx ctx, const void *handle);
+void compute_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d);
+void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k,
+             const void *x, void *y, cudaStream_t stream);
+void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out);
+void term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int8_t *out);
+int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_params &p,
+                         double *energy, double *vec_out, qsd_lanczos_info *info);
+
+// Read and clear the device error word (synchronises the stream).
+uint32_t take_device_error(qsd_ctx ctx);
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace qsd

@@ -1,0 +1,188 @@
+// Subspace construction and lookup (Methods, "Subspace data structure").
+//
+// The paper keeps bit-sets in an insertion-ordered CPU hash map with an
+// occupancy bit-set for fast rejection of empty buckets.  Here the strings are
+// sorted by integer value on the device (index = rank, the order the MSOB
+// triangle test needs) and stored as coalesced SoA words; a separate open
+// addressing table of 8-byte (tag, index) slots in 4-slot, 32-byte buckets
+// serves lookups: one sector load rejects most absent keys, as the occupancy
+// bit-set did, and the load factor is kept <= 1/2 because D is known before
+// the table is built.
+#include <algorithm>
+
+#include "qsd_internal.cuh"
+
+namespace qsd {
+
+namespace {
+
+__global__ void k_aos_to_soa(const uint64_t *__restrict__ in, int W, int64_t n, uint64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int w = 0; w < W; ++w) out[(size_t)w * n + i] = in[(size_t)i * W + w];
+}
+
+__global__ void k_soa_to_aos(const uint64_t *__restrict__ in, int W, int64_t n, uint64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int w = 0; w < W; ++w) out[(size_t)i * W + w] = in[(size_t)w * n + i];
+}
+
+__global__ void k_mask_top(uint64_t *words, int W, int64_t n, uint64_t top_mask, uint32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (words[(size_t)i * W + W - 1] & ~top_mask) atomicOr(err, 2u);
+}
+
+// One thread per key.  Slots of a bucket are claimed in order with CAS, so
+// in the finished table an empty slot ends every probe sequence that would
+// have reached a later slot.
+template <int W>
+__global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ nib,
+                              unsigned long long *slots, uint64_t bucket_mask, uint32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    uint64_t x[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
+    const uint64_t m = fmix64(prehash<W>(x, nib));
+    const unsigned long long val = ((unsigned long long)(uint32_t)(m >> 32) << 32) | (uint64_t)i;
+    uint64_t b = m & bucket_mask;
+    for (uint64_t step = 0; step <= bucket_mask; ++step) {
+        for (int s = 0; s < kBucketSlots; ++s)
+            if (atomicCAS(slots + b * kBucketSlots + s, (unsigned long long)kEmptySlot, val) == kEmptySlot) return;
+        b = (b + 1) & bucket_mask;
+    }
+    atomicOr(err, 1u);
+}
+
+__global__ void k_hash_insert_dyn(const uint64_t *__restrict__ keys, int W, int64_t D,
+                                  const uint64_t *__restrict__ nib, unsigned long long *slots,
+                                  uint64_t bucket_mask, uint32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    uint64_t x[kMaxWordsDyn];
+    for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
+    const uint64_t m = fmix64(prehash_dyn(x, W, nib));
+    const unsigned long long val = ((unsigned long long)(uint32_t)(m >> 32) << 32) | (uint64_t)i;
+    uint64_t b = m & bucket_mask;
+    for (uint64_t step = 0; step <= bucket_mask; ++step) {
+        for (int s = 0; s < kBucketSlots; ++s)
+            if (atomicCAS(slots + b * kBucketSlots + s, (unsigned long long)kEmptySlot, val) == kEmptySlot) return;
+        b = (b + 1) & bucket_mask;
+    }
+    atomicOr(err, 1u);
+}
+
+template <int W>
+__global__ void k_index(const uint64_t *__restrict__ q, int64_t n, const uint64_t *__restrict__ keys, int64_t D,
+                        const uint64_t *__restrict__ slots, uint64_t bucket_mask,
+                        const uint64_t *__restrict__ nib, int64_t *out, uint32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t c[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
+    out[i] = D > 0 ? probe<W>(c, prehash<W>(c, nib), slots, keys, D, bucket_mask, err) : -1;
+}
+
+__global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, const uint64_t *__restrict__ keys,
+                            int64_t D, const uint64_t *__restrict__ slots, uint64_t bucket_mask,
+                            const uint64_t *__restrict__ nib, int64_t *out, uint32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t c[kMaxWordsDyn];
+    for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
+    out[i] = D > 0 ? probe_dyn(c, W, prehash_dyn(c, W, nib), slots, keys, D, bucket_mask, err) : -1;
+}
+
+uint64_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_in, bool on_device) {
+    cudaStream_t s = ctx->stream;
+    const int W = sub->W;
+    ensure_nibble_tables(ctx, W);
+    const uint64_t top_bits = (uint64_t)(sub->n_qubits - 64 * (W - 1));
+    const uint64_t top_mask = top_bits >= 64 ? ~0ull : ((1ull << top_bits) - 1);
+    DevBuf soa;
+    int64_t D = 0;
+    if (n_in > 0) {
+        DevBuf staged;
+        const uint64_t *aos = words;
+        if (!on_device) {
+            staged.alloc((size_t)n_in * W * 8);
+            QSD_CUDA(cudaMemcpyAsync(staged.p, words, (size_t)n_in * W * 8, cudaMemcpyHostToDevice, s));
+            aos = staged.as<uint64_t>();
+        }
+        QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
+        k_mask_top<<<blocks_for(n_in, 256), 256, 0, s>>>(const_cast<uint64_t *>(aos), W, n_in, top_mask, ctx->d_err);
+        QSD_LAUNCH_CHECK();
+        if (take_device_error(ctx) & 2u)
+            fail(QSD_ERR_QUBIT_RANGE, "build_subspace: a bit-string has bits set at or above n_qubits");
+        soa.alloc((size_t)n_in * W * 8);
+        k_aos_to_soa<<<blocks_for(n_in, 256), 256, 0, s>>>(aos, W, n_in, soa.as<uint64_t>());
+        QSD_LAUNCH_CHECK();
+        radix_sort(ctx, soa.as<uint64_t>(), W, n_in, nullptr);
+        D = unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, nullptr, 0);
+        if (D > (int64_t)0xfffffffeLL) fail(QSD_ERR_CAPACITY, "build_subspace: more than 2^32-2 distinct strings");
+    }
+    sub->D = D;
+    sub->keys.alloc((size_t)std::max<int64_t>(D, 1) * W * 8);
+    if (D > 0) unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, sub->keys.as<uint64_t>(), D);
+    soa.release();
+    // load factor <= 1/2 with 4-slot buckets
+    sub->n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(1, (2 * D + kBucketSlots - 1) / kBucketSlots));
+    sub->slots.alloc((size_t)sub->n_buckets * kBucketSlots * 8);
+    QSD_CUDA(cudaMemsetAsync(sub->slots.p, 0xff, (size_t)sub->n_buckets * kBucketSlots * 8, s));
+    if (D > 0) {
+        QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
+        const uint64_t mask = (uint64_t)sub->n_buckets - 1;
+        auto *sl = sub->slots.as<unsigned long long>();
+        const uint64_t *nib = ctx->nib.as<uint64_t>();
+        const int nb = blocks_for(D, 256);
+        switch (W) {
+        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
+        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
+        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
+        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
+        default:
+            k_hash_insert_dyn<<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), W, D, nib, sl, mask, ctx->d_err);
+        }
+        QSD_LAUNCH_CHECK();
+        if (take_device_error(ctx)) fail(QSD_ERR_INTERNAL, "build_subspace: hash table overflow");
+    }
+    QSD_CUDA(cudaStreamSynchronize(s));
+}
+
+void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out) {
+    if (n <= 0) return;
+    cudaStream_t s = ctx->stream;
+    const int W = sub->W;
+    const uint64_t mask = (uint64_t)sub->n_buckets - 1;
+    const uint64_t *nib = ctx->nib.as<uint64_t>();
+    const uint64_t *keys = sub->keys.as<uint64_t>();
+    const uint64_t *sl = sub->slots.as<uint64_t>();
+    const int nb = blocks_for(n, 256);
+    switch (W) {
+    case 1: k_index<1><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
+    case 2: k_index<2><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
+    case 3: k_index<3><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
+    case 4: k_index<4><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
+    default: k_index_dyn<<<nb, 256, 0, s>>>(q, W, n, keys, sub->D, sl, mask, nib, out, ctx->d_err);
+    }
+    QSD_LAUNCH_CHECK();
+}
+
+void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev) {
+    if (sub->D <= 0) return;
+    k_soa_to_aos<<<blocks_for(sub->D, 256), 256, 0, ctx->stream>>>(sub->keys.as<uint64_t>(), sub->W, sub->D, out_dev);
+    QSD_LAUNCH_CHECK();
+}
+
+}  // namespace qsd

@@ -1,0 +1,266 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Integer results (subspace order and indices, target and term tables) must be
+bit-exact.  FP64 products must match to 1e-12 relative max-norm; the FP32
+storage path (FP64 accumulation, one rounding per output) to 2^-23 of the
+largest output plus the FP32 rounding of the input; ground energies to 1e-10
+(FP64) and 1e-7 (FP32-mixed after FP64 refinement) relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2.0 ** -22
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2603_18731_gb300 as q
+    c = q.create(0)
+    yield c
+    c.close()
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(float(np.max(np.abs(b))) if b.size else 0.0, 1e-300)
+    return float(np.max(np.abs(a - b))) / scale if a.size else 0.0
+
+
+def to_cuda(ctx, arr, dtype):
+    import torch
+    with torch.cuda.stream(ctx.stream):
+        return torch.as_tensor(np.ascontiguousarray(arr), device=ctx.device).to(dtype)
+
+
+def keys_tensor(ctx, words):
+    import torch
+    with torch.cuda.stream(ctx.stream):
+        return torch.as_tensor(np.ascontiguousarray(words).view(np.int64), device=ctx.device)
+
+
+# ---------------------------------------------------------------- subspace
+@pytest.mark.parametrize("n,count,dups", [(12, 3000, 500), (36, 5000, 1000), (64, 4097, 100), (65, 3000, 10),
+                                          (130, 2500, 300), (200, 6000, 50), (300, 1500, 20), (20, 1, 0)])
+def test_subspace_sorted_keys_and_index_exact(ctx, n, count, dups):
+    words = wl.random_subspace(n, count, seed=n + count, duplicates=dups)
+    sub = ctx.build_subspace(n, words)
+    ref = oracle.sort_unique(words)
+    assert sub.dim == ref.shape[0]
+    assert np.array_equal(ctx.subspace_keys(sub), ref)
+    queries = np.concatenate([words[: min(500, len(words))], wl.random_subspace(n, 300, seed=7 * n)])
+    got = ctx.subspace_index(sub, keys_tensor(ctx, queries))
+    ctx.synchronize()
+    assert np.array_equal(got.cpu().numpy(), oracle.find(ref, queries))
+    sub.free()
+
+
+def test_subspace_from_device_words_and_empty(ctx):
+    words = wl.random_subspace(40, 1000, seed=3, duplicates=100)
+    sub = ctx.build_subspace(40, keys_tensor(ctx, words))
+    assert np.array_equal(ctx.subspace_keys(sub), oracle.sort_unique(words))
+    empty = ctx.build_subspace(40, np.zeros((0, 1), np.uint64))
+    assert empty.dim == 0
+    got = ctx.subspace_index(empty, keys_tensor(ctx, words[:10]))
+    ctx.synchronize()
+    assert (got.cpu().numpy() == -1).all()
+
+
+def test_subspace_rejects_bits_above_n(ctx):
+    import paper_2603_18731_gb300 as q
+    words = np.array([[1 << 40]], np.uint64)
+    with pytest.raises(q.QsdError) as e:
+        ctx.build_subspace(36, words)
+    assert e.value.status == "QUBIT_RANGE"
+
+
+# ---------------------------------------------------------------- products
+def _check_apply(ctx, op, words, k, seed, mixed=True):
+    import torch
+    import paper_2603_18731_gb300 as q
+    keys = oracle.sort_unique(words)
+    D = keys.shape[0]
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(D, k)) if k > 1 else rng.normal(size=D)
+    ref = oracle.apply(op, keys, x)
+    assert np.max(np.abs(ref.imag)) <= 1e-12 * max(np.max(np.abs(ref.real)), 1.0)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(op.n_qubits, words)
+    y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+    ctx.synchronize()
+    assert rel_err(y.cpu().numpy(), ref.real) <= FP64_TOL
+    if mixed:
+        x32 = x.astype(np.float32)
+        ref32 = oracle.apply(op, keys, x32.astype(np.float64)).real
+        y32 = ctx.apply_H(h, sub, to_cuda(ctx, x32, torch.float32), precision=q.QSD_FP32_MIXED)
+        ctx.synchronize()
+        assert rel_err(y32.cpu().numpy().astype(np.float64), ref32) <= FP32_TOL
+    return h, sub
+
+
+@pytest.mark.parametrize("n,T,wmax,count,k", [(10, 40, 6, 700, 1), (36, 60, 8, 3000, 1), (64, 50, 10, 2000, 3),
+                                              (70, 50, 8, 2000, 16), (130, 40, 8, 1500, 21), (200, 40, 6, 1200, 4),
+                                              (300, 30, 6, 800, 2)])
+def test_apply_random_extended_ops(ctx, n, T, wmax, count, k):
+    op = wl.random_extended(n, T, max_weight=wmax, seed=n + T, hermitian=True, real=True)
+    # subspace closed enough under the operator to give hits: random strings
+    # plus their images under random words
+    base = wl.random_subspace(n, count // 2, seed=n)
+    rng = np.random.default_rng(n)
+    ints = wl.words_to_ints(base)
+    extra = []
+    for v in ints[: count // 2]:
+        coef, word = list(op.terms())[int(rng.integers(0, op.n_terms))]
+        f = 0
+        for qb, c in word:
+            if c in (wl.X, wl.Y, wl.LOWER, wl.RAISE):
+                f |= 1 << qb
+        extra.append(v ^ f)
+    words = np.concatenate([base, wl.ints_to_words(extra, n)])
+    _check_apply(ctx, op, words, k, seed=n)
+
+
+def test_apply_tfim_full_space(ctx):
+    op = wl.tfim_chain(12, g=1.0)
+    _check_apply(ctx, op, wl.full_space(12), 1, seed=1)
+    _check_apply(ctx, op, wl.full_space(12), 16, seed=2)
+
+
+def test_apply_xxz_walk_subspace(ctx):
+    op = wl.xxz_square(6, 6)
+    words = wl.xxz_walk_subspace(6, 6, count=30_000, seed=2)
+    _check_apply(ctx, op, words, 1, seed=3)
+
+
+def test_apply_fermionic_ladder_groups(ctx):
+    n_orb = 4
+    h1, eri = wl.chem_integrals(n_orb, seed=5)
+    op = wl.jordan_wigner(wl.molecular_fermionic(h1, eri))
+    alpha = [v for v in range(1 << n_orb) if bin(v).count("1") == 2]
+    words = wl.product_subspace(alpha, alpha, n_orb)
+    h, sub = _check_apply(ctx, op, words, 1, seed=4)
+    info = h.info()
+    assert info["n_ladder_groups"] > 0 and info["is_hermitian"] == 1
+
+
+def test_apply_deterministic_and_host_path(ctx):
+    import torch
+    op = wl.xxz_square(4, 4)
+    words = wl.xxz_walk_subspace(4, 4, count=5000, seed=1)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(16, words)
+    x = np.random.default_rng(0).normal(size=sub.dim)
+    xt = to_cuda(ctx, x, torch.float64)
+    y1 = ctx.apply_H(h, sub, xt)
+    y2 = ctx.apply_H(h, sub, xt)
+    ctx.synchronize()
+    assert torch.equal(y1, y2)
+    yh = ctx.apply_H_host(h, sub, x)
+    assert np.array_equal(yh, y1.cpu().numpy())
+
+
+# --------------------------------------------------------- integer tables
+@pytest.mark.parametrize("n,seed", [(10, 1), (70, 2), (200, 3)])
+def test_target_and_term_tables_exact(ctx, n, seed):
+    op = wl.random_extended(n, 30, max_weight=5, seed=seed, hermitian=True, real=True)
+    base = wl.random_subspace(n, 300, seed=seed)
+    ints = wl.words_to_ints(base)
+    extra = []
+    for i, (coef, word) in enumerate(op.terms()):
+        f = sum(1 << qb for qb, c in word if c in (wl.X, wl.Y, wl.LOWER, wl.RAISE))
+        extra.append(ints[i % len(ints)] ^ f)
+    words = np.concatenate([base, wl.ints_to_words(extra, n)])
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(n, words)
+    assert np.array_equal(h.groups(), oracle.groups(op))
+    tt = ctx.target_table(h, sub)
+    st = ctx.term_table(h, sub)
+    ctx.synchronize()
+    assert np.array_equal(tt.cpu().numpy(), oracle.target_table(op, keys))
+    assert np.array_equal(st.cpu().numpy(), oracle.term_table(op, keys))
+
+
+def test_diagonal_matches_oracle(ctx):
+    op = wl.random_extended(50, 40, max_weight=6, seed=9, hermitian=True, real=True)
+    words = wl.random_subspace(50, 2000, seed=9)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(50, words)
+    d = ctx.diagonal(h, sub)
+    ctx.synchronize()
+    assert rel_err(d.cpu().numpy(), oracle.diagonal(op, keys).real) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ errors
+def test_operator_errors(ctx):
+    import paper_2603_18731_gb300 as q
+    with pytest.raises(q.QsdError) as e:
+        ctx.load_operator(wl.QubitOperator.from_terms(3, [(1.0, [(0, "X"), (0, "Z")])]))
+    assert e.value.status == "REPEATED_INDEX"
+    with pytest.raises(q.QsdError) as e:
+        ctx.load_operator(wl.QubitOperator.from_terms(3, [(1.0, [(3, "X")])]))
+    assert e.value.status == "QUBIT_RANGE"
+    cplx = ctx.load_operator(wl.QubitOperator.from_terms(3, [(1.0, [(0, "Y")])]))
+    assert cplx.info()["is_real"] == 0
+    sub = ctx.build_subspace(3, wl.full_space(3))
+    import torch
+    x = to_cuda(ctx, np.ones(8), torch.float64)
+    with pytest.raises(q.QsdError) as e:
+        ctx.apply_H(cplx, sub, x)
+    assert e.value.status == "COMPLEX_UNSUPPORTED"
+    nonherm = ctx.load_operator(wl.QubitOperator.from_terms(3, [(1.0, [(0, "+")])]))
+    assert nonherm.info()["is_hermitian"] == 0
+    with pytest.raises(q.QsdError) as e:
+        ctx.lanczos_ground_state(nonherm, sub)
+    assert e.value.status == "NOT_HERMITIAN"
+    other = ctx.build_subspace(4, wl.full_space(4))
+    with pytest.raises(q.QsdError) as e:
+        ctx.apply_H(nonherm, other, to_cuda(ctx, np.ones(16), torch.float64))
+    assert e.value.status == "INVALID_ARG"
+
+
+# ------------------------------------------------------------- eigensolver
+def test_lanczos_tfim_closed_form(ctx):
+    import paper_2603_18731_gb300 as q
+    op = wl.tfim_chain(12, g=1.0)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(12, wl.full_space(12))
+    e_ref = -2.0 / math.sin(math.pi / 24)
+    e, info = ctx.lanczos_ground_state(h, sub, max_steps=200, tol=1e-10)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref), (e, e_ref, info)
+    e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=200, tol=1e-10, precision=q.QSD_FP32_MIXED)
+    assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (e2, e_ref, info2)
+
+
+def test_lanczos_xxz_subspace_vs_oracle(ctx):
+    import paper_2603_18731_gb300 as q
+    op = wl.xxz_square(4, 4)
+    words = wl.xxz_walk_subspace(4, 4, count=2000, max_len=8, seed=5)
+    keys = oracle.sort_unique(words)
+    e_ref = oracle.ground_energy(op, keys)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(16, words)
+    e, info = ctx.lanczos_ground_state(h, sub, max_steps=300, tol=1e-10)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref), (e, e_ref, info)
+    e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=300, tol=1e-10, precision=q.QSD_FP32_MIXED)
+    assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (e2, e_ref, info2)
+
+
+def test_lanczos_hubbard_dimer_closed_form(ctx):
+    t, U = 1.0, 3.0
+    h1 = np.array([[0.0, -t], [-t, 0.0]])
+    eri = np.zeros((2, 2, 2, 2))
+    eri[0, 0, 0, 0] = eri[1, 1, 1, 1] = U
+    op = wl.jordan_wigner(wl.molecular_fermionic(h1, eri))
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(4, wl.product_subspace([1, 2], [1, 2], 2))
+    e, _ = ctx.lanczos_ground_state(h, sub, max_steps=10, tol=1e-12)
+    assert abs(e - (U - math.sqrt(U * U + 16 * t * t)) / 2) < 1e-11
