@@ -215,11 +215,14 @@ def run_gpu(args):
     value = world * elems * k1 / (t_max * 1e-3) / 1e9
     variants = {}
     vsteps = max(3, min(args.steps, 20))
-    for name, x, prec, k in (("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp64_k16", xb64, q.QSD_FP64, 16),
-                             ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16)):
+    for name, x, prec, k in (("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp32_dot2_k1", x32, q.QSD_FP32_DOT2, 1),
+                             ("fp64_k16", xb64, q.QSD_FP64, 16), ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16),
+                             ("fp32_dot2_k16", xb32, q.QSD_FP32_DOT2, 16)):
         m, _, _ = time_variant(x, prec, vsteps, 3)
         variants[name] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
-    variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / value * world if value else None
+    fp64_1 = elems / (ms64 * 1e-3) / 1e9
+    variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / fp64_1
+    variants["dot2_block_over_fp64"] = variants["fp32_dot2_k16"]["gelem_s"] / fp64_1
 
     # roofline of the product kernel (FP64, k = 1): algorithmic bytes
     s_x = 8
@@ -250,7 +253,7 @@ def run_gpu(args):
     # one full ground-state solve per precision (not part of the timed steps)
     solve = {}
     if not args.no_solve:
-        for name, prec in (("fp64", q.QSD_FP64), ("fp32_mixed", q.QSD_FP32_MIXED)):
+        for name, prec in (("fp64", q.QSD_FP64), ("fp32_mixed", q.QSD_FP32_MIXED), ("fp32_dot2", q.QSD_FP32_DOT2)):
             ctx.synchronize()
             t0 = time.perf_counter()
             e, inf = ctx.lanczos_ground_state(h, sub, check=False, precision=prec, max_steps=args.solve_steps,

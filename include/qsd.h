@@ -57,6 +57,12 @@ extern "C" {
 /* ------------------------------------------------------------- precision */
 #define QSD_FP64        0  /* x, y stored as double; FP64 accumulation */
 #define QSD_FP32_MIXED  1  /* x, y stored as float; each row accumulated in FP64 */
+#define QSD_FP32_DOT2   2  /* x, y stored as float; each row accumulated in FP32 with
+                              error-free transformations (TwoProduct, TwoSum: the
+                              "Dot2" scheme of Ogita, Rump and Oishi, 2005), as
+                              accurate as accumulating in twice the FP32 precision,
+                              with no FP64 arithmetic (GB300 issues FP64 at 1/64 of
+                              the FP32 rate) */
 
 typedef struct qsd_ctx_s *qsd_ctx;
 typedef struct qsd_op_s *qsd_op;
@@ -124,8 +130,8 @@ int qsd_free_op(qsd_op op);
  * when words_on_device == 0, else device memory), any order, duplicates
  * allowed (Methods, "Subspace data structure").  The strings are sorted by
  * integer value on the device, duplicates dropped, and an open-addressing
- * hash table (load factor <= 1/2, 4-slot buckets of (32-bit tag, 32-bit
- * index)) is built for lookups.  *dim_out receives D.  Synchronises.
+ * hash table (load factor <= 1/4, buckets of eight 16-bit tags with a 32-bit
+ * row index per slot) is built for lookups.  *dim_out receives D.  Synchronises.
  * Errors: QSD_ERR_CAPACITY when D would exceed 2^32 - 2. */
 int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,
                        const uint64_t *words, int words_on_device,
@@ -150,7 +156,8 @@ int qsd_free_sub(qsd_sub sub);
  * matrix-free product recomputes each element per call, in parallel over
  * row bit-strings; each row gathers from the columns its groups reach).
  * x and y are device arrays [D][k] row-major, of double (QSD_FP64) or float
- * (QSD_FP32_MIXED, where each row is accumulated in FP64 and rounded once).
+ * (QSD_FP32_MIXED: each row accumulated in FP64 and rounded once;
+ * QSD_FP32_DOT2: each row accumulated by the Dot2 scheme and rounded once).
  * x and y must not overlap.  Per row the diagonal is applied first, then the
  * groups in group order, and the terms of a group in term order, so results
  * are deterministic.  Asynchronous on the context stream.  The first product
@@ -185,9 +192,10 @@ int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
 
 /* ------------------------------------------------------------- eigensolver */
 typedef struct {
-    int32_t precision;     /* QSD_FP64, or QSD_FP32_MIXED: FP32 Krylov basis and
-                              products, FP64 dots and tridiagonal, then FP64
-                              refinement of the Ritz value */
+    int32_t precision;     /* QSD_FP64, or QSD_FP32_MIXED / QSD_FP32_DOT2: FP32
+                              Krylov basis and products (of that mode), FP64 dots
+                              and tridiagonal, then FP64 refinement of the Ritz
+                              value */
     int32_t max_steps;     /* Krylov dimension limit (>= 1) */
     double tol;            /* stop when |H u - theta u| / |theta| <= tol */
     double refine_tol;     /* mixed only: stop refining when the relative change

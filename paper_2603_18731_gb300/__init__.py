@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libqsd.so")
 QSD_OK = 0
 QSD_FP64 = 0
 QSD_FP32_MIXED = 1
+QSD_FP32_DOT2 = 2
 STATUS = {
     0: "OK", 1: "INVALID_ARG", 2: "QUBIT_RANGE", 3: "REPEATED_INDEX", 4: "NOT_HERMITIAN",
     5: "COMPLEX_UNSUPPORTED", 6: "OOM", 7: "NOT_CONVERGED", 8: "TIMEOUT", 9: "CUDA", 10: "CAPACITY",

@@ -127,17 +127,11 @@ void drop_bindings(qsd_ctx ctx, const void *handle) {
 }
 
 // ------------------------------------------------------------ product
-// Lanes per row: a lane per row once there are enough rows to fill the GPU
-// twice over; otherwise more lanes per row (never more than the groups).
+// Lanes per row: a lane per row once the rows fill the GPU; 8 lanes per row
+// for small subspaces with enough groups to share.
 static int choose_lanes(qsd_ctx ctx, int64_t D, int64_t G) {
-    const int64_t full = (int64_t)ctx->num_sms * 2048 * 2;
-    int R = 1;
-    if (D > 0 && D < full) {
-        const int64_t want = (full + D - 1) / D;
-        R = want >= 32 ? 32 : (want >= 4 ? 4 : 1);
-    }
-    while (R > 1 && R / 2 >= G) R = R == 32 ? 4 : 1;
-    return R;
+    const int64_t slots = (int64_t)ctx->num_sms * 2048;
+    return (D < slots / 2 && G >= 16) ? 8 : 1;
 }
 
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
@@ -145,12 +139,13 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     ApplyParams p{};
     p.keys = sub->keys.as<uint64_t>();
     p.D = sub->D;
-    p.slots = sub->slots.as<uint64_t>();
-    p.bmask = (uint64_t)sub->n_buckets - 1;
+    p.hv = hash_view(sub);
     p.nib = ctx->nib.as<uint64_t>();
     p.G = op->G;
+    p.grec = op->grec.as<GroupRec>();
+    p.amp = op->amp.as<double>();
+    p.ampf = op->ampf.as<float2>();
     p.gF = op->gF.as<uint64_t>();
-    p.ghash = op->ghash.as<uint64_t>();
     p.grange = op->grange.as<int32_t>();
     p.gL = op->gL.as<uint8_t>();
     p.gpos = op->gpos.as<uint64_t>();
@@ -171,8 +166,9 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
         p.col0 = c;
-        if (precision == QSD_FP64) launch_apply<double>(p, op->W, R, KB, stream);
-        else launch_apply<float>(p, op->W, R, KB, stream);
+        if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, op->W, R, KB, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, op->W, R, KB, stream);
+        else launch_apply<QSD_FP32_DOT2>(p, op->W, R, KB, stream);
         c += KB;
     }
 }
@@ -393,7 +389,7 @@ int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, c
     std::lock_guard<std::mutex> lk(ctx->mu);
     QSD_GUARD(ctx, {
         check_pair(ctx, op, sub);
-        if (k < 1 || (precision != QSD_FP64 && precision != QSD_FP32_MIXED))
+        if (k < 1 || precision < QSD_FP64 || precision > QSD_FP32_DOT2)
             fail(QSD_ERR_INVALID_ARG, "qsd_apply_H: bad k or precision");
         if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_apply_H: operator has complex matrix elements");
         if (sub->D == 0) return QSD_OK;
@@ -410,7 +406,7 @@ int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t
     std::lock_guard<std::mutex> lk(ctx->mu);
     QSD_GUARD(ctx, {
         check_pair(ctx, op, sub);
-        if (k < 1 || (precision != QSD_FP64 && precision != QSD_FP32_MIXED))
+        if (k < 1 || precision < QSD_FP64 || precision > QSD_FP32_DOT2)
             fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_host: bad k or precision");
         if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_apply_H_host: complex operator");
         if (sub->D == 0) return QSD_OK;
@@ -487,8 +483,8 @@ int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanc
     int rc = QSD_OK;
     try {
         check_pair(ctx, op, sub);
-        if (!p || !energy || p->max_steps < 1 || p->check_every < 1 ||
-            (p->precision != QSD_FP64 && p->precision != QSD_FP32_MIXED))
+        if (!p || !energy || p->max_steps < 1 || p->check_every < 1 || p->precision < QSD_FP64 ||
+            p->precision > QSD_FP32_DOT2)
             fail(QSD_ERR_INVALID_ARG, "qsd_lanczos_ground_state: bad arguments");
         if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_lanczos_ground_state: complex operator");
         if (!op->info.is_hermitian) fail(QSD_ERR_NOT_HERMITIAN, "qsd_lanczos_ground_state: operator is not Hermitian");

@@ -1,33 +1,55 @@
 // The matrix-free product y = H_S x (Methods, "Matrix evaluation").
 //
-// Gather form, one output row per R consecutive lanes (R = 1: a lane per
-// row with every group broadcast to the warp; R = 32: a warp per row with
-// the groups split over lanes and a shuffle reduction).  Per row and group:
-//   1. ladder groups: the row's bits at the group's flipped qubits form the
-//      ladder integer, whose int_ptrs entry is the only term range that can
-//      be nonzero; an empty range skips the group with no lookup (Fig. 3b);
-//      other groups scan their term range;
-//   2. each candidate term passes its projector test (r & P) == V and adds
-//      phi (-1)^popc(r & Z) to the group's matrix element;
-//   3. if any term passed, the column r xor F is looked up once for the
-//      whole group (property 3: the terms of a group share the column);
-//   4. the element times x[column] is accumulated in FP64.
-// Finally y[r] = d[r] x[r] + sum, rounded once to the storage type.
+// Gather form: R lanes own one output row (R = 1: a lane per row, every group
+// broadcast to the warp; R = 8: the groups of a row split over 8 lanes and
+// reduced by shuffles).  Per row and group:
+//   1. table groups (every term tests and signs only bits inside a support
+//      of <= 5 qubits, e.g. all spin models): the row's bits on the support
+//      index a precomputed table of the group's matrix element, which is
+//      exactly zero when no term survives -- the group is then skipped with
+//      no lookup (the paper's rejection of null terms before the subspace
+//      query);
+//      scan groups (fermionic terms with Jordan-Wigner strings): the ladder
+//      integer of the row selects the int_ptrs term range (Fig. 3b) and each
+//      term passes its projector test and adds phi (-1)^popc(r & Z);
+//   2. the column r xor F is looked up once for the whole group (property 3);
+//   3. the element times x[column] is accumulated.
+// Groups are processed U = 4 at a time: the four bucket loads are issued
+// before any is inspected, so each lane keeps four lookups in flight.
+//
+// Accumulation: QSD_FP64 and QSD_FP32_MIXED accumulate in FP64 (DFMA);
+// QSD_FP32_DOT2 accumulates FP32 products with error-free transformations
+// (TwoProduct by FMA and TwoSum, Ogita-Rump-Oishi "Dot2", SIAM J. Sci.
+// Comput. 2005): the sum is as accurate as one computed in twice the FP32
+// precision and rounded once, with no FP64 instruction in the loop.
 #pragma once
 
 #include "qsd_internal.cuh"
 
 namespace qsd {
 
+constexpr int kTableBitsMax = 5;
+constexpr uint32_t kGroupScan = 0x80u;
+
+// 32-byte group record, one per off-diagonal group
+struct __align__(16) GroupRec {
+    uint64_t hF;    // prehash of the flip mask F
+    uint64_t pos;   // table groups: support qubits, 12 bits each, ascending
+    uint32_t off;   // table groups: offset of the 2^nb amplitudes
+    uint32_t info;  // bits 0..2: nb; kGroupScan: scan group
+    uint64_t F0;    // word 0 of F
+};
+
 struct ApplyParams {
     const uint64_t *keys;   // [W][D]
     int64_t D;
-    const uint64_t *slots;
-    uint64_t bmask;
+    HashView hv;
     const uint64_t *nib;
     int64_t G;
+    const GroupRec *grec;    // [G]
+    const double *amp;       // table amplitudes
+    const float2 *ampf;      // the same split into FP32 (hi, lo)
     const uint64_t *gF;      // [W][G]
-    const uint64_t *ghash;   // [G]
     const int32_t *grange;   // [G+1]
     const uint8_t *gL;       // [G]
     const uint64_t *gpos;    // [G]
@@ -53,8 +75,71 @@ __device__ __forceinline__ uint64_t word_of(const uint64_t (&x)[W], int q) {
     return v;
 }
 
-template <int W, int R, int KB, typename TIO>
-__global__ void __launch_bounds__(256) k_apply(const ApplyParams p) {
+// Matrix element of a scan group at the row (0 when no term survives).
+template <int W>
+__device__ __noinline__ double scan_amp(const ApplyParams &p, int64_t g, const uint64_t (&key)[W]) {
+    int32_t b, e;
+    const int L = __ldg(p.gL + g);
+    if (L) {
+        const uint64_t pos = __ldg(p.gpos + g);
+        int l = 0;
+        for (int i = 0; i < L; ++i) {
+            const int q = (int)((pos >> (16 * i)) & 0xffff);
+            l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+        }
+        b = __ldg(p.gptr + g * 17 + l);
+        e = __ldg(p.gptr + g * 17 + l + 1);
+    } else {
+        b = __ldg(p.grange + g);
+        e = __ldg(p.grange + g + 1);
+    }
+    double amp = 0.0;
+    for (int32_t t = b; t < e; ++t) {
+        const uint8_t f = __ldg(p.tflag + t);
+        bool ok = true;
+        if (f & 1) {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                ok &= (key[w] & __ldg(p.tP + (size_t)w * p.T + t)) == __ldg(p.tV + (size_t)w * p.T + t);
+        }
+        if (!ok) continue;
+        double ph = __ldg(p.tphi + t);
+        if (f & 2) {
+            int par = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(p.tZ + (size_t)w * p.T + t));
+            if (par & 1) ph = -ph;
+        }
+        amp += ph;
+    }
+    return amp;
+}
+
+// Error-free accumulation of hi*x + lo*x into (s, e).
+__device__ __forceinline__ void dot2_add(float &s, float &e, float hi, float lo, float xv) {
+    const float p = hi * xv;
+    float pe = fmaf(hi, xv, -p);
+    pe = fmaf(lo, xv, pe);
+    const float t = s + p;
+    const float bp = t - s;
+    const float te = (s - (t - bp)) + (p - bp);
+    s = t;
+    e += te + pe;
+}
+
+// Merge (s2, e2) into (s, e) (shuffle reduction of the DOT2 accumulators).
+__device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e2) {
+    const float t = s + s2;
+    const float bp = t - s;
+    const float te = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    e += te + e2;
+}
+
+template <int W, int R, int KB, int PREC>
+__global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParams p) {
+    using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
+    constexpr int U = 4;
     const int sub = threadIdx.x % R;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R;
     const bool active = row < p.D;
@@ -64,75 +149,126 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams p) {
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + r);
     const uint64_t hr = prehash<W>(key, p.nib);
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
+    // accumulators: FP64 (modes 0, 1) or FP32 (s, e) pairs (DOT2)
     double acc[KB];
+    float as[KB], ae[KB];
 #pragma unroll
-    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
-    if (active) {
-        for (int64_t g = sub; g < p.G; g += R) {
-            int32_t b, e;
-            const int L = __ldg(p.gL + g);
-            if (L) {
-                const uint64_t pos = __ldg(p.gpos + g);
-                int l = 0;
-                for (int i = 0; i < L; ++i) {
-                    const int q = (int)((pos >> (16 * i)) & 0xffff);
-                    l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+    for (int j = 0; j < KB; ++j) { acc[j] = 0.0; as[j] = 0.f; ae[j] = 0.f; }
+
+    for (int64_t g0 = (int64_t)sub * U; g0 < p.G; g0 += (int64_t)R * U) {
+        // phase 1: element of each of U groups, and its bucket load in flight
+        double a[U];
+        float ah[U], al[U];
+        uint4 tb[U];
+        uint64_t bidx[U];
+        uint32_t tag[U];
+        bool need[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = g0 + u;
+            bool nz = false;
+            a[u] = 0.0;
+            ah[u] = al[u] = 0.f;
+            uint64_t hF = 0;
+            if (g < p.G) {
+                const ulonglong2 *rp = reinterpret_cast<const ulonglong2 *>(p.grec + g);
+                const ulonglong2 r0 = __ldg(rp);
+                const uint64_t r1x = __ldg(reinterpret_cast<const unsigned long long *>(rp + 1));
+                hF = r0.x;
+                const uint32_t off = (uint32_t)r1x, info = (uint32_t)(r1x >> 32);
+                if (!(info & kGroupScan)) {
+                    // nb is uniform across the warp (lane per row): a real loop
+                    const int nb = (int)(info & 7u);
+                    int l = 0;
+                    for (int i = 0; i < nb; ++i) {
+                        const int q = (int)((r0.y >> (12 * i)) & 0xfff);
+                        l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+                    }
+                    if (PREC == QSD_FP32_DOT2) {
+                        const float2 f = __ldg(p.ampf + off + l);
+                        ah[u] = f.x;
+                        al[u] = f.y;
+                        nz = (__float_as_uint(f.x) << 1) != 0u;
+                    } else {
+                        a[u] = __ldg(p.amp + off + l);
+                        nz = ((uint64_t)__double_as_longlong(a[u]) << 1) != 0ull;
+                    }
+                } else if (active) {
+                    a[u] = scan_amp<W>(p, g, key);
+                    nz = ((uint64_t)__double_as_longlong(a[u]) << 1) != 0ull;
+                    if (PREC == QSD_FP32_DOT2) {
+                        ah[u] = (float)a[u];
+                        al[u] = (float)(a[u] - (double)ah[u]);
+                    }
                 }
-                b = __ldg(p.gptr + g * 17 + l);
-                e = __ldg(p.gptr + g * 17 + l + 1);
-            } else {
-                b = __ldg(p.grange + g);
-                e = __ldg(p.grange + g + 1);
             }
-            if (b >= e) continue;
-            double amp = 0.0;
-            bool any = false;
-            for (int32_t t = b; t < e; ++t) {
-                const uint8_t f = __ldg(p.tflag + t);
-                bool ok = true;
-                if (f & 1) {
-#pragma unroll
-                    for (int w = 0; w < W; ++w)
-                        ok &= (key[w] & __ldg(p.tP + (size_t)w * p.T + t)) == __ldg(p.tV + (size_t)w * p.T + t);
-                }
-                if (!ok) continue;
-                any = true;
-                double ph = __ldg(p.tphi + t);
-                if (f & 2) {
-                    int par = 0;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(p.tZ + (size_t)w * p.T + t));
-                    if (par & 1) ph = -ph;
-                }
-                amp += ph;
+            need[u] = active && nz;
+            if (need[u]) {
+                bidx[u] = hash_bucket(hr ^ hF, p.hv.shift, tag[u]);
+                tb[u] = load_tags(p.hv.tags, bidx[u]);
             }
-            if (!any) continue;
+        }
+        // phase 2: resolve the lookups and accumulate
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!need[u]) continue;
+            const int64_t g = g0 + u;
+            const bool full = bucket_full(tb[u]);
+            if (!tag_any(tb[u], tag[u]) && !full) continue;  // absent: the common case
+            const uint32_t match = tag_match(tb[u], tag[u]);
+            const GroupRec *rp = p.grec + g;
             uint64_t c[W];
+            c[0] = key[0] ^ __ldg(&rp->F0);
 #pragma unroll
-            for (int w = 0; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
-            const int64_t idx = probe<W>(c, hr ^ __ldg(p.ghash + g), p.slots, p.keys, p.D, p.bmask, p.err);
+            for (int w = 1; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
+            int64_t idx = verify_matches<W>(p.hv, bidx[u], match, c);
+            if (idx < 0 && full) idx = probe_from<W>(p.hv, bidx[u], tag[u], c, p.err);
             if (idx < 0) continue;
             const TIO *xc = x + idx * p.ld + p.col0;
+            if (PREC == QSD_FP32_DOT2) {
 #pragma unroll
-            for (int j = 0; j < KB; ++j) acc[j] = fma(amp, (double)__ldg(xc + j), acc[j]);
+                for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], ah[u], al[u], (float)__ldg(xc + j));
+            } else {
+#pragma unroll
+                for (int j = 0; j < KB; ++j) acc[j] = fma(a[u], (double)__ldg(xc + j), acc[j]);
+            }
         }
     }
     if (R > 1) {
 #pragma unroll
-        for (int j = 0; j < KB; ++j)
+        for (int j = 0; j < KB; ++j) {
 #pragma unroll
-            for (int o = R / 2; o >= 1; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+            for (int o = R / 2; o >= 1; o >>= 1) {
+                if (PREC == QSD_FP32_DOT2) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, as[j], o);
+                    const float e2 = __shfl_xor_sync(0xffffffffu, ae[j], o);
+                    dot2_merge(as[j], ae[j], s2, e2);
+                } else {
+                    acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+                }
+            }
+        }
     }
     if (active && sub == 0) {
         const double d = __ldg(p.diag + row);
         const TIO *xr = x + row * p.ld + p.col0;
         TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0;
+        if (PREC == QSD_FP32_DOT2) {
+            const float dh = (float)d, dl = (float)(d - (double)dh);
 #pragma unroll
-        for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
+            for (int j = 0; j < KB; ++j) {
+                dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
+                yr[j] = (TIO)(as[j] + ae[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
+        }
     }
 }
 
-// Run-time W (W > kMaxWordsStatic): a lane per row, keys in local memory.
+// Run-time W (W > kMaxWordsStatic): a lane per row, keys in local memory,
+// every group evaluated term by term, FP64 accumulation in all modes.
 template <int KB, typename TIO>
 __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,7 +311,7 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
         }
         if (!any) continue;
         for (int w = 0; w < W; ++w) c[w] = key[w] ^ p.gF[(size_t)w * p.G + g];
-        const int64_t idx = probe_dyn(c, W, hr ^ p.ghash[g], p.slots, p.keys, p.D, p.bmask, p.err);
+        const int64_t idx = probe_dyn(c, W, hr ^ p.grec[g].hF, p.hv, p.err);
         if (idx < 0) continue;
         const TIO *xc = x + idx * p.ld + p.col0;
 #pragma unroll
@@ -188,8 +324,8 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
     for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)xr[j], acc[j]);
 }
 
-// Launch one (W, R, KB) variant for storage type TIO.
-template <typename TIO>
+// Launch one (W, R, KB) variant of precision mode PREC.
+template <int PREC>
 void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
 
 }  // namespace qsd

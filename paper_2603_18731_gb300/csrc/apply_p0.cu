@@ -1,4 +1,4 @@
-// Instantiations of the product kernel for double storage.
+// Instantiations of the product kernel for precision mode 0.
 #include "apply_kernel.cuh"
 
 namespace qsd {
@@ -7,25 +7,22 @@ namespace {
 template <int W, int R>
 void launch_kb(const ApplyParams &p, int KB, int64_t blocks, cudaStream_t s) {
     switch (KB) {
-    case 16: k_apply<W, R, 16, double><<<(unsigned)blocks, 256, 0, s>>>(p); break;
-    case 4: k_apply<W, R, 4, double><<<(unsigned)blocks, 256, 0, s>>>(p); break;
-    default: k_apply<W, R, 1, double><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    case 16: k_apply<W, R, 16, 0><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    case 4: k_apply<W, R, 4, 0><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    default: k_apply<W, R, 1, 0><<<(unsigned)blocks, 256, 0, s>>>(p); break;
     }
 }
 
 template <int W>
 void launch_r(const ApplyParams &p, int R, int KB, cudaStream_t s) {
     const int64_t blocks = (p.D * R + 255) / 256;
-    switch (R) {
-    case 32: launch_kb<W, 32>(p, KB, blocks, s); break;
-    case 4: launch_kb<W, 4>(p, KB, blocks, s); break;
-    default: launch_kb<W, 1>(p, KB, blocks, s); break;
-    }
+    if (R == 8) launch_kb<W, 8>(p, KB, blocks, s);
+    else launch_kb<W, 1>(p, KB, blocks, s);
 }
 }  // namespace
 
 template <>
-void launch_apply<double>(const ApplyParams &p, int W, int R, int KB, cudaStream_t s) {
+void launch_apply<0>(const ApplyParams &p, int W, int R, int KB, cudaStream_t s) {
     if (p.D <= 0) return;
     switch (W) {
     case 1: launch_r<1>(p, R, KB, s); break;

@@ -1,0 +1,44 @@
+// Instantiations of the product kernel for precision mode 2.
+#include "apply_kernel.cuh"
+
+namespace qsd {
+
+namespace {
+template <int W, int R>
+void launch_kb(const ApplyParams &p, int KB, int64_t blocks, cudaStream_t s) {
+    switch (KB) {
+    case 16: k_apply<W, R, 16, 2><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    case 4: k_apply<W, R, 4, 2><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    default: k_apply<W, R, 1, 2><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    }
+}
+
+template <int W>
+void launch_r(const ApplyParams &p, int R, int KB, cudaStream_t s) {
+    const int64_t blocks = (p.D * R + 255) / 256;
+    if (R == 8) launch_kb<W, 8>(p, KB, blocks, s);
+    else launch_kb<W, 1>(p, KB, blocks, s);
+}
+}  // namespace
+
+template <>
+void launch_apply<2>(const ApplyParams &p, int W, int R, int KB, cudaStream_t s) {
+    if (p.D <= 0) return;
+    switch (W) {
+    case 1: launch_r<1>(p, R, KB, s); break;
+    case 2: launch_r<2>(p, R, KB, s); break;
+    case 3: launch_r<3>(p, R, KB, s); break;
+    case 4: launch_r<4>(p, R, KB, s); break;
+    default: {
+        const int64_t blocks = (p.D + 255) / 256;
+        switch (KB) {
+        case 16: k_apply_dyn<16, float><<<(unsigned)blocks, 256, 0, s>>>(p, W); break;
+        case 4: k_apply_dyn<4, float><<<(unsigned)blocks, 256, 0, s>>>(p, W); break;
+        default: k_apply_dyn<1, float><<<(unsigned)blocks, 256, 0, s>>>(p, W); break;
+        }
+    }
+    }
+    QSD_LAUNCH_CHECK();
+}
+
+}  // namespace qsd

@@ -308,11 +308,12 @@ struct LanczosResult {
 template <typename TV>
 LanczosResult run_lanczos(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, Krylov &K, const double *start,
                           uint64_t seed, int max_steps, double tol, int check_every, double *u,
-                          std::chrono::steady_clock::time_point deadline, bool has_deadline, int *applies) {
+                          std::chrono::steady_clock::time_point deadline, bool has_deadline, int *applies,
+                          int prec32 = QSD_FP32_DOT2) {
     cudaStream_t s = ctx->stream;
     const int64_t D = K.D;
     const int m = std::min<int64_t>(max_steps, D);
-    const int prec = std::is_same<TV, float>::value ? QSD_FP32_MIXED : QSD_FP64;
+    const int prec = std::is_same<TV, float>::value ? prec32 : QSD_FP64;
     TV *V = K.V.as<TV>();
     TV *hv = K.hv.as<TV>();
     double *w = K.w.as<double>(), *h = K.h.as<double>(), *part = K.partial.as<double>();
@@ -438,7 +439,7 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
     Binding *bind = get_binding(ctx, op, sub);
     const double *diag = bind->diag.as<double>();
     const int64_t D = sub->D;
-    const bool mixed = p.precision == QSD_FP32_MIXED;
+    const bool mixed = p.precision != QSD_FP64;
     // the tridiagonal CTA keeps 8 m doubles in shared memory (<= 48 KB)
     const int m = (int)std::min<int64_t>(std::min(p.max_steps, kMaxSteps), D);
     const double tol = p.tol > 0 ? p.tol : 1e-9;
@@ -454,7 +455,7 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
         const double phase_tol = mixed ? std::max(tol, 1e-5) : tol;
         if (mixed)
             res = run_lanczos<float>(ctx, op, sub, diag, K, p.v0, p.seed, m, phase_tol, p.check_every, u.as<double>(),
-                                     deadline, has_deadline, &applies);
+                                     deadline, has_deadline, &applies, p.precision);
         else
             res = run_lanczos<double>(ctx, op, sub, diag, K, p.v0, p.seed, m, phase_tol, p.check_every,
                                       u.as<double>(), deadline, has_deadline, &applies);

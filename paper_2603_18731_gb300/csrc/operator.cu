@@ -17,6 +17,7 @@
 #include <cmath>
 #include <complex>
 
+#include "apply_kernel.cuh"
 #include "qsd_internal.cuh"
 
 namespace qsd {
@@ -134,6 +135,80 @@ __global__ void k_group_tables(int W, int64_t G, const int32_t *__restrict__ gra
         }
         gptr[g * kLadderPtrs + l] = t;
     }
+}
+
+// Support of a group: every qubit any of its terms tests (projector and
+// ladder letters) or signs (Z, Y, Jordan-Wigner strings).  The flipped qubits
+// of pure X letters do not change the element and stay outside.  Groups with
+// a support of <= kTableBitsMax qubits get an amplitude table (a group of
+// X letters only has an empty support: one constant element).
+__global__ void k_group_support(int W, int64_t G, const int32_t *__restrict__ grange, const uint64_t *__restrict__ gF,
+                                int64_t T, const uint64_t *__restrict__ tP, const uint64_t *__restrict__ tZ,
+                                uint32_t *size, uint64_t *spos) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    int nb = 0;
+    uint64_t pos = 0;
+    for (int w = 0; w < W && nb <= kTableBitsMax; ++w) {
+        uint64_t u = 0;
+        for (int32_t t = grange[g]; t < grange[g + 1]; ++t) u |= tP[(size_t)w * T + t] | tZ[(size_t)w * T + t];
+        while (u) {
+            const int bit = __ffsll((long long)u) - 1;
+            if (nb < kTableBitsMax) pos |= (uint64_t)(64 * w + bit) << (12 * nb);
+            ++nb;
+            u &= u - 1;
+        }
+    }
+    size[g] = nb <= kTableBitsMax ? (1u << nb) : 0u;
+    spos[g] = nb <= kTableBitsMax ? pos | ((uint64_t)nb << 60) : 0;
+}
+
+// Amplitude tables and the 32-byte group records.
+__global__ void k_group_records(int W, int64_t G, const int32_t *__restrict__ grange, const uint64_t *__restrict__ gF,
+                                const uint64_t *__restrict__ ghash, int64_t T, const uint64_t *__restrict__ tP,
+                                const uint64_t *__restrict__ tV, const uint64_t *__restrict__ tZ,
+                                const double *__restrict__ tphi, const uint32_t *__restrict__ size,
+                                const uint32_t *__restrict__ off, const uint64_t *__restrict__ spos, double *amp,
+                                float2 *ampf, GroupRec *rec) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    GroupRec R;
+    R.hF = ghash[g];
+    R.F0 = gF[g];
+    if (size[g] == 0) {
+        R.pos = 0;
+        R.off = 0;
+        R.info = kGroupScan;
+        rec[g] = R;
+        return;
+    }
+    const int nb = (int)(spos[g] >> 60);
+    const uint64_t pos = spos[g] & ((1ull << 60) - 1);
+    R.pos = pos;
+    R.off = off[g];
+    R.info = (uint32_t)nb;
+    uint64_t rs[kMaxWordsDyn];
+    for (uint32_t l = 0; l < size[g]; ++l) {
+        for (int w = 0; w < W; ++w) rs[w] = 0;
+        for (int i = 0; i < nb; ++i) {
+            const int q = (int)((pos >> (12 * i)) & 0xfff);
+            if ((l >> i) & 1u) rs[q >> 6] |= 1ull << (q & 63);
+        }
+        double a = 0.0;
+        for (int32_t t = grange[g]; t < grange[g + 1]; ++t) {
+            bool ok = true;
+            int par = 0;
+            for (int w = 0; w < W; ++w) {
+                ok &= (rs[w] & tP[(size_t)w * T + t]) == tV[(size_t)w * T + t];
+                par ^= __popcll(rs[w] & tZ[(size_t)w * T + t]);
+            }
+            if (ok) a += (par & 1) ? -tphi[t] : tphi[t];
+        }
+        amp[R.off + l] = a;
+        const float hi = (float)a;
+        ampf[R.off + l] = make_float2(hi, (float)(a - (double)hi));
+    }
+    rec[g] = R;
 }
 
 __global__ void k_term_flags(int W, int64_t T, const uint64_t *__restrict__ tP, const uint64_t *__restrict__ tZ,
@@ -268,8 +343,8 @@ __global__ void k_term_table(const uint64_t *__restrict__ keys, int W, int64_t D
 
 // One thread per (row, group), with the same skip rule as the product.
 template <int W>
-__global__ void k_target_table(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ slots,
-                               uint64_t bmask, const uint64_t *__restrict__ nib, int64_t G,
+__global__ void k_target_table(const uint64_t *__restrict__ keys, int64_t D, const HashView hv,
+                               const uint64_t *__restrict__ nib, int64_t G,
                                const uint64_t *__restrict__ gF, const uint64_t *__restrict__ ghash,
                                const int32_t *__restrict__ grange, const uint8_t *__restrict__ gL,
                                const uint64_t *__restrict__ gpos, const int32_t *__restrict__ gptr, int64_t T,
@@ -311,11 +386,10 @@ __global__ void k_target_table(const uint64_t *__restrict__ keys, int64_t D, con
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = x[w] ^ gF[(size_t)w * G + g];
     uint64_t hr = prehash<W>(x, nib);
-    out[idx] = probe<W>(c, hr ^ ghash[g], slots, keys, D, bmask, err);
+    out[idx] = probe<W>(c, hr ^ ghash[g], hv, err);
 }
 
-__global__ void k_target_table_dyn(const uint64_t *__restrict__ keys, int W, int64_t D,
-                                   const uint64_t *__restrict__ slots, uint64_t bmask,
+__global__ void k_target_table_dyn(const uint64_t *__restrict__ keys, int W, int64_t D, const HashView hv,
                                    const uint64_t *__restrict__ nib, int64_t G, const uint64_t *__restrict__ gF,
                                    const uint64_t *__restrict__ ghash, const int32_t *__restrict__ grange,
                                    int64_t T, const uint64_t *__restrict__ tP, const uint64_t *__restrict__ tV,
@@ -333,7 +407,7 @@ __global__ void k_target_table_dyn(const uint64_t *__restrict__ keys, int W, int
     }
     if (!any) { out[idx] = -2; return; }
     for (int w = 0; w < W; ++w) c[w] = x[w] ^ gF[(size_t)w * G + g];
-    out[idx] = probe_dyn(c, W, prehash_dyn(x, W, nib) ^ ghash[g], slots, keys, D, bmask, err);
+    out[idx] = probe_dyn(c, W, prehash_dyn(x, W, nib) ^ ghash[g], hv, err);
 }
 
 struct HostWord {
@@ -551,6 +625,29 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
             stats.as<unsigned long long>() + 1);
         QSD_LAUNCH_CHECK();
         QSD_CUDA(cudaMemcpyAsync(h_stats, stats.p, 16, cudaMemcpyDeviceToHost, s));
+        // amplitude tables for small-support groups, and the group records
+        {
+            DevBuf size((size_t)G * 4), off((size_t)G * 4), spos((size_t)G * 8);
+            k_group_support<<<blocks_for(G, 128), 128, 0, s>>>(W, G, op->grange.as<int32_t>(), op->gF.as<uint64_t>(),
+                                                               T, op->tP.as<uint64_t>(), op->tZ.as<uint64_t>(),
+                                                               size.as<uint32_t>(), spos.as<uint64_t>());
+            QSD_LAUNCH_CHECK();
+            op->n_amp = (int64_t)exclusive_scan_u32(ctx, size.as<uint32_t>(), off.as<uint32_t>(), G, true);
+            op->amp.alloc((size_t)std::max<int64_t>(op->n_amp, 1) * 8);
+            op->ampf.alloc((size_t)std::max<int64_t>(op->n_amp, 1) * 8);
+            op->grec.alloc((size_t)G * sizeof(GroupRec));
+            k_group_records<<<blocks_for(G, 128), 128, 0, s>>>(
+                W, G, op->grange.as<int32_t>(), op->gF.as<uint64_t>(), op->ghash.as<uint64_t>(), T,
+                op->tP.as<uint64_t>(), op->tV.as<uint64_t>(), op->tZ.as<uint64_t>(), op->tphi.as<double>(),
+                size.as<uint32_t>(), off.as<uint32_t>(), spos.as<uint64_t>(), op->amp.as<double>(),
+                op->ampf.as<float2>(), op->grec.as<GroupRec>());
+            QSD_LAUNCH_CHECK();
+            std::vector<uint32_t> hsz(G);
+            QSD_CUDA(cudaMemcpyAsync(hsz.data(), size.p, (size_t)G * 4, cudaMemcpyDeviceToHost, s));
+            QSD_CUDA(cudaStreamSynchronize(s));
+            op->n_table_groups = 0;
+            for (auto v : hsz) op->n_table_groups += v > 0;
+        }
         op->host_groups.resize((size_t)G * W);
         std::vector<uint64_t> gsoa((size_t)G * W);
         QSD_CUDA(cudaMemcpyAsync(gsoa.data(), op->gF.p, (size_t)G * W * 8, cudaMemcpyDeviceToHost, s));
@@ -596,10 +693,10 @@ void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nro
     cudaStream_t s = ctx->stream;
     const int64_t total = nrows * G;
     const int nb = blocks_for(total, 256);
-    const uint64_t bm = (uint64_t)sub->n_buckets - 1;
-    const uint64_t *keys = sub->keys.as<uint64_t>(), *sl = sub->slots.as<uint64_t>(), *nib = ctx->nib.as<uint64_t>();
+    const HashView hv = hash_view(sub);
+    const uint64_t *keys = sub->keys.as<uint64_t>(), *nib = ctx->nib.as<uint64_t>();
 #define QSD_TT(WW)                                                                                             \
-    k_target_table<WW><<<nb, 256, 0, s>>>(keys, sub->D, sl, bm, nib, G, op->gF.as<uint64_t>(),                 \
+    k_target_table<WW><<<nb, 256, 0, s>>>(keys, sub->D, hv, nib, G, op->gF.as<uint64_t>(),                 \
                                           op->ghash.as<uint64_t>(), op->grange.as<int32_t>(), op->gL.as<uint8_t>(), \
                                           op->gpos.as<uint64_t>(), op->gptr.as<int32_t>(), op->T,              \
                                           op->tP.as<uint64_t>(), op->tV.as<uint64_t>(), row0, nrows, out, ctx->d_err)
@@ -609,7 +706,7 @@ void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nro
     case 3: QSD_TT(3); break;
     case 4: QSD_TT(4); break;
     default:
-        k_target_table_dyn<<<nb, 256, 0, s>>>(keys, op->W, sub->D, sl, bm, nib, G, op->gF.as<uint64_t>(),
+        k_target_table_dyn<<<nb, 256, 0, s>>>(keys, op->W, sub->D, hv, nib, G, op->gF.as<uint64_t>(),
                                               op->ghash.as<uint64_t>(), op->grange.as<int32_t>(), op->T,
                                               op->tP.as<uint64_t>(), op->tV.as<uint64_t>(), row0, nrows, out,
                                               ctx->d_err);

@@ -4,8 +4,8 @@
 // by the handles):
 //   subspace  keys   uint64 [W][D]   SoA, sorted ascending (word W-1 most
 //                                    significant); row index = rank
-//             slots  uint64 [cap]    4-slot buckets, slot = tag<<32 | index,
-//                                    empty = all ones; load factor <= 1/2
+//             tags   uint16 [cap]    8-slot buckets (16 bytes), 0 = empty
+//             sidx   uint32 [cap]    row index per slot; load factor <= 1/4
 //   operator  off-diagonal terms grouped by flip mask F (Methods, properties
 //             1-3): per group F[W][G], hash of F, term range, ladder table;
 //             per term P/V/Z masks [W][T] and the real phase phi[T]
@@ -94,9 +94,11 @@ struct qsd_sub_s {
     int32_t n_qubits = 0;
     int W = 1;
     int64_t D = 0;
-    int64_t n_buckets = 0;  // power of two; capacity = 4 * n_buckets slots
+    int64_t n_buckets = 0;  // power of two >= 2; capacity = 8 * n_buckets slots
+    int bucket_shift = 63;  // 64 - log2(n_buckets)
     qsd::DevBuf keys;   // uint64 [W][D]
-    qsd::DevBuf slots;  // uint64 [4 * n_buckets]
+    qsd::DevBuf tags;   // uint16 [8 * n_buckets], 0 = empty
+    qsd::DevBuf sidx;   // uint32 [8 * n_buckets]
 };
 
 struct qsd_op_s {
@@ -113,6 +115,10 @@ struct qsd_op_s {
     qsd::DevBuf gL;      // uint8  [G]  ladder bits with a table (0: scan the group)
     qsd::DevBuf gpos;    // uint64 [G]  4 x 16-bit flipped-qubit positions, ascending
     qsd::DevBuf gptr;    // int32  [G][17] ladder-integer term offsets (absolute)
+    qsd::DevBuf grec;    // GroupRec [G] (32 bytes): what the product reads per group
+    qsd::DevBuf amp;     // double [n_amp] matrix element per support pattern (table groups)
+    qsd::DevBuf ampf;    // float2 [n_amp] the same split into FP32 (hi, lo)
+    int64_t n_amp = 0, n_table_groups = 0;
     qsd::DevBuf tP, tV, tZ;  // uint64 [W][T]
     qsd::DevBuf tphi;    // double [T] real phase * coefficient
     qsd::DevBuf tphi_im; // double [T]
@@ -139,17 +145,31 @@ struct Binding {
 // L_1(x_1) xor ... where L_w is a random linear map of word w given by 16
 // nibble tables of 16 entries (one 128-byte line each).  Linearity gives
 // h(r xor F) = h(r) xor h(F): a row's prehash is computed once and each
-// group costs one xor.  (2) The SplitMix64 finaliser (Steele, Lea & Flood,
-// OOPSLA 2014) mixes h into the bucket (low bits) and the 32-bit tag (high
-// bits).  Collisions of h only cost probes; every hit is verified against
-// the full key.
-constexpr uint64_t kEmptySlot = ~0ull;
-constexpr int kBucketSlots = 4;
+// group costs one xor.  (2) One multiplicative step (multiply-shift hashing,
+// Dietzfelbinger et al. 1997, with the golden-ratio multiplier of Fibonacci
+// hashing) gives the bucket (top bits of the product) and a 16-bit tag (bits
+// 16..31, never 0).
+//
+// Table layout: buckets of 8 slots.  tags: uint16 [8 * n_buckets], 0 = empty,
+// one 16-byte load per bucket; sidx: uint32 [8 * n_buckets], the row index of
+// each occupied slot, read only when its tag matches.  Slots of a bucket fill
+// in order, so a bucket whose last slot is empty ends the probe.  Tag
+// collisions only cost a key comparison: every hit is verified against the
+// full key.
+constexpr int kBucketSlots = 8;
 
 __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+// bucket in [0, 2^(64 - shift)); tag in [1, 65535]
+__host__ __device__ __forceinline__ uint64_t hash_bucket(uint64_t h, int shift, uint32_t &tag) {
+    const uint64_t m = (h ^ (h >> 32)) * 0x9E3779B97F4A7C15ull;
+    const uint32_t t = (uint32_t)(m >> 16) & 0xffffu;
+    tag = t ? t : 1u;
+    return m >> shift;
 }
 
 // nib: tables for words 1..W-1, [(w-1)][16 nibble positions][16 values]
@@ -181,60 +201,97 @@ uint64_t host_prehash(const uint64_t *x, int W);
 const std::vector<uint64_t> &host_nibble_tables(int W);
 void ensure_nibble_tables(qsd_ctx ctx, int W);
 
-// Lookup of column key c (W words, prehash hc) in the subspace; returns the
-// row index or -1.  Probing ends at the first bucket with an empty slot; at
-// most n_buckets buckets are visited (a full table yields -1 and sets *err).
+// The 8 tags of bucket b.
+__device__ __forceinline__ uint4 load_tags(const uint16_t *__restrict__ tags, uint64_t b) {
+    return __ldg(reinterpret_cast<const uint4 *>(tags + b * kBucketSlots));
+}
+
+// Bit i set when tag i of the bucket equals `tag`.
+__device__ __forceinline__ uint32_t tag_match(const uint4 t, uint32_t tag) {
+    const uint32_t tt = tag | (tag << 16);
+    const uint32_t m0 = __vcmpeq2(t.x, tt), m1 = __vcmpeq2(t.y, tt);
+    const uint32_t m2 = __vcmpeq2(t.z, tt), m3 = __vcmpeq2(t.w, tt);
+    return (m0 & 1u) | ((m0 >> 15) & 2u) | ((m1 & 1u) << 2) | ((m1 >> 13) & 8u) | ((m2 & 1u) << 4) |
+           ((m2 >> 11) & 32u) | ((m3 & 1u) << 6) | ((m3 >> 9) & 128u);
+}
+
+// Some tag of the bucket equals `tag`.
+__device__ __forceinline__ bool tag_any(const uint4 t, uint32_t tag) {
+    const uint32_t tt = tag | (tag << 16);
+    return (__vcmpeq2(t.x, tt) | __vcmpeq2(t.y, tt) | __vcmpeq2(t.z, tt) | __vcmpeq2(t.w, tt)) != 0u;
+}
+
+// The bucket's last slot is occupied: the probe continues in the next bucket.
+__device__ __forceinline__ bool bucket_full(const uint4 t) { return (t.w >> 16) != 0u; }
+
+struct HashView {
+    const uint16_t *tags;
+    const uint32_t *sidx;
+    const uint64_t *keys;  // [W][D]
+    int64_t D;
+    uint64_t bmask;
+    int shift;
+};
+
+// Index of the verified key among the matching slots of bucket b, or -1.
 template <int W>
-__device__ __forceinline__ int64_t probe(const uint64_t (&c)[W], uint64_t hc,
-                                         const uint64_t *__restrict__ slots,
-                                         const uint64_t *__restrict__ keys, int64_t D,
-                                         uint64_t bucket_mask, uint32_t *err) {
-    const uint64_t m = fmix64(hc);
-    const uint32_t tag = (uint32_t)(m >> 32);
-    uint64_t b = m & bucket_mask;
-    for (uint64_t step = 0; step <= bucket_mask; ++step) {
-        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(slots + b * kBucketSlots);
-        const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1);
-        const uint64_t s[4] = {s01.x, s01.y, s23.x, s23.y};
+__device__ __forceinline__ int64_t verify_matches(const HashView &hv, uint64_t b, uint32_t match,
+                                                  const uint64_t (&c)[W]) {
+    while (match) {
+        const int i = __ffs(match) - 1;
+        match &= match - 1;
+        const uint64_t cand = __ldg(hv.sidx + b * kBucketSlots + i);
+        bool eq = true;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (s[i] == kEmptySlot) return -1;
-            if ((uint32_t)(s[i] >> 32) == tag) {
-                const uint64_t idx = (uint32_t)s[i];
-                bool eq = true;
-#pragma unroll
-                for (int w = 0; w < W; ++w) eq &= (__ldg(keys + (size_t)w * D + idx) == c[w]);
-                if (eq) return (int64_t)idx;
-            }
-        }
-        b = (b + 1) & bucket_mask;
+        for (int w = 0; w < W; ++w) eq &= (__ldg(hv.keys + (size_t)w * hv.D + cand) == c[w]);
+        if (eq) return (int64_t)cand;
+    }
+    return -1;
+}
+
+// Continue a probe after bucket b (whose tags were already inspected).
+template <int W>
+__device__ int64_t probe_from(const HashView &hv, uint64_t b, uint32_t tag, const uint64_t (&c)[W], uint32_t *err) {
+    for (uint64_t step = 1; step <= hv.bmask; ++step) {
+        b = (b + 1) & hv.bmask;
+        const uint4 t = load_tags(hv.tags, b);
+        const int64_t idx = verify_matches<W>(hv, b, tag_match(t, tag), c);
+        if (idx >= 0) return idx;
+        if (!bucket_full(t)) return -1;
     }
     if (err) atomicOr(err, 1u);
     return -1;
 }
 
-__device__ __forceinline__ int64_t probe_dyn(const uint64_t *c, int W, uint64_t hc,
-                                             const uint64_t *__restrict__ slots,
-                                             const uint64_t *__restrict__ keys, int64_t D,
-                                             uint64_t bucket_mask, uint32_t *err) {
-    const uint64_t m = fmix64(hc);
-    const uint32_t tag = (uint32_t)(m >> 32);
-    uint64_t b = m & bucket_mask;
-    for (uint64_t step = 0; step <= bucket_mask; ++step) {
-        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(slots + b * kBucketSlots);
-        const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1);
-        const uint64_t s[4] = {s01.x, s01.y, s23.x, s23.y};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (s[i] == kEmptySlot) return -1;
-            if ((uint32_t)(s[i] >> 32) == tag) {
-                const uint64_t idx = (uint32_t)s[i];
-                bool eq = true;
-                for (int w = 0; w < W; ++w) eq &= (__ldg(keys + (size_t)w * D + idx) == c[w]);
-                if (eq) return (int64_t)idx;
-            }
+// Lookup of column key c (W words, prehash hc); returns the row index or -1.
+// At most n_buckets buckets are visited (a full table yields -1, sets *err).
+template <int W>
+__device__ __forceinline__ int64_t probe(const uint64_t (&c)[W], uint64_t hc, const HashView &hv, uint32_t *err) {
+    uint32_t tag;
+    const uint64_t b = hash_bucket(hc, hv.shift, tag);
+    const uint4 t = load_tags(hv.tags, b);
+    const int64_t idx = verify_matches<W>(hv, b, tag_match(t, tag), c);
+    if (idx >= 0 || !bucket_full(t)) return idx;
+    return probe_from<W>(hv, b, tag, c, err);
+}
+
+__device__ __forceinline__ int64_t probe_dyn(const uint64_t *c, int W, uint64_t hc, const HashView &hv,
+                                             uint32_t *err) {
+    uint32_t tag;
+    uint64_t b = hash_bucket(hc, hv.shift, tag);
+    for (uint64_t step = 0; step <= hv.bmask; ++step) {
+        const uint4 t = load_tags(hv.tags, b);
+        uint32_t match = tag_match(t, tag);
+        while (match) {
+            const int i = __ffs(match) - 1;
+            match &= match - 1;
+            const uint64_t cand = __ldg(hv.sidx + b * kBucketSlots + i);
+            bool eq = true;
+            for (int w = 0; w < W; ++w) eq &= (__ldg(hv.keys + (size_t)w * hv.D + cand) == c[w]);
+            if (eq) return (int64_t)cand;
         }
-        b = (b + 1) & bucket_mask;
+        if (!bucket_full(t)) return -1;
+        b = (b + 1) & hv.bmask;
     }
     if (err) atomicOr(err, 1u);
     return -1;
@@ -262,6 +319,10 @@ int64_t unique_sorted(qsd_ctx ctx, const uint64_t *keys, int K, int64_t n, uint6
 void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_in, bool on_device);
 void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out);
 void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev);
+inline HashView hash_view(qsd_sub sub) {
+    return HashView{sub->tags.as<uint16_t>(), sub->sidx.as<uint32_t>(), sub->keys.as<uint64_t>(), sub->D,
+                    (uint64_t)sub->n_buckets - 1, sub->bucket_shift};
+}
 void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_ptr,
                    const int32_t *op_qubit, const uint8_t *op_code, const double *coef_re,
                    const double *coef_im);

@@ -4,10 +4,10 @@
 // occupancy bit-set for fast rejection of empty buckets.  Here the strings are
 // sorted by integer value on the device (index = rank, the order the MSOB
 // triangle test needs) and stored as coalesced SoA words; a separate open
-// addressing table of 8-byte (tag, index) slots in 4-slot, 32-byte buckets
-// serves lookups: one sector load rejects most absent keys, as the occupancy
-// bit-set did, and the load factor is kept <= 1/2 because D is known before
-// the table is built.
+// addressing table of 8-slot buckets (16-bit tags, 32-bit row indices)
+// serves lookups: one 16-byte load of eight 16-bit tags rejects almost every
+// absent key, as the occupancy bit-set did, and the load factor is kept
+// <= 1/4 because D is known before the table is built.
 #include <algorithm>
 
 #include "qsd_internal.cuh"
@@ -34,66 +34,71 @@ __global__ void k_mask_top(uint64_t *words, int W, int64_t n, uint64_t top_mask,
     if (words[(size_t)i * W + W - 1] & ~top_mask) atomicOr(err, 2u);
 }
 
-// One thread per key.  Slots of a bucket are claimed in order with CAS, so
-// in the finished table an empty slot ends every probe sequence that would
-// have reached a later slot.
+// One thread per key.  The slots of a bucket are claimed in order with a
+// 16-bit CAS on the tag, then the row index is stored; so in the finished
+// table every probe that would reach a later slot passes an occupied one.
+__device__ __forceinline__ bool claim_slot(unsigned short *tags, uint32_t *sidx, uint64_t b, uint32_t tag,
+                                           uint32_t i) {
+    for (int s = 0; s < kBucketSlots; ++s) {
+        if (atomicCAS(tags + b * kBucketSlots + s, (unsigned short)0, (unsigned short)tag) == 0) {
+            sidx[b * kBucketSlots + s] = i;
+            return true;
+        }
+    }
+    return false;
+}
+
 template <int W>
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ nib,
-                              unsigned long long *slots, uint64_t bucket_mask, uint32_t *err) {
+                              unsigned short *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     uint64_t x[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
-    const uint64_t m = fmix64(prehash<W>(x, nib));
-    const unsigned long long val = ((unsigned long long)(uint32_t)(m >> 32) << 32) | (uint64_t)i;
-    uint64_t b = m & bucket_mask;
+    uint32_t tag;
+    uint64_t b = hash_bucket(prehash<W>(x, nib), shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
-        for (int s = 0; s < kBucketSlots; ++s)
-            if (atomicCAS(slots + b * kBucketSlots + s, (unsigned long long)kEmptySlot, val) == kEmptySlot) return;
+        if (claim_slot(tags, sidx, b, tag, (uint32_t)i)) return;
         b = (b + 1) & bucket_mask;
     }
     atomicOr(err, 1u);
 }
 
 __global__ void k_hash_insert_dyn(const uint64_t *__restrict__ keys, int W, int64_t D,
-                                  const uint64_t *__restrict__ nib, unsigned long long *slots,
-                                  uint64_t bucket_mask, uint32_t *err) {
+                                  const uint64_t *__restrict__ nib, unsigned short *tags, uint32_t *sidx,
+                                  uint64_t bucket_mask, int shift, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     uint64_t x[kMaxWordsDyn];
     for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
-    const uint64_t m = fmix64(prehash_dyn(x, W, nib));
-    const unsigned long long val = ((unsigned long long)(uint32_t)(m >> 32) << 32) | (uint64_t)i;
-    uint64_t b = m & bucket_mask;
+    uint32_t tag;
+    uint64_t b = hash_bucket(prehash_dyn(x, W, nib), shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
-        for (int s = 0; s < kBucketSlots; ++s)
-            if (atomicCAS(slots + b * kBucketSlots + s, (unsigned long long)kEmptySlot, val) == kEmptySlot) return;
+        if (claim_slot(tags, sidx, b, tag, (uint32_t)i)) return;
         b = (b + 1) & bucket_mask;
     }
     atomicOr(err, 1u);
 }
 
 template <int W>
-__global__ void k_index(const uint64_t *__restrict__ q, int64_t n, const uint64_t *__restrict__ keys, int64_t D,
-                        const uint64_t *__restrict__ slots, uint64_t bucket_mask,
+__global__ void k_index(const uint64_t *__restrict__ q, int64_t n, const HashView hv,
                         const uint64_t *__restrict__ nib, int64_t *out, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t c[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
-    out[i] = D > 0 ? probe<W>(c, prehash<W>(c, nib), slots, keys, D, bucket_mask, err) : -1;
+    out[i] = hv.D > 0 ? probe<W>(c, prehash<W>(c, nib), hv, err) : -1;
 }
 
-__global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, const uint64_t *__restrict__ keys,
-                            int64_t D, const uint64_t *__restrict__ slots, uint64_t bucket_mask,
+__global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, const HashView hv,
                             const uint64_t *__restrict__ nib, int64_t *out, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t c[kMaxWordsDyn];
     for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
-    out[i] = D > 0 ? probe_dyn(c, W, prehash_dyn(c, W, nib), slots, keys, D, bucket_mask, err) : -1;
+    out[i] = hv.D > 0 ? probe_dyn(c, W, prehash_dyn(c, W, nib), hv, err) : -1;
 }
 
 uint64_t next_pow2(uint64_t v) {
@@ -136,23 +141,31 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     sub->keys.alloc((size_t)std::max<int64_t>(D, 1) * W * 8);
     if (D > 0) unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, sub->keys.as<uint64_t>(), D);
     soa.release();
-    // load factor <= 1/2 with 4-slot buckets
-    sub->n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(1, (2 * D + kBucketSlots - 1) / kBucketSlots));
-    sub->slots.alloc((size_t)sub->n_buckets * kBucketSlots * 8);
-    QSD_CUDA(cudaMemsetAsync(sub->slots.p, 0xff, (size_t)sub->n_buckets * kBucketSlots * 8, s));
+    // load factor <= 1/4 over buckets of 8 slots: a bucket overflows into the
+    // next one with probability ~1e-3, so probes almost never diverge
+    sub->n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (4 * D + kBucketSlots - 1) / kBucketSlots));
+    int lg = 0;
+    while ((1ll << lg) < sub->n_buckets) ++lg;
+    sub->bucket_shift = 64 - lg;
+    const int shift = sub->bucket_shift;
+    const size_t cap = (size_t)sub->n_buckets * kBucketSlots;
+    sub->tags.alloc(cap * 2);
+    sub->sidx.alloc(cap * 4);
+    QSD_CUDA(cudaMemsetAsync(sub->tags.p, 0, cap * 2, s));
     if (D > 0) {
         QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
         const uint64_t mask = (uint64_t)sub->n_buckets - 1;
-        auto *sl = sub->slots.as<unsigned long long>();
+        auto *tg = sub->tags.as<unsigned short>();
+        auto *si = sub->sidx.as<uint32_t>();
         const uint64_t *nib = ctx->nib.as<uint64_t>();
         const int nb = blocks_for(D, 256);
+        const uint64_t *k = sub->keys.as<uint64_t>();
         switch (W) {
-        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
-        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
-        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
-        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), D, nib, sl, mask, ctx->d_err); break;
-        default:
-            k_hash_insert_dyn<<<nb, 256, 0, s>>>(sub->keys.as<uint64_t>(), W, D, nib, sl, mask, ctx->d_err);
+        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        default: k_hash_insert_dyn<<<nb, 256, 0, s>>>(k, W, D, nib, tg, si, mask, shift, ctx->d_err);
         }
         QSD_LAUNCH_CHECK();
         if (take_device_error(ctx)) fail(QSD_ERR_INTERNAL, "build_subspace: hash table overflow");
@@ -163,18 +176,15 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
 void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out) {
     if (n <= 0) return;
     cudaStream_t s = ctx->stream;
-    const int W = sub->W;
-    const uint64_t mask = (uint64_t)sub->n_buckets - 1;
+    const HashView hv = hash_view(sub);
     const uint64_t *nib = ctx->nib.as<uint64_t>();
-    const uint64_t *keys = sub->keys.as<uint64_t>();
-    const uint64_t *sl = sub->slots.as<uint64_t>();
     const int nb = blocks_for(n, 256);
-    switch (W) {
-    case 1: k_index<1><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
-    case 2: k_index<2><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
-    case 3: k_index<3><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
-    case 4: k_index<4><<<nb, 256, 0, s>>>(q, n, keys, sub->D, sl, mask, nib, out, ctx->d_err); break;
-    default: k_index_dyn<<<nb, 256, 0, s>>>(q, W, n, keys, sub->D, sl, mask, nib, out, ctx->d_err);
+    switch (sub->W) {
+    case 1: k_index<1><<<nb, 256, 0, s>>>(q, n, hv, nib, out, ctx->d_err); break;
+    case 2: k_index<2><<<nb, 256, 0, s>>>(q, n, hv, nib, out, ctx->d_err); break;
+    case 3: k_index<3><<<nb, 256, 0, s>>>(q, n, hv, nib, out, ctx->d_err); break;
+    case 4: k_index<4><<<nb, 256, 0, s>>>(q, n, hv, nib, out, ctx->d_err); break;
+    default: k_index_dyn<<<nb, 256, 0, s>>>(q, sub->W, n, hv, nib, out, ctx->d_err);
     }
     QSD_LAUNCH_CHECK();
 }

@@ -99,9 +99,10 @@ def _check_apply(ctx, op, words, k, seed, mixed=True):
     if mixed:
         x32 = x.astype(np.float32)
         ref32 = oracle.apply(op, keys, x32.astype(np.float64)).real
-        y32 = ctx.apply_H(h, sub, to_cuda(ctx, x32, torch.float32), precision=q.QSD_FP32_MIXED)
-        ctx.synchronize()
-        assert rel_err(y32.cpu().numpy().astype(np.float64), ref32) <= FP32_TOL
+        for prec in (q.QSD_FP32_MIXED, q.QSD_FP32_DOT2):
+            y32 = ctx.apply_H(h, sub, to_cuda(ctx, x32, torch.float32), precision=prec)
+            ctx.synchronize()
+            assert rel_err(y32.cpu().numpy().astype(np.float64), ref32) <= FP32_TOL, prec
     return h, sub
 
 
@@ -236,8 +237,9 @@ def test_lanczos_tfim_closed_form(ctx):
     e_ref = -2.0 / math.sin(math.pi / 24)
     e, info = ctx.lanczos_ground_state(h, sub, max_steps=200, tol=1e-10)
     assert abs(e - e_ref) <= 1e-10 * abs(e_ref), (e, e_ref, info)
-    e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=200, tol=1e-10, precision=q.QSD_FP32_MIXED)
-    assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (e2, e_ref, info2)
+    for prec in (q.QSD_FP32_MIXED, q.QSD_FP32_DOT2):
+        e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=200, tol=1e-10, precision=prec)
+        assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (prec, e2, e_ref, info2)
 
 
 def test_lanczos_xxz_subspace_vs_oracle(ctx):
@@ -250,8 +252,9 @@ def test_lanczos_xxz_subspace_vs_oracle(ctx):
     sub = ctx.build_subspace(16, words)
     e, info = ctx.lanczos_ground_state(h, sub, max_steps=300, tol=1e-10)
     assert abs(e - e_ref) <= 1e-10 * abs(e_ref), (e, e_ref, info)
-    e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=300, tol=1e-10, precision=q.QSD_FP32_MIXED)
-    assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (e2, e_ref, info2)
+    for prec in (q.QSD_FP32_MIXED, q.QSD_FP32_DOT2):
+        e2, info2 = ctx.lanczos_ground_state(h, sub, max_steps=300, tol=1e-10, precision=prec)
+        assert abs(e2 - e_ref) <= 1e-7 * abs(e_ref), (prec, e2, e_ref, info2)
 
 
 def test_lanczos_hubbard_dimer_closed_form(ctx):
