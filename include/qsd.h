@@ -190,6 +190,15 @@ int qsd_target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
 int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
                    int64_t nrows, int8_t *out);
 
+/* FP64 Rayleigh quotient of a real vector u (device double [D]), the step
+ * that refines a mixed-precision Ritz value (the Rayleigh quotient of a vector
+ * with residual r is off by O(|r|^2)).  out (host double [3]) receives
+ * out[0] = u^T H u / u^T u, out[1] = |H u - out[0] u| / |u| and out[2] = u^T u.
+ * Uses device scratch of D + 4 * 2048 doubles held by the context (allocated on
+ * first use, grown when a larger subspace comes).  Synchronises the stream.
+ * Errors: QSD_ERR_COMPLEX_UNSUPPORTED, QSD_ERR_INVALID_ARG (u^T u == 0). */
+int qsd_rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *u, double *out);
+
 /* ------------------------------------------------------------- eigensolver */
 typedef struct {
     int32_t precision;     /* QSD_FP64, or QSD_FP32_MIXED / QSD_FP32_DOT2: FP32

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("qsd_diagonal", C.c_int, [_P, _P, _P, _P]),
     ("qsd_target_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
     ("qsd_term_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
+    ("qsd_rayleigh_quotient", C.c_int, [_P, _P, _P, _P, _P]),
     ("qsd_lanczos_default_params", None, [C.POINTER(LanczosParams)]),
     ("qsd_lanczos_ground_state", C.c_int, [_P, _P, _P, C.POINTER(LanczosParams), C.POINTER(_D), _P,
                                           C.POINTER(LanczosInfo)]),
@@ -275,6 +276,12 @@ class Context:
         out = self.empty((nrows, T), self.torch.int8)
         self._check(lib().qsd_term_table(self.handle, op.handle, sub.handle, row0, nrows, _t_ptr(out)))
         return out
+
+    def rayleigh_quotient(self, op: Operator, sub: Subspace, u):
+        """(u^T H u / u^T u, |H u - theta u| / |u|, u^T u) for a CUDA float64 vector u."""
+        out = np.zeros(3)
+        self._check(lib().qsd_rayleigh_quotient(self.handle, op.handle, sub.handle, _t_ptr(u), _np_ptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
 
     def lanczos_ground_state(self, op: Operator, sub: Subspace, want_vector: bool = False,
                              check: bool = True, **params):

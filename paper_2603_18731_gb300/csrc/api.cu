@@ -161,6 +161,7 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     p.y = y;
     p.ld = k;
     p.err = ctx->d_err;
+    p.num_sms = ctx->num_sms;
     const int R = choose_lanes(ctx, sub->D, op->G);
     int64_t c = 0;
     while (c < k) {
@@ -457,6 +458,19 @@ int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nr
         if (nrows > 0 && op->T_in > 0 && !out) fail(QSD_ERR_INVALID_ARG, "qsd_term_table: NULL output");
         set_device(ctx);
         term_table(ctx, op, sub, row0, nrows, out);
+    });
+}
+
+int qsd_rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *u, double *out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (!u || !out || sub->D == 0) fail(QSD_ERR_INVALID_ARG, "qsd_rayleigh_quotient: bad arguments");
+        if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_rayleigh_quotient: complex operator");
+        set_device(ctx);
+        Binding *b = get_binding(ctx, op, sub);
+        rayleigh_quotient(ctx, op, sub, b->diag.as<double>(), u, out);
     });
 }
 

@@ -64,6 +64,7 @@ struct ApplyParams {
     int64_t ld;              // row stride of x and y (= k)
     int64_t col0;            // first column handled by this launch
     uint32_t *err;
+    int num_sms;
 };
 
 template <int W>
@@ -136,12 +137,12 @@ __device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e
     e += te + e2;
 }
 
+// One output row; the R lanes of a row call this together.
 template <int W, int R, int KB, int PREC>
-__global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParams p) {
+__device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t row) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     constexpr int U = 4;
     const int sub = threadIdx.x % R;
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R;
     const bool active = row < p.D;
     const int64_t r = active ? row : p.D - 1;
     uint64_t key[W];
@@ -180,9 +181,17 @@ __global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParam
                     // nb is uniform across the warp (lane per row): a real loop
                     const int nb = (int)(info & 7u);
                     int l = 0;
-                    for (int i = 0; i < nb; ++i) {
-                        const int q = (int)((r0.y >> (12 * i)) & 0xfff);
-                        l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+                    if (nb > 0) {
+                        const int q0 = (int)(r0.y & 0xfff);
+                        l = (int)((word_of<W>(key, q0) >> (q0 & 63)) & 1);
+                        if (nb > 1) {
+                            const int q1 = (int)((r0.y >> 12) & 0xfff);
+                            l |= (int)((word_of<W>(key, q1) >> (q1 & 63)) & 1) << 1;
+                            for (int i = 2; i < nb; ++i) {
+                                const int q = (int)((r0.y >> (12 * i)) & 0xfff);
+                                l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+                            }
+                        }
                     }
                     if (PREC == QSD_FP32_DOT2) {
                         const float2 f = __ldg(p.ampf + off + l);
@@ -265,6 +274,12 @@ __global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParam
             for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
         }
     }
+}
+
+// One launch covers all rows: R lanes per row, rows past D inactive.
+template <int W, int R, int KB, int PREC>
+__global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParams p) {
+    apply_row<W, R, KB, PREC>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
 }
 
 // Run-time W (W > kMaxWordsStatic): a lane per row, keys in local memory,

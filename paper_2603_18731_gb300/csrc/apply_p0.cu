@@ -1,4 +1,6 @@
 // Instantiations of the product kernel for precision mode 0.
+#include <algorithm>
+
 #include "apply_kernel.cuh"
 
 namespace qsd {

@@ -1,4 +1,6 @@
 // Instantiations of the product kernel for precision mode 1.
+#include <algorithm>
+
 #include "apply_kernel.cuh"
 
 namespace qsd {

@@ -431,6 +431,38 @@ std::pair<double, double> fp64_residual(qsd_ctx ctx, qsd_op op, qsd_sub sub, con
 
 }  // namespace
 
+void rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const double *u, double *out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t D = sub->D;
+    const int B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
+    double *hu = static_cast<double *>(ctx->scratch[2].get((size_t)D * 8));
+    double *part = static_cast<double *>(ctx->scratch[3].get((size_t)4 * 2048 * 8));
+    double *scal = part + 3 * 2048;
+    apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu, s);
+    k_dot_partial<<<B, kRedThreads, 0, s>>>(u, hu, D, part);
+    k_sum<<<1, kRedThreads, 0, s>>>(part, B, scal);            // u^T H u
+    k_dot_partial<<<B, kRedThreads, 0, s>>>(u, u, D, part + 2048);
+    k_sum<<<1, kRedThreads, 0, s>>>(part + 2048, B, scal + 1); // u^T u
+    QSD_LAUNCH_CHECK();
+    double h[2];
+    QSD_CUDA(cudaMemcpyAsync(h, scal, 16, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
+    if (!(h[1] > 0.0)) fail(QSD_ERR_INVALID_ARG, "rayleigh_quotient: u is zero");
+    const double theta = h[0] / h[1];
+    QSD_CUDA(cudaMemcpyAsync(scal + 2, &theta, 8, cudaMemcpyHostToDevice, s));
+    // r = H u - theta u, |r|^2
+    k_axpy_res<<<blocks_for(D, 256), 256, 0, s>>>(hu, u, scal + 2, D, hu);
+    k_sq_partial<<<B, kRedThreads, 0, s>>>(hu, D, part);
+    k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, scal + 3);
+    QSD_LAUNCH_CHECK();
+    double rn = 0.0;
+    QSD_CUDA(cudaMemcpyAsync(&rn, scal + 3, 8, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
+    out[0] = theta;
+    out[1] = rn / std::sqrt(h[1]);
+    out[2] = h[1];
+}
+
 int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_params &p, double *energy,
                          double *vec_out, qsd_lanczos_info *info) {
     const auto t0 = std::chrono::steady_clock::now();

@@ -95,7 +95,7 @@ struct qsd_sub_s {
     int W = 1;
     int64_t D = 0;
     int64_t n_buckets = 0;  // power of two >= 2; capacity = 8 * n_buckets slots
-    int bucket_shift = 63;  // 64 - log2(n_buckets)
+    int bucket_shift = 31;  // 32 - log2(n_buckets)
     qsd::DevBuf keys;   // uint64 [W][D]
     qsd::DevBuf tags;   // uint16 [8 * n_buckets], 0 = empty
     qsd::DevBuf sidx;   // uint32 [8 * n_buckets]
@@ -147,8 +147,8 @@ struct Binding {
 // h(r xor F) = h(r) xor h(F): a row's prehash is computed once and each
 // group costs one xor.  (2) One multiplicative step (multiply-shift hashing,
 // Dietzfelbinger et al. 1997, with the golden-ratio multiplier of Fibonacci
-// hashing) gives the bucket (top bits of the product) and a 16-bit tag (bits
-// 16..31, never 0).
+// hashing) on a 32-bit fold of h gives the bucket (top bits of the product)
+// and a second product gives a 16-bit tag (never 0).
 //
 // Table layout: buckets of 8 slots.  tags: uint16 [8 * n_buckets], 0 = empty,
 // one 16-byte load per bucket; sidx: uint32 [8 * n_buckets], the row index of
@@ -164,12 +164,15 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-// bucket in [0, 2^(64 - shift)); tag in [1, 65535]
+// bucket in [0, 2^(32 - shift)); tag in [1, 65535].  32-bit arithmetic
+// only: the prehash is folded to 32 bits (lo xor hi * odd constant), the
+// bucket is the top bits of one multiply (multiply-shift) and the tag the top
+// 16 bits of a second, xorshifted multiply.
 __host__ __device__ __forceinline__ uint64_t hash_bucket(uint64_t h, int shift, uint32_t &tag) {
-    const uint64_t m = (h ^ (h >> 32)) * 0x9E3779B97F4A7C15ull;
-    const uint32_t t = (uint32_t)(m >> 16) & 0xffffu;
+    const uint32_t x = (uint32_t)h ^ ((uint32_t)(h >> 32) * 0x9E3779B1u);
+    const uint32_t t = ((x ^ (x >> 15)) * 0xC2B2AE3Du) >> 16;
     tag = t ? t : 1u;
-    return m >> shift;
+    return (uint64_t)((x * 0x85EBCA77u) >> shift);
 }
 
 // nib: tables for words 1..W-1, [(w-1)][16 nibble positions][16 values]
@@ -206,19 +209,27 @@ __device__ __forceinline__ uint4 load_tags(const uint16_t *__restrict__ tags, ui
     return __ldg(reinterpret_cast<const uint4 *>(tags + b * kBucketSlots));
 }
 
-// Bit i set when tag i of the bucket equals `tag`.
+// For v = (tags of two slots) xor (tag, tag): nonzero iff one halfword of v
+// is zero, i.e. one of the two slots matches (the "has a zero element" test of
+// Hacker's Delight, section 6-1, on 16-bit lanes; exact as an existence test).
+__device__ __forceinline__ uint32_t zero_half(uint32_t v) { return (v - 0x00010001u) & ~v & 0x80008000u; }
+
+// Bit i set when tag i of the bucket equals `tag` (exact per slot).
 __device__ __forceinline__ uint32_t tag_match(const uint4 t, uint32_t tag) {
-    const uint32_t tt = tag | (tag << 16);
-    const uint32_t m0 = __vcmpeq2(t.x, tt), m1 = __vcmpeq2(t.y, tt);
-    const uint32_t m2 = __vcmpeq2(t.z, tt), m3 = __vcmpeq2(t.w, tt);
-    return (m0 & 1u) | ((m0 >> 15) & 2u) | ((m1 & 1u) << 2) | ((m1 >> 13) & 8u) | ((m2 & 1u) << 4) |
-           ((m2 >> 11) & 32u) | ((m3 & 1u) << 6) | ((m3 >> 9) & 128u);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        m |= (((w[i] & 0xffffu) == tag) ? 1u : 0u) << (2 * i);
+        m |= (((w[i] >> 16) == tag) ? 1u : 0u) << (2 * i + 1);
+    }
+    return m;
 }
 
 // Some tag of the bucket equals `tag`.
 __device__ __forceinline__ bool tag_any(const uint4 t, uint32_t tag) {
     const uint32_t tt = tag | (tag << 16);
-    return (__vcmpeq2(t.x, tt) | __vcmpeq2(t.y, tt) | __vcmpeq2(t.z, tt) | __vcmpeq2(t.w, tt)) != 0u;
+    return (zero_half(t.x ^ tt) | zero_half(t.y ^ tt) | zero_half(t.z ^ tt) | zero_half(t.w ^ tt)) != 0u;
 }
 
 // The bucket's last slot is occupied: the probe continues in the next bucket.
@@ -333,6 +344,7 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
              const void *x, void *y, cudaStream_t stream);
 void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out);
 void term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int8_t *out);
+void rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const double *u, double *out);
 int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_params &p,
                          double *energy, double *vec_out, qsd_lanczos_info *info);
 

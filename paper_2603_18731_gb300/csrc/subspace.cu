@@ -146,7 +146,8 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     sub->n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (4 * D + kBucketSlots - 1) / kBucketSlots));
     int lg = 0;
     while ((1ll << lg) < sub->n_buckets) ++lg;
-    sub->bucket_shift = 64 - lg;
+    if (lg > 32) fail(QSD_ERR_CAPACITY, "build_subspace: hash table larger than 2^32 buckets");
+    sub->bucket_shift = 32 - lg;
     const int shift = sub->bucket_shift;
     const size_t cap = (size_t)sub->n_buckets * kBucketSlots;
     sub->tags.alloc(cap * 2);

@@ -228,6 +228,23 @@ def test_operator_errors(ctx):
     assert e.value.status == "INVALID_ARG"
 
 
+def test_rayleigh_quotient_matches_oracle(ctx):
+    import torch
+    op = wl.xxz_square(4, 4)
+    words = wl.xxz_walk_subspace(4, 4, count=3000, max_len=8, seed=6)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(16, words)
+    u = np.random.default_rng(5).normal(size=sub.dim)
+    hu = oracle.apply(op, keys, u).real
+    theta_ref = float(u @ hu / (u @ u))
+    res_ref = float(np.linalg.norm(hu - theta_ref * u) / np.linalg.norm(u))
+    theta, res, nrm = ctx.rayleigh_quotient(h, sub, to_cuda(ctx, u, torch.float64))
+    assert abs(theta - theta_ref) <= 1e-12 * abs(theta_ref)
+    assert abs(res - res_ref) <= 1e-10 * res_ref
+    assert abs(nrm - u @ u) <= 1e-12 * (u @ u)
+
+
 # ------------------------------------------------------------- eigensolver
 def test_lanczos_tfim_closed_form(ctx):
     import paper_2603_18731_gb300 as q
