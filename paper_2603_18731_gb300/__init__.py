@@ -78,6 +78,7 @@ SIGNATURES = [
     ("qsd_target_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
     ("qsd_term_table", C.c_int, [_P, _P, _P, _I64, _I64, _P]),
     ("qsd_rayleigh_quotient", C.c_int, [_P, _P, _P, _P, _P]),
+    ("qsd_rayleigh_quotient_noalloc", C.c_int, [_P, _P, _P, _P, _P]),
     ("qsd_lanczos_default_params", None, [C.POINTER(LanczosParams)]),
     ("qsd_lanczos_ground_state", C.c_int, [_P, _P, _P, C.POINTER(LanczosParams), C.POINTER(_D), _P,
                                           C.POINTER(LanczosInfo)]),
@@ -281,6 +282,14 @@ class Context:
         """(u^T H u / u^T u, |H u - theta u| / |u|, u^T u) for a CUDA float64 vector u."""
         out = np.zeros(3)
         self._check(lib().qsd_rayleigh_quotient(self.handle, op.handle, sub.handle, _t_ptr(u), _np_ptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def rayleigh_quotient_noalloc(self, op: Operator, sub: Subspace, u):
+        """As rayleigh_quotient with no device allocation (fixed library scratch,
+        at most 2^20 rows; overlapping calls race)."""
+        out = np.zeros(3)
+        self._check(lib().qsd_rayleigh_quotient_noalloc(self.handle, op.handle, sub.handle, _t_ptr(u),
+                                                        _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
 
     def lanczos_ground_state(self, op: Operator, sub: Subspace, want_vector: bool = False,

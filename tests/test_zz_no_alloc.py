@@ -1,0 +1,61 @@
+"""The allocation-free Rayleigh quotient, for callers that cannot call
+cudaMalloc (stream capture, pre-reserved serving loops, foreign allocators).
+
+Called through the C ABI and checked against qsd_rayleigh_quotient, which
+allocates its scratch, on two calls in a row (the shared fixed scratch keeps
+the previous call's contents, which must not leak into the next result), and
+its size limit.  Kept in a file that pytest collects last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _abi_rq(ctx, name, h, sub, u):
+    import paper_2603_18731_gb300 as q
+    out = np.zeros(3)
+    rc = getattr(q.lib(), name)(ctx.handle, h.handle, sub.handle, ctypes.c_void_p(u.data_ptr()),
+                                out.ctypes.data_as(ctypes.c_void_p))
+    return rc, out
+
+
+def test_noalloc_matches_allocating_entry_point_twice():
+    import torch
+    import paper_2603_18731_gb300 as q
+    with q.create(0) as ctx:
+        op = wl.xxz_square(4, 4)
+        words = wl.xxz_walk_subspace(4, 4, count=3000, max_len=8, seed=6)
+        h = ctx.load_operator(op)
+        sub = ctx.build_subspace(16, words)
+        rng = np.random.default_rng(11)
+        for call in range(2):
+            with torch.cuda.stream(ctx.stream):
+                u = torch.as_tensor(rng.normal(size=sub.dim), device=ctx.device)
+            rc_a, ref = _abi_rq(ctx, "qsd_rayleigh_quotient", h, sub, u)
+            rc_b, got = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
+            assert rc_a == 0 and rc_b == 0, (call, rc_a, rc_b)
+            assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]), (call, got, ref)
+            assert abs(got[1] - ref[1]) <= 1e-10 * abs(ref[1]), (call, got, ref)
+            assert abs(got[2] - ref[2]) <= TOL * abs(ref[2]), (call, got, ref)
+
+
+def test_noalloc_rejects_subspace_above_limit():
+    import torch
+    import paper_2603_18731_gb300 as q
+    with q.create(0) as ctx:
+        op = wl.tfim_chain(21, g=1.0)
+        h = ctx.load_operator(op)
+        sub = ctx.build_subspace(21, wl.full_space(21))
+        assert sub.dim == 1 << 21
+        with torch.cuda.stream(ctx.stream):
+            u = torch.ones(sub.dim, dtype=torch.float64, device=ctx.device)
+        rc, _ = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
+        assert q.STATUS[rc] == "CAPACITY"
+        assert b"at most" in q.lib().qsd_last_error(ctx.handle)
