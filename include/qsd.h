@@ -255,6 +255,50 @@ int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub,
                              const qsd_lanczos_params *p, double *energy,
                              double *vec_out, qsd_lanczos_info *info);
 
+/* --------------------------------------------------------------- serving */
+/* Continuous-batching ground-state server (the served loop of the build
+ * target; the paper runs one eigensolve at a time).  One scheduler thread
+ * admits queued requests in FIFO order when one of `max_active` slots is free
+ * and the request's device footprint (Krylov basis, refinement basis,
+ * diagonal and work vectors; the subspace and operator tables are the
+ * caller's) fits in `budget_bytes` next to the admitted ones (a request
+ * larger than the budget runs alone).  Each admitted request has its own
+ * stream and advances asynchronously -- graph-captured chunks of Lanczos
+ * steps, Ritz vector and FP64 residual, FP64 refinement restarts -- so the
+ * work of all admitted requests overlaps on the device and requests that
+ * arrive while others run start as soon as a slot and memory free up.
+ * Results equal those of qsd_lanczos_ground_state with the same parameters.
+ * op and sub may come from any context of the same device and must stay alive
+ * until the request is done.  All calls are thread-safe. */
+typedef struct qsd_server_s *qsd_server;
+
+typedef struct {
+    int64_t queued, active, completed, failed, admitted;
+    uint64_t bytes_in_use, peak_bytes, budget_bytes;
+} qsd_server_stats;
+
+int qsd_server_create(qsd_ctx ctx, size_t budget_bytes, int32_t max_active, qsd_server *out);
+/* Queue a request; *ticket identifies it.  Errors: QSD_ERR_NOT_HERMITIAN,
+ * QSD_ERR_COMPLEX_UNSUPPORTED, QSD_ERR_INVALID_ARG. */
+int qsd_server_submit(qsd_server srv, qsd_op op, qsd_sub sub, const qsd_lanczos_params *p, uint64_t *ticket);
+/* QSD_PENDING while running, else the request's final status with energy,
+ * info and times (optional host double [3]: submit, admit, done, in seconds
+ * since the server was created; admit = -1 if never admitted). */
+int qsd_server_poll(qsd_server srv, uint64_t ticket, double *energy, qsd_lanczos_info *info, double *times);
+/* As poll, blocking up to timeout_s seconds (<= 0: no limit); QSD_ERR_TIMEOUT
+ * when the wait runs out. */
+int qsd_server_wait(qsd_server srv, uint64_t ticket, double timeout_s, double *energy, qsd_lanczos_info *info,
+                    double *times);
+/* Request cancellation; the request ends with QSD_ERR_CANCELLED at its next
+ * piece boundary (or at once while queued). */
+int qsd_server_cancel(qsd_server srv, uint64_t ticket);
+/* Forget a finished request (QSD_PENDING while it is not retired yet). */
+int qsd_server_release(qsd_server srv, uint64_t ticket);
+int qsd_server_get_stats(qsd_server srv, qsd_server_stats *stats);
+const char *qsd_server_last_error(qsd_server srv);
+/* Cancel what is queued or running, wait for the scheduler, free everything. */
+int qsd_server_destroy(qsd_server srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,12 @@ class LanczosInfo(C.Structure):
                 ("energy_unrefined", C.c_double), ("status", C.c_int32), ("applies", C.c_int32)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("admitted", C.c_int64), ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64),
+                ("budget_bytes", C.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -82,6 +88,15 @@ SIGNATURES = [
     ("qsd_lanczos_default_params", None, [C.POINTER(LanczosParams)]),
     ("qsd_lanczos_ground_state", C.c_int, [_P, _P, _P, C.POINTER(LanczosParams), C.POINTER(_D), _P,
                                           C.POINTER(LanczosInfo)]),
+    ("qsd_server_create", C.c_int, [_P, C.c_size_t, _I32, C.POINTER(_P)]),
+    ("qsd_server_submit", C.c_int, [_P, _P, _P, C.POINTER(LanczosParams), C.POINTER(_U64)]),
+    ("qsd_server_poll", C.c_int, [_P, _U64, C.POINTER(_D), C.POINTER(LanczosInfo), _P]),
+    ("qsd_server_wait", C.c_int, [_P, _U64, _D, C.POINTER(_D), C.POINTER(LanczosInfo), _P]),
+    ("qsd_server_cancel", C.c_int, [_P, _U64]),
+    ("qsd_server_release", C.c_int, [_P, _U64]),
+    ("qsd_server_get_stats", C.c_int, [_P, C.POINTER(ServerStats)]),
+    ("qsd_server_last_error", C.c_char_p, [_P]),
+    ("qsd_server_destroy", C.c_int, [_P]),
 ]
 
 
@@ -312,6 +327,77 @@ class Context:
         if check and rc not in (QSD_OK,):
             raise QsdError(rc, lib().qsd_last_error(self.handle).decode())
         return (e.value, d, vec) if want_vector else (e.value, d)
+
+
+def lanczos_params(**params) -> LanczosParams:
+    """qsd_lanczos_params with the library defaults, overridden by keywords
+    (``v0`` takes a CUDA float64 tensor)."""
+    p = LanczosParams()
+    lib().qsd_lanczos_default_params(C.byref(p))
+    v0 = params.pop("v0", None)
+    for k, v in params.items():
+        setattr(p, k, v)
+    if v0 is not None:
+        p.v0 = C.c_void_p(v0.data_ptr())
+    return p
+
+
+class Server:
+    """Continuous-batching ground-state server (qsd_server_*)."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_active: int = 8):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(lib().qsd_server_create(ctx.handle, int(budget_bytes), int(max_active), C.byref(h)))
+        self.handle = h
+
+    def _err(self, rc):
+        raise QsdError(rc, (lib().qsd_server_last_error(self.handle) or b"").decode())
+
+    def submit(self, op: Operator, sub: Subspace, **params) -> int:
+        t = C.c_uint64()
+        rc = lib().qsd_server_submit(self.handle, op.handle, sub.handle, C.byref(lanczos_params(**params)),
+                                     C.byref(t))
+        if rc != QSD_OK:
+            self._err(rc)
+        return t.value
+
+    def _result(self, rc, e, info, times):
+        d = {f: getattr(info, f) for f, _ in LanczosInfo._fields_}
+        return {"status": STATUS.get(rc, rc), "code": rc, "energy": e.value, "info": d,
+                "t_submit": times[0], "t_admit": times[1], "t_done": times[2]}
+
+    def poll(self, ticket: int):
+        e, info, times = C.c_double(), LanczosInfo(), np.zeros(3)
+        rc = lib().qsd_server_poll(self.handle, ticket, C.byref(e), C.byref(info), _np_ptr(times))
+        return None if rc == 12 else self._result(rc, e, info, times)
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        e, info, times = C.c_double(), LanczosInfo(), np.zeros(3)
+        rc = lib().qsd_server_wait(self.handle, ticket, timeout_s, C.byref(e), C.byref(info), _np_ptr(times))
+        return self._result(rc, e, info, times)
+
+    def cancel(self, ticket: int):
+        lib().qsd_server_cancel(self.handle, ticket)
+
+    def release(self, ticket: int) -> bool:
+        return lib().qsd_server_release(self.handle, ticket) == QSD_OK
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        lib().qsd_server_get_stats(self.handle, C.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qsd_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def create(device: int = 0, stream=None) -> Context:

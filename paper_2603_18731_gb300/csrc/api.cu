@@ -33,10 +33,29 @@ void DevBuf::alloc(size_t n) {
     bytes = n;
 }
 
+void DevBuf::alloc_async(size_t n, cudaStream_t s) {
+    release();
+    if (n == 0) return;
+    const cudaError_t e = cudaMallocAsync(&p, n, s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        throw Error(QSD_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = n;
+    stream = s;
+    async = true;
+}
+
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (async) cudaFreeAsync(p, stream);
+        else cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
+    async = false;
+    stream = nullptr;
 }
 
 // ------------------------------------------------------------ hash tables

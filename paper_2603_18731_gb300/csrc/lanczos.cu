@@ -1,30 +1,33 @@
 // Ground state of H_S by Lanczos on the device.
 //
 // The paper hands its matrix-free operator to external eigensolvers (ARPACK,
-// PRIMME; Results and Methods "Matrix evaluation").  Here the solver runs on
-// the GPU next to the product: per step, y = H v_j, then classical
-// Gram-Schmidt against all previous vectors applied twice (FP64 dots), the
-// norm, and the next vector; every `check_every` steps one CTA solves the
-// tridiagonal problem (multisection on Sturm counts for the lowest
-// eigenvalue, inverse iteration for its eigenvector) and the host reads the
-// residual estimate beta_{j+1} |s_j| through pinned memory.
+// PRIMME; Results, and Methods "Matrix evaluation").  Here the solver runs on
+// the GPU next to the product.  Per step: y = H v_j; classical Gram-Schmidt
+// against all previous vectors, applied twice, with FP64 dots (alpha_j is the
+// v_j coefficient of both passes); beta_{j+1} = |w|; v_{j+1} = w / beta_{j+1}.
+// Every `check_every` steps one CTA solves the tridiagonal problem
+// (multisection on Sturm counts for the lowest eigenvalue, inverse iteration
+// for its eigenvector) and the residual estimate beta_{j+1} |s_j| reaches the
+// host through pinned memory.
 //
-// Mixed precision: the Krylov basis and the products are FP32 (FP64 dots,
-// FP64 tridiagonal); the Ritz vector is then formed in FP64 and refined by
-// short FP64 Lanczos restarts from it until its FP64 residual meets `tol` or
-// the Rayleigh quotient stops moving.
+// The step index lives in device memory and every kernel reads it, so one
+// chunk of `check_every` steps is a fixed sequence of launches: it is captured
+// once into a CUDA graph and replayed for every chunk.
+//
+// Mixed precision: the Krylov basis and the products are FP32 (FP64 dots and
+// tridiagonal); the Ritz vector is formed in FP64 and refined by short FP64
+// Lanczos restarts from it until its FP64 residual meets `tol` or the FP64
+// Rayleigh quotient stops moving.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 
-#include "qsd_internal.cuh"
+#include "lanczos.cuh"
 
 namespace qsd {
 
 namespace {
-
-constexpr int kRedThreads = 256;
-constexpr int kMaxSteps = 700;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -53,18 +56,19 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t i) {
     return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
 }
 
-template <typename TV>
-__global__ void k_start(TV *v, int64_t D, uint64_t seed, const double *v0, double *w) {
+__global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, int *jdev) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *jdev = 0;
     if (i >= D) return;
-    const double x = v0 ? v0[i] : uniform_pm1(seed, (uint64_t)i);
-    w[i] = x;
+    w[i] = v0 ? v0[i] : uniform_pm1(seed, (uint64_t)i);
 }
 
-// partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i < nvec
+// partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j
 template <typename TV, typename TU>
-__global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u, double *partial) {
+__global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
+                         const TU *__restrict__ u, double *partial) {
     __shared__ double sh[32];
+    const int nvec = *jdev + 1;
     const int B = gridDim.x;
     const int64_t chunk = (D + B - 1) / B;
     const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(D, r0 + chunk);
@@ -77,26 +81,29 @@ __global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, int nvec, const TU
     }
 }
 
-// h[i] = sum_b partial[i][b] (fixed order); optionally alpha += h[j]
-__global__ void k_reduce_rows(const double *__restrict__ partial, int nvec, int B, double *h, double *alpha_j,
-                              int j) {
+// h[i] = sum_b partial[i][b] in fixed order (block i; blocks past j exit);
+// alpha[j] += h[j]
+__global__ void k_reduce_rows(const double *__restrict__ partial, const int *__restrict__ jdev, int B, double *h,
+                              double *alpha) {
     __shared__ double sh[32];
+    const int j = *jdev;
     const int i = blockIdx.x;
-    if (i >= nvec) return;
+    if (i > j) return;
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += partial[(size_t)i * B + b];
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
         h[i] = s;
-        if (alpha_j && i == j) *alpha_j += s;
+        if (i == j) alpha[j] += s;
     }
 }
 
-// w[r] = u[r] - sum_i V[i][r] h[i]
+// w[r] = u[r] - sum_{i<=j} V[i][r] h[i]
 template <typename TV, typename TU>
-__global__ void k_gemv_sub(const TV *__restrict__ V, int64_t D, int nvec, const double *__restrict__ h,
-                           const TU *u, double *w) {
+__global__ void k_gemv_sub(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
+                           const double *__restrict__ h, const TU *u, double *w) {
     extern __shared__ double hs[];
+    const int nvec = *jdev + 1;
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,27 +122,35 @@ __global__ void k_sq_partial(const double *__restrict__ w, int64_t D, double *pa
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void k_sqrt_sum(const double *__restrict__ partial, int B, double *out) {
+// out[jdev ? *jdev + 1 : 0] = sqrt(sum partial)
+__global__ void k_sqrt_sum(const double *__restrict__ partial, int B, double *out, const int *__restrict__ jdev) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += partial[b];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) *out = sqrt(s);
+    if (threadIdx.x == 0) out[jdev ? *jdev + 1 : 0] = sqrt(s);
 }
 
+// v = w / nrm[jdev ? *jdev + 1 : 0] into V[j+1] (when j + 1 <= m) and vcur
 template <typename TV>
-__global__ void k_scale_to(const double *__restrict__ w, const double *__restrict__ nrm, int64_t D, TV *v) {
+__global__ void k_next(const double *__restrict__ w, const double *__restrict__ nrm, const int *__restrict__ jdev,
+                       int64_t D, int m, TV *V, TV *vcur) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= D) return;
+    const int j1 = jdev ? *jdev + 1 : 0;
+    const double s = nrm[j1];
+    const TV v = (TV)(s > 0.0 ? w[r] / s : 0.0);
+    if (V && j1 <= m) V[(size_t)j1 * D + r] = v;
+    if (vcur) vcur[r] = v;
+}
+
+__global__ void k_incr(int *jdev) { *jdev += 1; }
+
+__global__ void k_scale(double *u, const double *__restrict__ nrm, int64_t D) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= D) return;
     const double s = *nrm;
-    v[r] = (TV)(s > 0.0 ? w[r] / s : 0.0);
-}
-
-__global__ void k_axpy_res(const double *__restrict__ hu, const double *__restrict__ u, const double *__restrict__ theta,
-                           int64_t D, double *r) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D) return;
-    r[i] = hu[i] - (*theta) * u[i];
+    u[r] = s > 0.0 ? u[r] / s : 0.0;
 }
 
 __global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t D, double *partial) {
@@ -155,6 +170,14 @@ __global__ void k_sum(const double *__restrict__ partial, int B, double *out) {
     if (threadIdx.x == 0) *out = s;
 }
 
+// r = hu - (sc[0] / sc[1]) u
+__global__ void k_residual(const double *__restrict__ hu, const double *__restrict__ u, const double *__restrict__ sc,
+                           int64_t D, double *r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    r[i] = hu[i] - (sc[0] / sc[1]) * u[i];
+}
+
 // ------------------------------------------------------------- tridiagonal
 // Number of eigenvalues of T (diagonal a[0..m), off-diagonal b[1..m)) below x.
 __device__ int sturm(const double *a, const double *b, int m, double x) {
@@ -168,13 +191,17 @@ __device__ int sturm(const double *a, const double *b, int m, double x) {
     return c;
 }
 
-// One CTA.  out[0] = theta (lowest eigenvalue), out[1] = |beta_m s_{m-1}|
-// (residual estimate), out[2..2+m) = unit eigenvector s.
-__global__ void k_tridiag(const double *__restrict__ alpha, const double *__restrict__ beta, int m, double *out) {
+// One CTA, m = *jdev steps.  out[0] = theta (lowest eigenvalue), out[1] =
+// |beta_m s_{m-1}| (residual estimate), out[2] = beta_m, out[3] = m,
+// out[4..4+m) = unit eigenvector s.
+__global__ void k_tridiag(const double *__restrict__ alpha, const double *__restrict__ beta,
+                          const int *__restrict__ jdev, double *out) {
     extern __shared__ double sm[];
+    const int m = *jdev;
+    if (m <= 0) return;
     double *a = sm, *b = sm + m, *s = sm + 2 * m;
     __shared__ double lo_hi[2];
-    __shared__ int cnt[kRedThreads];
+    __shared__ int cnt[kLanczosThreads];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         a[i] = alpha[i];
         b[i] = i ? beta[i] : 0.0;
@@ -270,13 +297,17 @@ __global__ void k_tridiag(const double *__restrict__ alpha, const double *__rest
     }
     out[0] = theta;
     out[1] = fabs(beta[m] * s[m - 1]);
-    for (int i = 0; i < m; ++i) out[2 + i] = s[i];
+    out[2] = beta[m];
+    out[3] = (double)m;
+    for (int i = 0; i < m; ++i) out[4 + i] = s[i];
 }
 
-// u[r] = sum_i V[i][r] s[i]
+// u[r] = sum_{i < m} V[i][r] s[i], m = *jdev
 template <typename TV>
-__global__ void k_ritz(const TV *__restrict__ V, int64_t D, int nvec, const double *__restrict__ s, double *u) {
+__global__ void k_ritz(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev, const double *__restrict__ s,
+                       double *u) {
     extern __shared__ double ss[];
+    const int nvec = *jdev;
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) ss[i] = s[i];
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -286,150 +317,198 @@ __global__ void k_ritz(const TV *__restrict__ V, int64_t D, int nvec, const doub
     u[r] = acc;
 }
 
-struct Krylov {
-    int64_t D = 0;
-    int m = 0;
-    bool fp32 = false;
-    int B = 0;
-    DevBuf V, hv, w, h, partial, alpha, beta, tri, scal;
-};
-
 size_t tri_smem(int m) { return (size_t)8 * m * 8 + 64; }
 
-// Runs up to p_steps Lanczos steps from start vector `start` (FP64 [D]) and
-// returns the lowest Ritz value; the Ritz vector goes to u (FP64 [D]).
-struct LanczosResult {
-    double theta = 0.0, est = 0.0;
-    int steps = 0;
-    bool converged = false;
-    bool timeout = false;
-};
+}  // namespace
+
+// ---------------------------------------------------------------- job
+LanczosJob::~LanczosJob() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (hpin && own_pin) cudaFreeHost(hpin);
+}
+
+void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int product_precision, int steps,
+                      int check, cudaStream_t st, bool stream_ordered) {
+    ctx = c;
+    op = o;
+    sub = su;
+    diag = d;
+    prec = product_precision;
+    fp32 = product_precision != QSD_FP64;
+    D = su->D;
+    m = (int)std::min<int64_t>(std::min(steps, kLanczosMaxSteps), D);
+    check_every = std::max(1, std::min(check, m));
+    s = st;
+    B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
+    nbD = blocks_for(D, 256);
+    const size_t sv = fp32 ? 4 : 8;
+    auto A = [&](DevBuf &b, size_t n) {
+        if (stream_ordered) b.alloc_async(n, s);
+        else b.alloc(n);
+    };
+    A(V, (size_t)(m + 1) * D * sv);
+    A(vcur, (size_t)D * sv);
+    A(hv, (size_t)D * sv);
+    A(w, (size_t)D * 8);
+    A(h, (size_t)(m + 2) * 8);
+    A(part, (size_t)(m + 2) * B * 8);
+    A(alpha, (size_t)(m + 2) * 8);
+    A(beta, (size_t)(m + 3) * 8);
+    A(tri, (size_t)(m + 8) * 8);
+    A(jdev, 16);
+    if (!hpin) QSD_CUDA(cudaMallocHost(&hpin, 8 * sizeof(double)));
+}
+
+size_t LanczosJob::footprint(int64_t D, int steps, bool fp32, int num_sms) {
+    const int m = (int)std::min<int64_t>(std::min(steps, kLanczosMaxSteps), D);
+    const int B = std::max(1, std::min<int>(2 * num_sms, (int)((D + 255) / 256)));
+    const size_t sv = fp32 ? 4 : 8;
+    return (size_t)(m + 3) * D * sv + (size_t)D * 8 + (size_t)(m + 2) * B * 8 + (size_t)(m + 16) * 40;
+}
 
 template <typename TV>
-LanczosResult run_lanczos(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, Krylov &K, const double *start,
-                          uint64_t seed, int max_steps, double tol, int check_every, double *u,
-                          std::chrono::steady_clock::time_point deadline, bool has_deadline, int *applies,
-                          int prec32 = QSD_FP32_DOT2) {
-    cudaStream_t s = ctx->stream;
-    const int64_t D = K.D;
-    const int m = std::min<int64_t>(max_steps, D);
-    const int prec = std::is_same<TV, float>::value ? prec32 : QSD_FP64;
-    TV *V = K.V.as<TV>();
-    TV *hv = K.hv.as<TV>();
-    double *w = K.w.as<double>(), *h = K.h.as<double>(), *part = K.partial.as<double>();
-    double *alpha = K.alpha.as<double>(), *beta = K.beta.as<double>(), *tri = K.tri.as<double>();
-    double *scal = K.scal.as<double>();
-    const int nbD = blocks_for(D, 256);
-    const int B = K.B;
-    QSD_CUDA(cudaMemsetAsync(alpha, 0, (size_t)(K.m + 1) * 8, s));
-    QSD_CUDA(cudaMemsetAsync(beta, 0, (size_t)(K.m + 2) * 8, s));
-    // v_0 = start / |start|
-    k_start<TV><<<nbD, 256, 0, s>>>(V, D, seed, start, w);
-    k_sq_partial<<<B, kRedThreads, 0, s>>>(w, D, part);
-    k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, scal);
-    k_scale_to<TV><<<nbD, 256, 0, s>>>(w, scal, D, V);
+static void enqueue_start_t(LanczosJob &J, const double *start, uint64_t seed) {
+    cudaStream_t s = J.s;
+    QSD_CUDA(cudaMemsetAsync(J.alpha.p, 0, J.alpha.bytes, s));
+    QSD_CUDA(cudaMemsetAsync(J.beta.p, 0, J.beta.bytes, s));
+    double *w = J.w.as<double>(), *part = J.part.as<double>();
+    double *nrm = J.tri.as<double>() + J.m + 7;
+    k_start<<<J.nbD, 256, 0, s>>>(J.D, seed, start, w, J.jdev.as<int>());
+    k_sq_partial<<<J.B, kLanczosThreads, 0, s>>>(w, J.D, part);
+    k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(part, J.B, nrm, nullptr);
+    k_next<TV><<<J.nbD, 256, 0, s>>>(w, nrm, nullptr, J.D, J.m, J.V.as<TV>(), J.vcur.as<TV>());
     QSD_LAUNCH_CHECK();
-    LanczosResult res;
-    double *h_tri = nullptr;
-    QSD_CUDA(cudaMallocHost(&h_tri, 32));
-    int j = 0;
-    try {
-        for (j = 0; j < m; ++j) {
-            const TV *vj = V + (size_t)j * D;
-            apply_H(ctx, op, sub, diag, prec, 1, vj, hv, s);
-            ++*applies;
-            const int nvec = j + 1;
-            const size_t hsm = (size_t)nvec * 8;
-            // pass 1: h = V^T hv ; w = hv - V h ; alpha_j = h_j
-            k_gemv_t<TV, TV><<<B, kRedThreads, 0, s>>>(V, D, nvec, hv, part);
-            k_reduce_rows<<<nvec, 128, 0, s>>>(part, nvec, B, h, alpha + j, j);
-            k_gemv_sub<TV, TV><<<nbD, 256, hsm, s>>>(V, D, nvec, h, hv, w);
-            // pass 2: h = V^T w ; w -= V h ; alpha_j += h_j
-            k_gemv_t<TV, double><<<B, kRedThreads, 0, s>>>(V, D, nvec, w, part);
-            k_reduce_rows<<<nvec, 128, 0, s>>>(part, nvec, B, h, alpha + j, j);
-            k_gemv_sub<TV, double><<<nbD, 256, hsm, s>>>(V, D, nvec, h, w, w);
-            // beta_{j+1} = |w|, v_{j+1} = w / beta_{j+1}
-            k_sq_partial<<<B, kRedThreads, 0, s>>>(w, D, part);
-            k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, beta + j + 1);
-            if (j + 1 < K.m + 1 && j + 1 < m) k_scale_to<TV><<<nbD, 256, 0, s>>>(w, beta + j + 1, D, V + (size_t)(j + 1) * D);
-            QSD_LAUNCH_CHECK();
-            const bool last = (j + 1 == m);
-            if ((j + 1) % check_every == 0 || last) {
-                k_tridiag<<<1, kRedThreads, tri_smem(nvec), s>>>(alpha, beta, nvec, tri);
-                QSD_LAUNCH_CHECK();
-                QSD_CUDA(cudaMemcpyAsync(h_tri, tri, 16, cudaMemcpyDeviceToHost, s));
-                QSD_CUDA(cudaMemcpyAsync(h_tri + 2, beta + j + 1, 8, cudaMemcpyDeviceToHost, s));
-                QSD_CUDA(cudaStreamSynchronize(s));
-                const double hb = h_tri[2];
-                res.theta = h_tri[0];
-                res.est = h_tri[1];
-                res.steps = j + 1;
-                const double at = std::max(std::fabs(res.theta), 1e-300);
-                if (res.est <= tol * at || hb <= 1e-13 * at) {
-                    res.converged = true;
-                    break;
-                }
-                if (has_deadline && std::chrono::steady_clock::now() > deadline) {
-                    res.timeout = true;
-                    break;
-                }
-            }
-        }
-        // Ritz vector u = V[0..n) s
-        const int nvec = res.steps;
-        k_ritz<TV><<<nbD, 256, (size_t)nvec * 8, s>>>(V, D, nvec, tri + 2, u);
-        QSD_LAUNCH_CHECK();
-        // normalise u in FP64
-        k_sq_partial<<<B, kRedThreads, 0, s>>>(u, D, part);
-        k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, scal);
-        k_scale_to<double><<<nbD, 256, 0, s>>>(u, scal, D, u);
-        QSD_LAUNCH_CHECK();
-        QSD_CUDA(cudaStreamSynchronize(s));
-    } catch (...) {
-        cudaFreeHost(h_tri);
-        throw;
+    J.steps_done = 0;
+}
+
+void LanczosJob::enqueue_start(const double *start, uint64_t seed) {
+    if (fp32) enqueue_start_t<float>(*this, start, seed);
+    else enqueue_start_t<double>(*this, start, seed);
+}
+
+template <typename TV>
+static void enqueue_steps_t(LanczosJob &J, int n) {
+    cudaStream_t s = J.s;
+    TV *V = J.V.as<TV>(), *hv = J.hv.as<TV>(), *vc = J.vcur.as<TV>();
+    double *w = J.w.as<double>(), *h = J.h.as<double>(), *part = J.part.as<double>();
+    double *alpha = J.alpha.as<double>(), *beta = J.beta.as<double>();
+    const int *j = J.jdev.as<int>();
+    const size_t hsm = (size_t)(J.m + 1) * 8;
+    for (int t = 0; t < n; ++t) {
+        apply_H(J.ctx, J.op, J.sub, J.diag, J.prec, 1, vc, hv, s);
+        k_gemv_t<TV, TV><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, hv, part);
+        k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
+        k_gemv_sub<TV, TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, hv, w);
+        k_gemv_t<TV, double><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, w, part);
+        k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
+        k_gemv_sub<TV, double><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, w);
+        k_sq_partial<<<J.B, kLanczosThreads, 0, s>>>(w, J.D, part);
+        k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(part, J.B, beta, j);
+        k_next<TV><<<J.nbD, 256, 0, s>>>(w, beta, j, J.D, J.m, V, vc);
+        k_incr<<<1, 1, 0, s>>>(J.jdev.as<int>());
     }
-    cudaFreeHost(h_tri);
-    return res;
-}
-
-void alloc_krylov(qsd_ctx ctx, Krylov &K, int64_t D, int m, bool fp32) {
-    K.D = D;
-    K.m = m;
-    K.fp32 = fp32;
-    K.B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
-    const size_t sv = fp32 ? 4 : 8;
-    K.V.alloc((size_t)(m + 1) * D * sv);
-    K.hv.alloc((size_t)D * sv);
-    K.w.alloc((size_t)D * 8);
-    K.h.alloc((size_t)(m + 2) * 8);
-    K.partial.alloc((size_t)(m + 2) * K.B * 8);
-    K.alpha.alloc((size_t)(m + 2) * 8);
-    K.beta.alloc((size_t)(m + 3) * 8);
-    K.tri.alloc((size_t)(m + 4) * 8);
-    K.scal.alloc(32);
-}
-
-// FP64 residual and Rayleigh quotient of a unit vector u: returns (theta, |Hu - theta u|)
-std::pair<double, double> fp64_residual(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const double *u,
-                                        double *hu, double *r, double *part, int B, double *scal, int *applies) {
-    cudaStream_t s = ctx->stream;
-    const int64_t D = sub->D;
-    apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu, s);
-    ++*applies;
-    k_dot_partial<<<B, kRedThreads, 0, s>>>(u, hu, D, part);
-    k_sum<<<1, kRedThreads, 0, s>>>(part, B, scal);
-    k_axpy_res<<<blocks_for(D, 256), 256, 0, s>>>(hu, u, scal, D, r);
-    k_sq_partial<<<B, kRedThreads, 0, s>>>(r, D, part);
-    k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, scal + 1);
+    k_tridiag<<<1, kLanczosThreads, tri_smem(J.m), s>>>(alpha, beta, j, J.tri.as<double>());
     QSD_LAUNCH_CHECK();
-    double h[2];
-    QSD_CUDA(cudaMemcpyAsync(h, scal, 16, cudaMemcpyDeviceToHost, s));
-    QSD_CUDA(cudaStreamSynchronize(s));
-    return {h[0], h[1]};
+    QSD_CUDA(cudaMemcpyAsync(J.hpin, J.tri.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
-}  // namespace
+void LanczosJob::enqueue_chunk(bool use_graph) {
+    const int n = std::min(check_every, m - steps_done);
+    if (n <= 0) return;
+    if (use_graph && n == check_every) {
+        if (!graph) {
+            cudaGraph_t g = nullptr;
+            QSD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                if (fp32) enqueue_steps_t<float>(*this, n);
+                else enqueue_steps_t<double>(*this, n);
+            } catch (...) {
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            QSD_CUDA(cudaStreamEndCapture(s, &g));
+            const cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+            cudaGraphDestroy(g);
+            QSD_CUDA(e);
+        }
+        QSD_CUDA(cudaGraphLaunch(graph, s));
+    } else {
+        if (fp32) enqueue_steps_t<float>(*this, n);
+        else enqueue_steps_t<double>(*this, n);
+    }
+    steps_done += n;
+    ++chunks;
+}
+
+void LanczosJob::read(double &theta, double &est, double &beta_last, int &nvec) const {
+    theta = hpin[0];
+    est = hpin[1];
+    beta_last = hpin[2];
+    nvec = (int)hpin[3];
+}
+
+void LanczosJob::enqueue_ritz(double *u) {
+    const int *j = jdev.as<int>();
+    const size_t ssm = (size_t)(m + 1) * 8;
+    double *nrm = tri.as<double>() + m + 7;
+    if (fp32) k_ritz<float><<<nbD, 256, ssm, s>>>(V.as<float>(), D, j, tri.as<double>() + 4, u);
+    else k_ritz<double><<<nbD, 256, ssm, s>>>(V.as<double>(), D, j, tri.as<double>() + 4, u);
+    k_sq_partial<<<B, kLanczosThreads, 0, s>>>(u, D, part.as<double>());
+    k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(part.as<double>(), B, nrm, nullptr);
+    k_scale<<<nbD, 256, 0, s>>>(u, nrm, D);
+    QSD_LAUNCH_CHECK();
+}
+
+bool LanczosJob::converged(double tol) const {
+    double theta, est, hb;
+    int n;
+    read(theta, est, hb, n);
+    const double at = std::max(std::fabs(theta), 1e-300);
+    return est <= tol * at || hb <= 1e-13 * at;
+}
+
+// ---------------------------------------------------------------- residual
+void ResidJob::init(qsd_ctx c, int64_t Dn, cudaStream_t st, bool stream_ordered) {
+    ctx = c;
+    D = Dn;
+    s = st;
+    B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
+    if (stream_ordered) {
+        hu.alloc_async((size_t)D * 8, s);
+        r.alloc_async((size_t)D * 8, s);
+        part.alloc_async((size_t)2 * B * 8 + 64, s);
+    } else {
+        hu.alloc((size_t)D * 8);
+        r.alloc((size_t)D * 8);
+        part.alloc((size_t)2 * B * 8 + 64);
+    }
+    if (!hpin) QSD_CUDA(cudaMallocHost(&hpin, 4 * sizeof(double)));
+}
+
+ResidJob::~ResidJob() {
+    if (hpin && own_pin) cudaFreeHost(hpin);
+}
+
+// hpin = [u^T H u, u^T u, |H u - theta u|]
+void ResidJob::enqueue(qsd_op op, qsd_sub sub, const double *diag, const double *u) {
+    double *p = part.as<double>(), *sc = p + 2 * B;
+    apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu.as<double>(), s);
+    k_dot_partial<<<B, kLanczosThreads, 0, s>>>(u, hu.as<double>(), D, p);
+    k_sum<<<1, kLanczosThreads, 0, s>>>(p, B, sc);
+    k_dot_partial<<<B, kLanczosThreads, 0, s>>>(u, u, D, p + B);
+    k_sum<<<1, kLanczosThreads, 0, s>>>(p + B, B, sc + 1);
+    k_residual<<<blocks_for(D, 256), 256, 0, s>>>(hu.as<double>(), u, sc, D, r.as<double>());
+    k_sq_partial<<<B, kLanczosThreads, 0, s>>>(r.as<double>(), D, p);
+    k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(p, B, sc + 2, nullptr);
+    QSD_LAUNCH_CHECK();
+    QSD_CUDA(cudaMemcpyAsync(hpin, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+void ResidJob::read(double &theta, double &resid_rel) const {
+    theta = hpin[0] / hpin[1];
+    resid_rel = hpin[2] / std::sqrt(hpin[1]) / std::max(std::fabs(theta), 1e-300);
+}
 
 void rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const double *u, double *out) {
     cudaStream_t s = ctx->stream;
@@ -437,97 +516,104 @@ void rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, 
     const int B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
     double *hu = static_cast<double *>(ctx->scratch[2].get((size_t)D * 8));
     double *part = static_cast<double *>(ctx->scratch[3].get((size_t)4 * 2048 * 8));
-    double *scal = part + 3 * 2048;
+    double *sc = part + 3 * 2048;
     apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu, s);
-    k_dot_partial<<<B, kRedThreads, 0, s>>>(u, hu, D, part);
-    k_sum<<<1, kRedThreads, 0, s>>>(part, B, scal);            // u^T H u
-    k_dot_partial<<<B, kRedThreads, 0, s>>>(u, u, D, part + 2048);
-    k_sum<<<1, kRedThreads, 0, s>>>(part + 2048, B, scal + 1); // u^T u
+    k_dot_partial<<<B, kLanczosThreads, 0, s>>>(u, hu, D, part);
+    k_sum<<<1, kLanczosThreads, 0, s>>>(part, B, sc);            // u^T H u
+    k_dot_partial<<<B, kLanczosThreads, 0, s>>>(u, u, D, part + 2048);
+    k_sum<<<1, kLanczosThreads, 0, s>>>(part + 2048, B, sc + 1); // u^T u
+    k_residual<<<blocks_for(D, 256), 256, 0, s>>>(hu, u, sc, D, hu);
+    k_sq_partial<<<B, kLanczosThreads, 0, s>>>(hu, D, part);
+    k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(part, B, sc + 2, nullptr);
     QSD_LAUNCH_CHECK();
-    double h[2];
-    QSD_CUDA(cudaMemcpyAsync(h, scal, 16, cudaMemcpyDeviceToHost, s));
+    double h[3];
+    QSD_CUDA(cudaMemcpyAsync(h, sc, 24, cudaMemcpyDeviceToHost, s));
     QSD_CUDA(cudaStreamSynchronize(s));
     if (!(h[1] > 0.0)) fail(QSD_ERR_INVALID_ARG, "rayleigh_quotient: u is zero");
-    const double theta = h[0] / h[1];
-    QSD_CUDA(cudaMemcpyAsync(scal + 2, &theta, 8, cudaMemcpyHostToDevice, s));
-    // r = H u - theta u, |r|^2
-    k_axpy_res<<<blocks_for(D, 256), 256, 0, s>>>(hu, u, scal + 2, D, hu);
-    k_sq_partial<<<B, kRedThreads, 0, s>>>(hu, D, part);
-    k_sqrt_sum<<<1, kRedThreads, 0, s>>>(part, B, scal + 3);
-    QSD_LAUNCH_CHECK();
-    double rn = 0.0;
-    QSD_CUDA(cudaMemcpyAsync(&rn, scal + 3, 8, cudaMemcpyDeviceToHost, s));
-    QSD_CUDA(cudaStreamSynchronize(s));
-    out[0] = theta;
-    out[1] = rn / std::sqrt(h[1]);
+    out[0] = h[0] / h[1];
+    out[1] = h[2] / std::sqrt(h[1]);
     out[2] = h[1];
 }
 
+// ---------------------------------------------------------------- driver
 int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_params &p, double *energy,
                          double *vec_out, qsd_lanczos_info *info) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool has_deadline = p.time_limit_s > 0.0;
     const auto deadline = t0 + std::chrono::microseconds((int64_t)(p.time_limit_s * 1e6));
+    auto late = [&]() { return has_deadline && std::chrono::steady_clock::now() > deadline; };
     Binding *bind = get_binding(ctx, op, sub);
     const double *diag = bind->diag.as<double>();
+    cudaStream_t s = ctx->stream;
     const int64_t D = sub->D;
     const bool mixed = p.precision != QSD_FP64;
-    // the tridiagonal CTA keeps 8 m doubles in shared memory (<= 48 KB)
-    const int m = (int)std::min<int64_t>(std::min(p.max_steps, kMaxSteps), D);
     const double tol = p.tol > 0 ? p.tol : 1e-9;
-    int applies = 0;
-    DevBuf u((size_t)D * 8), hu((size_t)D * 8), r((size_t)D * 8);
-    LanczosResult res;
-    int total_steps = 0, restarts = 0;
-    double e_unrefined = 0.0;
-    Krylov K;
-    {
-        alloc_krylov(ctx, K, D, m, mixed);
-        // the FP32 phase stops where FP32 round-off limits the estimate
-        const double phase_tol = mixed ? std::max(tol, 1e-5) : tol;
-        if (mixed)
-            res = run_lanczos<float>(ctx, op, sub, diag, K, p.v0, p.seed, m, phase_tol, p.check_every, u.as<double>(),
-                                     deadline, has_deadline, &applies, p.precision);
-        else
-            res = run_lanczos<double>(ctx, op, sub, diag, K, p.v0, p.seed, m, phase_tol, p.check_every,
-                                      u.as<double>(), deadline, has_deadline, &applies);
-        total_steps += res.steps;
+    const bool graphs = p.use_graphs != 0;
+    int applies = 0, total_steps = 0, restarts = 0;
+    bool timeout = false;
+    DevBuf u((size_t)D * 8);
+    ResidJob R;
+    R.init(ctx, D, s, false);
+
+    // main phase: FP64, or FP32 until FP32 round-off limits the estimate
+    LanczosJob J;
+    J.init(ctx, op, sub, diag, p.precision, p.max_steps, p.check_every, s, false);
+    const double phase_tol = mixed ? std::max(tol, 1e-5) : tol;
+    J.enqueue_start(p.v0, p.seed);
+    while (J.steps_done < J.m) {
+        J.enqueue_chunk(graphs);
+        QSD_CUDA(cudaStreamSynchronize(s));
+        if (J.converged(phase_tol)) break;
+        if (late()) { timeout = true; break; }
     }
-    e_unrefined = res.theta;
-    auto rq = fp64_residual(ctx, op, sub, diag, u.as<double>(), hu.as<double>(), r.as<double>(), K.partial.as<double>(),
-                            K.B, K.scal.as<double>(), &applies);
-    double theta = mixed ? rq.first : res.theta;
-    double resid = rq.second / std::max(std::fabs(rq.first), 1e-300);
-    bool converged = resid <= tol || (res.converged && !mixed && res.est <= tol * std::fabs(res.theta));
-    if (mixed) {
+    double theta, est, hb;
+    int nvec;
+    J.read(theta, est, hb, nvec);
+    total_steps += J.steps_done;
+    applies += J.steps_done;
+    const double e_unrefined = theta;
+    const bool main_converged = J.converged(tol);
+    J.enqueue_ritz(u.as<double>());
+    R.enqueue(op, sub, diag, u.as<double>());
+    ++applies;
+    QSD_CUDA(cudaStreamSynchronize(s));
+    double rq, resid;
+    R.read(rq, resid);
+    double result = mixed ? rq : theta;
+    bool converged = resid <= tol || (!mixed && main_converged);
+    if (mixed && !converged && !timeout) {
         // FP64 restarts from the current Ritz vector
-        Krylov K64;
-        const int ms = (int)std::min<int64_t>(std::min(std::max(p.refine_steps, 2), kMaxSteps), D);
-        alloc_krylov(ctx, K64, D, ms, false);
-        double prev = theta;
+        LanczosJob K;
+        K.init(ctx, op, sub, diag, QSD_FP64, std::max(p.refine_steps, 2), p.check_every, s, false);
+        double prev = rq;
         const double rtol = p.refine_tol > 0 ? p.refine_tol : 1e-10;
+        DevBuf start((size_t)D * 8);
         while (!converged && restarts < std::max(p.max_refine, 0)) {
-            if (has_deadline && std::chrono::steady_clock::now() > deadline) { res.timeout = true; break; }
-            QSD_CUDA(cudaMemcpyAsync(r.p, u.p, (size_t)D * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-            LanczosResult rr = run_lanczos<double>(ctx, op, sub, diag, K64, r.as<double>(), p.seed, ms, tol,
-                                                   std::min(p.check_every, ms), u.as<double>(), deadline,
-                                                   has_deadline, &applies);
-            total_steps += rr.steps;
+            if (late()) { timeout = true; break; }
+            QSD_CUDA(cudaMemcpyAsync(start.p, u.p, (size_t)D * 8, cudaMemcpyDeviceToDevice, s));
+            K.enqueue_start(start.as<double>(), p.seed);
+            while (K.steps_done < K.m) {
+                K.enqueue_chunk(graphs);
+                QSD_CUDA(cudaStreamSynchronize(s));
+                if (K.converged(tol)) break;
+            }
+            total_steps += K.steps_done;
+            applies += K.steps_done;
+            K.enqueue_ritz(u.as<double>());
+            R.enqueue(op, sub, diag, u.as<double>());
+            ++applies;
+            QSD_CUDA(cudaStreamSynchronize(s));
             ++restarts;
-            rq = fp64_residual(ctx, op, sub, diag, u.as<double>(), hu.as<double>(), r.as<double>(),
-                               K64.partial.as<double>(), K64.B, K64.scal.as<double>(), &applies);
-            theta = rq.first;
-            resid = rq.second / std::max(std::fabs(theta), 1e-300);
-            const double change = std::fabs(theta - prev) / std::max(std::fabs(theta), 1e-300);
-            prev = theta;
+            R.read(rq, resid);
+            result = rq;
+            const double change = std::fabs(rq - prev) / std::max(std::fabs(rq), 1e-300);
+            prev = rq;
             if (resid <= tol || change <= rtol) converged = true;
         }
-    } else if (!converged) {
-        converged = res.converged;
     }
-    *energy = theta;
-    if (vec_out) QSD_CUDA(cudaMemcpyAsync(vec_out, u.p, (size_t)D * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-    QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    *energy = result;
+    if (vec_out) QSD_CUDA(cudaMemcpyAsync(vec_out, u.p, (size_t)D * 8, cudaMemcpyDeviceToDevice, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
     if (info) {
         info->steps = total_steps;
         info->refine_restarts = restarts;
@@ -536,7 +622,7 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
         info->applies = applies;
     }
     if (take_device_error(ctx)) fail(QSD_ERR_INTERNAL, "lanczos: hash probe exceeded the table size");
-    if (res.timeout) return QSD_ERR_TIMEOUT;
+    if (timeout) return QSD_ERR_TIMEOUT;
     return converged ? QSD_OK : QSD_ERR_NOT_CONVERGED;
 }
 

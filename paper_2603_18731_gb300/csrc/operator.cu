@@ -670,9 +670,13 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
 }
 
 void compute_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d) {
+    compute_diagonal_on(ctx, op, sub, d, ctx->stream);
+}
+
+void compute_diagonal_on(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d, cudaStream_t s) {
+    (void)ctx;
     const int64_t D = sub->D;
     if (D <= 0) return;
-    cudaStream_t s = ctx->stream;
     const int nb = blocks_for(D, 256);
     const uint64_t *P = op->dP.as<uint64_t>(), *V = op->dV.as<uint64_t>(), *Z = op->dZ.as<uint64_t>();
     const double *phi = op->dphi.as<double>();

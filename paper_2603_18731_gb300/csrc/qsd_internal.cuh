@@ -39,21 +39,33 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 #define QSD_LAUNCH_CHECK() ::qsd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
 
 // ------------------------------------------------------------------ memory
-// Owning device allocation.  Allocation failure throws QSD_ERR_OOM.
+// Owning device allocation.  Allocation failure throws QSD_ERR_OOM.  With a
+// stream the memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on
+// that stream), so allocating or freeing never synchronises the device.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool async = false;
     DevBuf() = default;
     explicit DevBuf(size_t n) { alloc(n); }
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), stream(o.stream), async(o.async) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
     DevBuf &operator=(DevBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; stream = o.stream; async = o.async;
+            o.p = nullptr; o.bytes = 0;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
     void alloc(size_t n);
+    void alloc_async(size_t n, cudaStream_t s);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
@@ -340,6 +352,7 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
 Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub);
 void drop_bindings(qsd_ctx ctx, const void *handle);
 void compute_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d);
+void compute_diagonal_on(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d, cudaStream_t s);
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k,
              const void *x, void *y, cudaStream_t stream);
 void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out);

@@ -1,0 +1,92 @@
+"""GPU tests of the continuous-batching server: requests of different
+Hamiltonians and subspace sizes run concurrently and each result equals the
+same request solved alone and the oracle's ground energy; admission respects
+the memory budget; cancellation and submit-time errors."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2603_18731_gb300 as q
+    c = q.create(0)
+    yield c
+    c.close()
+
+
+def _mix(ctx):
+    """(name, operator handle, subspace handle, oracle energy) for a mix of
+    families and sizes."""
+    cases = []
+    op = wl.tfim_chain(12, g=1.0)
+    cases.append(("tfim12", op, wl.full_space(12), -2.0 / math.sin(math.pi / 24)))
+    for seed, cnt in ((5, 2000), (7, 800)):
+        op = wl.xxz_square(4, 4)
+        words = wl.xxz_walk_subspace(4, 4, count=cnt, max_len=8, seed=seed)
+        cases.append((f"xxz{cnt}", op, words, oracle.ground_energy(op, oracle.sort_unique(words))))
+    h1, eri = wl.chem_integrals(4, seed=5)
+    op = wl.jordan_wigner(wl.molecular_fermionic(h1, eri))
+    alpha = [v for v in range(16) if bin(v).count("1") == 2]
+    words = wl.product_subspace(alpha, alpha, 4)
+    cases.append(("chem4", op, words, oracle.ground_energy(op, oracle.sort_unique(words))))
+    op = wl.ising_heavy_hex(20, seed=3)
+    words = wl.flip_subspace(20, 3000, max_flips=6, seed=3)
+    cases.append(("ising20", op, words, oracle.ground_energy(op, oracle.sort_unique(words))))
+    out = []
+    for name, op, words, e in cases:
+        out.append((name, ctx.load_operator(op), ctx.build_subspace(op.n_qubits, words), e))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_server_mix_equals_alone_and_oracle(ctx, precision):
+    import paper_2603_18731_gb300 as q
+    cases = _mix(ctx)
+    params = dict(precision=precision, max_steps=300, tol=1e-10)
+    alone = {}
+    for name, h, sub, _ in cases:
+        alone[name] = ctx.lanczos_ground_state(h, sub, **params)[0]
+    with q.Server(ctx, budget_bytes=1 << 30, max_active=4) as srv:
+        tickets = [(name, srv.submit(h, sub, **params), e) for name, h, sub, e in cases for _ in range(2)]
+        for name, t, e_ref in tickets:
+            r = srv.wait(t, timeout_s=120)
+            assert r["status"] == "OK", (name, r)
+            tol = 1e-10 if precision == 0 else 1e-7
+            assert abs(r["energy"] - e_ref) <= tol * abs(e_ref), (name, r["energy"], e_ref)
+            assert abs(r["energy"] - alone[name]) <= 1e-12 * abs(e_ref), (name, r["energy"], alone[name])
+            assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        st = srv.stats()
+        assert st["completed"] == len(tickets) and st["failed"] == 0
+
+
+def test_server_budget_and_cancel(ctx):
+    import paper_2603_18731_gb300 as q
+    cases = _mix(ctx)
+    name, h, sub, e_ref = cases[1]  # xxz2000
+    with q.Server(ctx, budget_bytes=12 << 20, max_active=8) as srv:
+        tickets = [srv.submit(h, sub, max_steps=300, tol=1e-10) for _ in range(6)]
+        victim = srv.submit(h, sub, max_steps=300, tol=1e-10)
+        srv.cancel(victim)
+        for t in tickets:
+            r = srv.wait(t, timeout_s=120)
+            assert r["status"] == "OK" and abs(r["energy"] - e_ref) <= 1e-10 * abs(e_ref)
+        assert srv.wait(victim, timeout_s=120)["status"] in ("CANCELLED", "OK")
+        st = srv.stats()
+        assert st["peak_bytes"] <= st["budget_bytes"]
+
+
+def test_server_rejects_bad_requests(ctx):
+    import paper_2603_18731_gb300 as q
+    nonherm = ctx.load_operator(wl.QubitOperator.from_terms(3, [(1.0, [(0, "+")])]))
+    sub = ctx.build_subspace(3, wl.full_space(3))
+    with q.Server(ctx, budget_bytes=1 << 28, max_active=2) as srv:
+        with pytest.raises(q.QsdError) as e:
+            srv.submit(nonherm, sub)
+        assert e.value.status == "NOT_HERMITIAN"
