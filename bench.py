@@ -262,6 +262,10 @@ def run_gpu(args):
             solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "steps": inf["steps"],
                            "applies": inf["applies"], "residual": inf["residual"], "status": inf["status"]}
 
+    serve = None
+    if not args.no_serve:
+        serve = run_serve(args, q, local)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(op, words, G, target_seconds=args.cpu_seconds)
@@ -274,7 +278,7 @@ def run_gpu(args):
                        "k": 1, "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "variants": variants, "solve": solve,
+            "clocks": clk.summary(), "variants": variants, "solve": solve, "serve": serve,
             "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
         }
         print(json.dumps(line))
@@ -282,6 +286,115 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ serving
+def serve_pool(n_pool: int, seed: int, dmin: float, dmax: float):
+    """Workloads for the served stream: the three families, each with fresh
+    seeds and a log-uniform target dimension.  Host generation only; each
+    request does its own device build (sort, dedup, hash, grouping)."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    ferm_ops = {}
+    for i in range(n_pool):
+        fam = ("ising", "xxz", "fermion")[i % 3]
+        s_ = int(rng.integers(1, 1 << 30))
+        target = int(np.exp(rng.uniform(np.log(dmin), np.log(dmax))))
+        if fam == "ising":
+            op = wl.ising_heavy_hex(200, seed=s_ % 1000)
+            words = wl.flip_words(200, target, 20, s_)
+        elif fam == "xxz":
+            op = wl.xxz_square(6, 6)
+            words = wl.xxz_walk_words(6, 6, target, 12, s_)
+        else:
+            n_orb, ne = 8, 4
+            key = s_ % 4
+            if key not in ferm_ops:
+                h1, eri = wl.chem_integrals(n_orb, seed=1000 + key)
+                ferm_ops[key] = wl.molecular_qubit_operator(h1, eri)
+            op = ferm_ops[key]
+            side = int(min(70, max(2, round(np.sqrt(target)))))
+            alpha = wl.excitation_strings(n_orb, ne, side, 4, s_)
+            beta = wl.excitation_strings(n_orb, ne, side, 4, s_ + 1)
+            words = wl.product_subspace(alpha, beta, n_orb)
+        pool.append((fam, op, words))
+    return pool
+
+
+def run_serve(args, q, local):
+    """512 Poisson arrivals at 0.8x the measured closed-loop capacity; latency
+    from arrival to energy ready, including the request's device build."""
+    import torch
+    rng = np.random.default_rng(args.serve_seed)
+    pool = serve_pool(args.serve_pool, args.serve_seed, 1e3, 2e6)
+    client = q.create(local)
+    srvctx = q.create(local)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    params = dict(precision=q.QSD_FP32_DOT2, max_steps=300, tol=1e-7, check_every=10)
+    handles = []
+
+    def build(i):
+        fam, op, words = pool[i]
+        h = client.load_operator(op)
+        sub = client.build_subspace(op.n_qubits, words)
+        handles.append((h, sub))
+        return h, sub
+
+    def run(order, arrivals, srv, host_t0):
+        tickets = [None] * len(order)
+        t_arr = [0.0] * len(order)
+        start = time.perf_counter()
+
+        def feeder():
+            for k, i in enumerate(order):
+                delay = start + arrivals[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                t_arr[k] = time.perf_counter()
+                h, sub = build(i)
+                tickets[k] = srv.submit(h, sub, **params)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = []
+        for k, t in enumerate(tickets):
+            r = srv.wait(t)
+            r["latency_s"] = host_t0 + r["t_done"] - t_arr[k]
+            r["family"] = pool[order[k]][0]
+            res.append(r)
+        wall = time.perf_counter() - start
+        return res, wall
+
+    with q.Server(srvctx, budget_bytes=budget, max_active=args.serve_slots) as srv:
+        host_t0 = time.perf_counter()
+        # closed-loop capacity: every pool item submitted at once
+        burst, t_burst = run(list(range(len(pool))), [0.0] * len(pool), srv, host_t0)
+        capacity = len(pool) / t_burst
+        lam = 0.8 * capacity
+        n = args.serve_requests
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n)).tolist()
+        order = rng.integers(0, len(pool), size=n).tolist()
+        res, wall = run(order, arrivals, srv, host_t0)
+        st = srv.stats()
+    lat = np.array([r["latency_s"] for r in res]) * 1e3
+    ok = [r for r in res if r["status"] == "OK"]
+    fams = {}
+    for r in res:
+        fams.setdefault(r["family"], []).append(r["latency_s"] * 1e3)
+    dims = [pool[i][2].shape[0] for i in order]
+    out = {"requests": n, "ok": len(ok), "rate_hz": lam, "closed_loop_capacity_solves_s": capacity,
+           "solves_per_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+           "max_active": args.serve_slots, "budget_bytes": budget, "peak_bytes": st["peak_bytes"],
+           "per_family_p50_ms": {k: float(np.percentile(v, 50)) for k, v in fams.items()},
+           "candidate_dims_min_max": [int(min(dims)), int(max(dims))],
+           "precision": "fp32_dot2 + fp64 refinement", "tol": params["tol"],
+           "note": "latency = arrival to energy ready, including the request's device subspace build "
+                   "and operator grouping; host synthetic generation excluded (pool of %d workloads)" % len(pool)}
+    client.close()
+    srvctx.close()
+    return out
 
 
 # ------------------------------------------------------------------ CPU arm
@@ -362,6 +475,12 @@ def main():
     ap.add_argument("--solve-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=2.0)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-pool", type=int, default=36)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-seed", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

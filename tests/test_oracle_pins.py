@@ -222,6 +222,14 @@ def test_jordan_wigner_matches_second_quantisation(seed):
     np.testing.assert_allclose(brute.full_matrix(qop), fermion.dense(fop), atol=1e-13)
 
 
+@pytest.mark.parametrize("n_orb,seed", [(2, 0), (3, 1), (4, 2)])
+def test_vectorised_jordan_wigner_matches_second_quantisation(n_orb, seed):
+    h1, eri = wl.chem_integrals(n_orb, seed=seed)
+    fop = wl.molecular_fermionic(h1, eri)
+    qop = wl.molecular_qubit_operator(h1, eri)
+    np.testing.assert_allclose(brute.full_matrix(qop), fermion.dense(fop), atol=1e-13)
+
+
 def test_hubbard_dimer_closed_form():
     t, U = 1.0, 3.0
     h = np.array([[0.0, -t], [-t, 0.0]])

@@ -355,6 +355,49 @@ def flip_subspace(n: int, count: int, max_flips: int = 20, seed: int = 4) -> np.
     return np.asarray(rows, np.uint64).reshape(count, W)
 
 
+def flip_words(n: int, count: int, max_flips: int, seed: int, ref=None) -> np.ndarray:
+    """``count`` candidate strings (duplicates possible; the library drops
+    them), each the reference (seeded uniform unless given) with d ~
+    U{1..max_flips} distinct uniformly chosen bits flipped.  The d-subset is
+    drawn with Floyd's algorithm, vectorised over rows."""
+    rng = np.random.default_rng(seed)
+    W = n_words(n)
+    ref = random_subspace(n, 1, seed + 7)[0] if ref is None else np.asarray(ref, np.uint64)
+    k = min(max_flips, n)
+    out = np.empty((count, W), np.uint64)
+    chunk = 1 << 17
+    for c0 in range(0, count, chunk):
+        m = min(chunk, count - c0)
+        d = rng.integers(1, k + 1, size=m)
+        chosen = np.zeros((m, 64 * W), bool)
+        rows = np.arange(m)
+        for j in range(n - k, n):
+            act = j >= n - d
+            t = rng.integers(0, j + 1, size=m)
+            pick = np.where(chosen[rows, t], j, t)
+            chosen[rows[act], pick[act]] = True
+        flips = np.packbits(chosen, axis=1, bitorder="little").view(np.uint64)
+        out[c0:c0 + m] = ref[None, :] ^ flips
+    return out
+
+
+def xxz_walk_words(Lx: int, Ly: int, count: int, max_len: int, seed: int) -> np.ndarray:
+    """``count`` candidate strings (duplicates possible) from bond-swap walks of
+    length U{1..max_len} from the Neel state (as ``xxz_walk_subspace``,
+    without dropping duplicates).  Vectorised; Lx*Ly <= 64."""
+    bonds = np.asarray(square_lattice_bonds(Lx, Ly), np.uint64)
+    rng = np.random.default_rng(seed)
+    one = np.uint64(1)
+    state = np.full(count, np.uint64(neel_square(Lx, Ly)), np.uint64)
+    length = rng.integers(1, max_len + 1, size=count)
+    for step in range(max_len):
+        b = rng.integers(0, bonds.shape[0], size=count)
+        i, j = bonds[b, 0], bonds[b, 1]
+        flip = (((state >> i) & one) != ((state >> j) & one)) & (length > step)
+        state = np.where(flip, state ^ ((one << i) | (one << j)), state)
+    return state.reshape(-1, 1)
+
+
 # ------------------------------------------------ fermionic Hamiltonians --
 @dataclass
 class FermionicOperator:
@@ -437,6 +480,119 @@ def jordan_wigner(fop: FermionicOperator) -> QubitOperator:
         acc[key] = acc.get(key, 0.0) + scale
     terms = [(c, list(k)) for k, c in acc.items() if c != 0]
     return QubitOperator.from_terms(n, terms)
+
+
+# ---- vectorised extended-alphabet Jordan-Wigner for molecular Hamiltonians
+_MONO = ["I", "Z", "0", "1", "+", "-"]  # single-mode letters; index 6 = null
+
+
+def _monoid_table():
+    """mul[a, b] = (letter of _MAT[a] @ _MAT[b], its scale), null = 6."""
+    code = np.zeros((7, 7), np.int8)
+    sign = np.zeros((7, 7), np.float64)
+    for i, a in enumerate(_MONO):
+        for j, b in enumerate(_MONO):
+            name, sc = _classify(_MAT[a] @ _MAT[b])
+            code[i, j] = 6 if name == "null" else _MONO.index(name)
+            sign[i, j] = sc
+    code[6, :] = 6
+    code[:, 6] = 6
+    return code, sign
+
+
+def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray, n_modes: int):
+    """Extended-alphabet JW of many products of ladder operators at once.
+
+    ``modes``/``dags``: [T, L] mode indices and creation flags of T products of
+    L operators (leftmost first); ``coef``: [T].  Same algebra as
+    ``jordan_wigner`` (per qubit, the ordered product of the factors each
+    operator places there: its ladder letter on its own mode, Z below it), with
+    numpy over the T products.  Equal words are combined.  n_modes <= 64.
+    """
+    assert n_modes <= 64
+    code, sign = _monoid_table()
+    T, L = modes.shape
+    modes = modes.astype(np.int64)
+    letter = np.where(dags, 4, 5).astype(np.int8)  # "+" / "-"
+    scale = coef.astype(np.float64).copy()
+    # product on each touched qubit (one per operator position b); the scale
+    # of a qubit touched by several operators is counted once (first position)
+    prod = np.zeros((T, L), np.int8)
+    for b in range(L):
+        qb = modes[:, b]
+        p = np.zeros(T, np.int8)  # identity
+        acc = np.ones(T)
+        for a in range(L):
+            f = np.where(modes[:, a] == qb, letter[:, a], np.where(modes[:, a] > qb, 1, 0)).astype(np.int8)
+            acc = acc * sign[p, f]
+            p = code[p, f]
+        prod[:, b] = p
+        first = np.ones(T, bool)
+        for c in range(b):
+            first &= modes[:, c] != qb
+        scale = np.where(first, scale * acc, scale)
+    # drop null products
+    alive = ~np.any(prod == 6, axis=1) & (scale != 0)
+    modes, prod, scale = modes[alive], prod[alive], scale[alive]
+    T = modes.shape[0]
+    one = np.uint64(1)
+    bits = (one << modes.astype(np.uint64))
+    touched = np.zeros(T, np.uint64)
+    zstr = np.zeros(T, np.uint64)
+    for a in range(L):
+        touched |= bits[:, a]
+        zstr ^= bits[:, a] - one  # Z on every mode below operator a
+    zstr &= ~touched
+    masks = {c: np.zeros(T, np.uint64) for c in range(1, 6)}
+    for b in range(L):
+        for c in range(1, 6):
+            masks[c] |= np.where(prod[:, b] == c, bits[:, b], np.uint64(0))
+    masks[1] |= zstr
+    key = np.stack([masks[c] for c in range(1, 6)], axis=1)
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    csum = np.zeros(uniq.shape[0])
+    np.add.at(csum, inv.ravel(), scale)
+    keep = csum != 0
+    uniq, csum = uniq[keep], csum[keep]
+    # words: letters on qubits in ascending order
+    n = n_modes
+    lettermap = {1: Z, 2: P0, 3: P1, 4: RAISE, 5: LOWER}
+    mat = np.full((uniq.shape[0], n), 255, np.uint8)
+    for c in range(1, 6):
+        for q in range(n):
+            sel = (uniq[:, c - 1] >> np.uint64(q)) & one
+            mat[sel.astype(bool), q] = lettermap[c]
+    nz = mat != 255
+    counts = nz.sum(axis=1)
+    term_ptr = np.zeros(uniq.shape[0] + 1, np.int64)
+    np.cumsum(counts, out=term_ptr[1:])
+    qq = np.nonzero(nz)[1].astype(np.int32)
+    cc = mat[nz].astype(np.uint8)
+    return QubitOperator(n, term_ptr, qq, cc, csum.astype(np.complex128))
+
+
+def molecular_qubit_operator(h1: np.ndarray, eri: np.ndarray):
+    """The molecular Hamiltonian of ``molecular_fermionic`` (chemists'
+    notation, alpha orbital p -> mode p, beta -> n_orb + p) transformed with
+    ``jordan_wigner_products`` -- the fast path for larger orbital counts."""
+    n = h1.shape[0]
+    p, q = np.nonzero(h1)
+    m1, d1, c1 = [], [], []
+    for s in (0, 1):
+        m1.append(np.stack([p + s * n, q + s * n], axis=1))
+        d1.append(np.tile([True, False], (p.size, 1)))
+        c1.append(h1[p, q])
+    P, Q, R, S = np.nonzero(eri)
+    v = eri[P, Q, R, S]
+    m2, d2, c2 = [], [], []
+    for s in (0, 1):
+        for t in (0, 1):
+            m2.append(np.stack([P + s * n, R + t * n, S + t * n, Q + s * n], axis=1))
+            d2.append(np.tile([True, True, False, False], (P.size, 1)))
+            c2.append(0.5 * v)
+    op1 = jordan_wigner_products(np.concatenate(m1), np.concatenate(d1), np.concatenate(c1), 2 * n)
+    op2 = jordan_wigner_products(np.concatenate(m2), np.concatenate(d2), np.concatenate(c2), 2 * n)
+    return op1 + op2
 
 
 def molecular_fermionic(h1: np.ndarray, eri: np.ndarray, const: float = 0.0):
