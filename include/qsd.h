@@ -90,6 +90,8 @@ typedef struct {
     int64_t n_diag_terms;     /* diagonal terms (no flipped qubit) after combining */
     int64_t n_groups;         /* off-diagonal groups (distinct flip sets) */
     int64_t n_ladder_groups;  /* groups that use the ladder-integer table */
+    int64_t n_excitation_groups; /* ladder groups in the excitation index (0: none) */
+    int32_t n_excitation_shapes; /* distinct occupied/empty shapes of their terms */
     int64_t max_group_terms;
     int32_t is_real;          /* every matrix element is real */
     int32_t is_hermitian;     /* term set closed under adjoint (rel. 1e-14) */
@@ -150,6 +152,16 @@ int qsd_subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n,
                        const uint64_t *keys, int64_t *idx_out);
 
 int qsd_free_sub(qsd_sub sub);
+
+/* ------------------------------------------------------------------ tuning */
+#define QSD_TUNE_APPLY_PATH     1  /* 0 auto; 1 per-row scan of all groups; 2 excitation
+                                      index (ladder groups enumerated from each row's
+                                      occupation; ignored when the operator has none) */
+#define QSD_TUNE_LANES_PER_ROW  2  /* per-row scan: 0 auto, 1 or 8 lanes per row */
+
+/* Set a product-path choice on a context (later products of this context
+ * use it).  Results are identical up to summation order for every choice. */
+int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
 
 /* --------------------------------------------------------------- products */
 /* y = H_S x for k right-hand sides (Methods, "Matrix evaluation": the

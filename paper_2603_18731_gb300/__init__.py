@@ -38,7 +38,8 @@ class QsdError(RuntimeError):
 class OpInfo(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_words", C.c_int32), ("n_terms_in", C.c_int64),
                 ("n_terms", C.c_int64), ("n_diag_terms", C.c_int64), ("n_groups", C.c_int64),
-                ("n_ladder_groups", C.c_int64), ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
+                ("n_ladder_groups", C.c_int64), ("n_excitation_groups", C.c_int64),
+                ("n_excitation_shapes", C.c_int32), ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
                 ("is_hermitian", C.c_int32), ("identity_coef", C.c_double)]
 
 
@@ -78,6 +79,7 @@ SIGNATURES = [
     ("qsd_subspace_keys", C.c_int, [_P, _P, _P, C.c_int]),
     ("qsd_subspace_index", C.c_int, [_P, _P, _I64, _P, _P]),
     ("qsd_free_sub", C.c_int, [_P]),
+    ("qsd_set_tuning", C.c_int, [_P, _I32, _I64]),
     ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
     ("qsd_apply_H_host", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
     ("qsd_diagonal", C.c_int, [_P, _P, _P, _P]),
@@ -212,6 +214,11 @@ class Context:
         self.close()
 
     # -- ABI calls
+    def set_tuning(self, knob: int, value: int):
+        """knob 1: product path (0 auto, 1 group scan, 2 excitation index);
+        knob 2: lanes per row of the group scan (0 auto, 1, 8)."""
+        self._check(lib().qsd_set_tuning(self.handle, int(knob), int(value)))
+
     def load_operator(self, op) -> Operator:
         """``op``: any object with n_qubits, term_ptr, op_qubit, op_code, coef
         (complex) as numpy arrays (e.g. ``workloads.QubitOperator``)."""

@@ -4,7 +4,7 @@
 #include <chrono>
 #include <cstring>
 
-#include "apply_kernel.cuh"
+#include "excite.cuh"
 #include "qsd_internal.cuh"
 
 namespace qsd {
@@ -149,8 +149,18 @@ void drop_bindings(qsd_ctx ctx, const void *handle) {
 // Lanes per row: a lane per row once the rows fill the GPU; 8 lanes per row
 // for small subspaces with enough groups to share.
 static int choose_lanes(qsd_ctx ctx, int64_t D, int64_t G) {
+    if (ctx->tune_lanes == 1 || ctx->tune_lanes == 8) return ctx->tune_lanes;
     const int64_t slots = (int64_t)ctx->num_sms * 2048;
     return (D < slots / 2 && G >= 16) ? 8 : 1;
+}
+
+// Excitation path when a row reaches far fewer candidate flip masks than the
+// operator has groups (the per-row scan visits every group).
+static bool use_excitation(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    if (!op->exc_ok || ctx->tune_mode == 1) return false;
+    if (ctx->tune_mode == 2) return true;
+    const double cand = excitation_candidates(op, sub);
+    return cand >= 0.0 && 4.0 * cand < (double)op->G;
 }
 
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
@@ -182,10 +192,30 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     p.err = ctx->d_err;
     p.num_sms = ctx->num_sms;
     const int R = choose_lanes(ctx, sub->D, op->G);
+    const bool exc = use_excitation(ctx, op, sub);
+    ExcParams e{};
+    if (exc) {
+        e.ght = HashView{op->gtags.as<uint16_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
+                         (uint64_t)op->g_nbuckets - 1, op->g_shift};
+        e.exc_gid = op->exc_gid.as<int32_t>();
+        e.rest_gid = op->rest_gid.as<int32_t>();
+        e.n_rest = op->G_rest;
+        e.split = op->exc_split;
+        e.n_qubits = op->n_qubits;
+        e.n_shapes = op->n_shapes;
+        for (int i = 0; i < op->n_shapes; ++i) e.shapes[i] = op->shapes[i];
+    }
     int64_t c = 0;
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
         p.col0 = c;
+        if (exc) {
+            if (precision == QSD_FP64) launch_apply_exc<QSD_FP64>(p, e, op->W, KB, stream);
+            else if (precision == QSD_FP32_MIXED) launch_apply_exc<QSD_FP32_MIXED>(p, e, op->W, KB, stream);
+            else launch_apply_exc<QSD_FP32_DOT2>(p, e, op->W, KB, stream);
+            c += KB;
+            continue;
+        }
         if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, op->W, R, KB, stream);
         else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, op->W, R, KB, stream);
         else launch_apply<QSD_FP32_DOT2>(p, op->W, R, KB, stream);
@@ -491,6 +521,23 @@ int qsd_rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *u, 
         Binding *b = get_binding(ctx, op, sub);
         rayleigh_quotient(ctx, op, sub, b->diag.as<double>(), u, out);
     });
+}
+
+int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    switch (knob) {
+    case QSD_TUNE_APPLY_PATH:
+        if (value < 0 || value > 2) return QSD_ERR_INVALID_ARG;
+        ctx->tune_mode = (int)value;
+        return QSD_OK;
+    case QSD_TUNE_LANES_PER_ROW:
+        if (value != 0 && value != 1 && value != 8) return QSD_ERR_INVALID_ARG;
+        ctx->tune_lanes = (int)value;
+        return QSD_OK;
+    default:
+        return QSD_ERR_INVALID_ARG;
+    }
 }
 
 void qsd_lanczos_default_params(qsd_lanczos_params *p) {

@@ -31,6 +31,17 @@ namespace qsd {
 constexpr int kTableBitsMax = 5;
 constexpr uint32_t kGroupScan = 0x80u;
 
+// Groups per batch (bucket loads in flight per lane) and the minimum resident
+// blocks of 256 threads per SM asked of the compiler, per key width W, for the
+// k = 1 kernels (measured on GB300: one-word keys run best at full occupancy
+// with one lookup in flight per lane; four-word keys, whose rows hold more
+// registers, with two lookups in flight at half occupancy).  k > 1 kernels
+// keep two lookups in flight and their register budget.
+template <int W, int KB> struct ApplyShape {
+    static constexpr int U = (KB == 1 && W == 1) ? 1 : 2;
+    static constexpr int MINB = KB == 1 ? (W == 1 ? 8 : 4) : 1;
+};
+
 // 32-byte group record, one per off-diagonal group
 struct __align__(16) GroupRec {
     uint64_t hF;    // prehash of the flip mask F
@@ -141,7 +152,7 @@ __device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e
 template <int W, int R, int KB, int PREC>
 __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t row) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
-    constexpr int U = 4;
+    constexpr int U = ApplyShape<W, KB>::U;
     const int sub = threadIdx.x % R;
     const bool active = row < p.D;
     const int64_t r = active ? row : p.D - 1;
@@ -278,7 +289,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
 
 // One launch covers all rows: R lanes per row, rows past D inactive.
 template <int W, int R, int KB, int PREC>
-__global__ void __launch_bounds__(256, KB == 1 ? 3 : 1) k_apply(const ApplyParams p) {
+__global__ void __launch_bounds__(256, (ApplyShape<W, KB>::MINB)) k_apply(const ApplyParams p) {
     apply_row<W, R, KB, PREC>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
 }
 

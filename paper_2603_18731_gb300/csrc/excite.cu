@@ -1,0 +1,128 @@
+// Excitation index of an operator's ladder groups (built at load time).
+//
+// The paper rejects groups whose ladder integer has no term before any lookup
+// (Methods, "Fermionic Hamiltonians", Fig. 3b) and names bulk rejection of
+// groups as future work (Discussion).  Here a row does not visit the groups
+// at all: a ladder term is nonzero only where its raising qubits are occupied
+// and its lowering qubits empty, so a row enumerates exactly the flip masks of
+// that form -- its single and double "excitations" per shape of the operator --
+// and finds their groups in a hash table keyed by the flip mask.
+#include <algorithm>
+#include <set>
+
+#include "excite.cuh"
+
+namespace qsd {
+
+namespace {
+
+// Shape of each term (0xffffffff: not indexable), see excite.cuh.
+__global__ void k_term_shapes(int W, int64_t G, const int32_t *__restrict__ grange, const uint64_t *__restrict__ gF,
+                              int64_t T, const uint64_t *__restrict__ tP, const uint64_t *__restrict__ tV, int split,
+                              uint32_t *shape) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    for (int32_t t = grange[g]; t < grange[g + 1]; ++t) {
+        int c[4] = {0, 0, 0, 0};
+        bool ladder = true;
+        for (int w = 0; w < W; ++w) {
+            const uint64_t F = gF[(size_t)w * G + g], P = tP[(size_t)w * T + t], V = tV[(size_t)w * T + t];
+            ladder &= (P & F) == F;
+            // sector masks of this word
+            uint64_t s0 = 0;
+            const int lo = 64 * w;
+            if (split >= lo + 64) s0 = ~0ull;
+            else if (split > lo) s0 = (1ull << (split - lo)) - 1;
+            c[0] += __popcll(V & F & s0);
+            c[1] += __popcll(F & ~V & s0);
+            c[2] += __popcll(V & F & ~s0);
+            c[3] += __popcll(F & ~V & ~s0);
+        }
+        const bool ok = ladder && c[0] <= 2 && c[1] <= 2 && c[2] <= 2 && c[3] <= 2;
+        shape[t] = ok ? (uint32_t)(c[0] | (c[1] << 4) | (c[2] << 8) | (c[3] << 12)) : 0xffffffffu;
+    }
+}
+
+__global__ void k_gather_exc(int W, int64_t G, const int32_t *__restrict__ ids, int64_t n,
+                             const uint64_t *__restrict__ gF, uint64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t g = ids[i];
+    for (int w = 0; w < W; ++w) out[(size_t)w * n + i] = gF[(size_t)w * G + g];
+}
+
+int64_t choose_h(int64_t m, int k) { return k == 0 ? 1 : (k == 1 ? m : m * (m - 1) / 2); }
+
+}  // namespace
+
+void build_excitation_index(qsd_ctx ctx, qsd_op op) {
+    op->exc_ok = false;
+    const int W = op->W;
+    const int64_t G = op->G, T = op->T;
+    if (G == 0 || W > kMaxWordsStatic) return;
+    cudaStream_t s = ctx->stream;
+    op->exc_split = op->n_qubits / 2;
+    DevBuf shape((size_t)T * 4);
+    k_term_shapes<<<blocks_for(G, 128), 128, 0, s>>>(W, G, op->grange.as<int32_t>(), op->gF.as<uint64_t>(), T,
+                                                     op->tP.as<uint64_t>(), op->tV.as<uint64_t>(), op->exc_split,
+                                                     shape.as<uint32_t>());
+    QSD_LAUNCH_CHECK();
+    std::vector<uint32_t> hs(T);
+    std::vector<int32_t> gr(G + 1);
+    QSD_CUDA(cudaMemcpyAsync(hs.data(), shape.p, (size_t)T * 4, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(gr.data(), op->grange.p, (size_t)(G + 1) * 4, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> exc, rest;
+    std::set<uint32_t> shapes;
+    for (int64_t g = 0; g < G; ++g) {
+        bool ok = true;
+        for (int32_t t = gr[g]; t < gr[g + 1] && ok; ++t) ok = hs[t] != 0xffffffffu;
+        if (ok) {
+            exc.push_back((int32_t)g);
+            for (int32_t t = gr[g]; t < gr[g + 1]; ++t) shapes.insert(hs[t]);
+        } else {
+            rest.push_back((int32_t)g);
+        }
+    }
+    if (exc.empty() || shapes.size() > (size_t)kMaxShapes) return;
+    op->n_shapes = 0;
+    for (uint32_t v : shapes) op->shapes[op->n_shapes++] = v;
+    op->G_exc = (int64_t)exc.size();
+    op->G_rest = (int64_t)rest.size();
+    op->exc_gid.alloc(exc.size() * 4);
+    op->rest_gid.alloc(std::max<size_t>(rest.size(), 1) * 4);
+    QSD_CUDA(cudaMemcpyAsync(op->exc_gid.p, exc.data(), exc.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!rest.empty())
+        QSD_CUDA(cudaMemcpyAsync(op->rest_gid.p, rest.data(), rest.size() * 4, cudaMemcpyHostToDevice, s));
+    op->excF.alloc((size_t)W * op->G_exc * 8);
+    k_gather_exc<<<blocks_for(op->G_exc, 256), 256, 0, s>>>(W, G, op->exc_gid.as<int32_t>(), op->G_exc,
+                                                           op->gF.as<uint64_t>(), op->excF.as<uint64_t>());
+    QSD_LAUNCH_CHECK();
+    HashTable t = build_hash(ctx, op->excF.as<uint64_t>(), W, op->G_exc);
+    op->gtags = std::move(t.tags);
+    op->gsidx = std::move(t.sidx);
+    op->g_nbuckets = t.n_buckets;
+    op->g_shift = t.shift;
+    QSD_CUDA(cudaStreamSynchronize(s));
+    op->exc_ok = true;
+}
+
+double excitation_candidates(qsd_op op, qsd_sub sub) {
+    if (!op->exc_ok || sub->key0.empty()) return -1.0;
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (int q = 0; q < op->n_qubits; ++q) {
+        const bool occ = (sub->key0[q >> 6] >> (q & 63)) & 1;
+        const int sct = q < op->exc_split ? 0 : 1;
+        cnt[2 * sct + (occ ? 0 : 1)]++;
+    }
+    double total = 0.0;
+    for (int i = 0; i < op->n_shapes; ++i) {
+        const uint32_t sh = op->shapes[i];
+        double n = 1.0;
+        for (int j = 0; j < 4; ++j) n *= (double)choose_h(cnt[j], (int)((sh >> (4 * j)) & 15));
+        total += n;
+    }
+    return total + (double)op->G_rest;
+}
+
+}  // namespace qsd

@@ -1,0 +1,173 @@
+// Warp-per-row excitation product (included by the apply_exc_p*.cu units).
+//
+// Per row (one warp): the occupied and empty qubits of each sector are listed
+// in shared memory; for every shape of the operator's ladder terms, the lanes
+// split the product of combinations "k occupied of sector 0 x l empty of
+// sector 0 x ..." (k, l <= 2).  Each candidate flip mask F is looked up in the
+// group hash table; a group found contributes its matrix element at the row
+// (ladder-integer term range, projector tests, Jordan-Wigner signs), and a
+// nonzero element costs one subspace lookup of r xor F.  The row's pattern on
+// F fixes the shape, so each (row, group) pair is visited at most once.
+// Groups outside the index (letters X, Y, or more than two excitations per
+// sector) are scanned by the lanes.  Lanes accumulate their own candidates in
+// a fixed order and the warp reduces with shuffles: deterministic.
+#pragma once
+
+#include "excite.cuh"
+
+namespace qsd {
+
+__device__ __forceinline__ int choose(int m, int k) { return k == 0 ? 1 : (k == 1 ? m : m * (m - 1) / 2); }
+
+// The i-th k-subset (k <= 2) of list[0..m) as qubit positions.
+__device__ __forceinline__ void unrank(int i, int k, const uint8_t *list, int &q0, int &q1) {
+    if (k == 1) {
+        q0 = list[i];
+    } else if (k == 2) {
+        int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)i)) * 0.5f);
+        while (y * (y - 1) / 2 > i) --y;
+        while ((y + 1) * y / 2 <= i) ++y;
+        const int x = i - y * (y - 1) / 2;
+        q0 = list[x];
+        q1 = list[y];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void set_bit(uint64_t (&F)[W], int q) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if ((q >> 6) == w) F[w] |= 1ull << (q & 63);
+}
+
+template <int W, int KB, int PREC>
+__global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const ExcParams e) {
+    using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
+    __shared__ uint8_t lists[8][4][64 * W];
+    __shared__ int cnt[8][4];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= p.D) return;  // warp-uniform
+    uint64_t key[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
+    const uint64_t hr = prehash<W>(key, p.nib);
+    // occupied / empty lists per sector
+    for (int sct = 0; sct < 2; ++sct) {
+        const int lo = sct ? e.split : 0, hi = sct ? e.n_qubits : e.split;
+        int no = 0, nv = 0;
+        for (int base = lo; base < hi; base += 32) {
+            const int q = base + lane;
+            const bool in = q < hi;
+            const bool occ = in && ((word_of<W>(key, q) >> (q & 63)) & 1);
+            const uint32_t bo = __ballot_sync(0xffffffffu, occ), bv = __ballot_sync(0xffffffffu, in && !occ);
+            const uint32_t lt = (1u << lane) - 1u;
+            if (occ) lists[wib][2 * sct][no + __popc(bo & lt)] = (uint8_t)q;
+            if (in && !occ) lists[wib][2 * sct + 1][nv + __popc(bv & lt)] = (uint8_t)q;
+            no += __popc(bo);
+            nv += __popc(bv);
+        }
+        if (lane == 0) {
+            cnt[wib][2 * sct] = no;
+            cnt[wib][2 * sct + 1] = nv;
+        }
+    }
+    __syncwarp();
+    const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
+    double acc[KB];
+    float as[KB], ae[KB];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) { acc[j] = 0.0; as[j] = 0.f; ae[j] = 0.f; }
+
+    auto contribute = [&](double amp, const uint64_t (&F)[W], uint64_t hF) {
+        uint64_t c[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) c[w] = key[w] ^ F[w];
+        const int64_t idx = probe<W>(c, hr ^ hF, p.hv, p.err);
+        if (idx < 0) return;
+        const TIO *xc = x + idx * p.ld + p.col0;
+        if (PREC == QSD_FP32_DOT2) {
+            const float h = (float)amp, l = (float)(amp - (double)h);
+#pragma unroll
+            for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], h, l, (float)__ldg(xc + j));
+        } else {
+#pragma unroll
+            for (int j = 0; j < KB; ++j) acc[j] = fma(amp, (double)__ldg(xc + j), acc[j]);
+        }
+    };
+
+    for (int si = 0; si < e.n_shapes; ++si) {
+        const uint32_t sh = e.shapes[si];
+        const int k[4] = {(int)(sh & 15), (int)((sh >> 4) & 15), (int)((sh >> 8) & 15), (int)((sh >> 12) & 15)};
+        int f[4];
+        int64_t N = 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            f[i] = choose(cnt[wib][i], k[i]);
+            N *= f[i];
+        }
+        for (int64_t t = lane; t < N; t += 32) {
+            int64_t rest = t;
+            uint64_t F[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) F[w] = 0;
+#pragma unroll
+            for (int i = 3; i >= 0; --i) {
+                const int id = (int)(rest % f[i]);
+                rest /= f[i];
+                int q0 = -1, q1 = -1;
+                unrank(id, k[i], lists[wib][i], q0, q1);
+                if (q0 >= 0) set_bit<W>(F, q0);
+                if (q1 >= 0) set_bit<W>(F, q1);
+            }
+            const uint64_t hF = prehash<W>(F, p.nib);
+            const int64_t ge = probe<W>(F, hF, e.ght, p.err);
+            if (ge < 0) continue;
+            const int64_t g = __ldg(e.exc_gid + ge);
+            const double amp = scan_amp<W>(p, g, key);
+            if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
+            contribute(amp, F, hF);
+        }
+    }
+    for (int64_t i = lane; i < e.n_rest; i += 32) {
+        const int64_t g = __ldg(e.rest_gid + i);
+        const double amp = scan_amp<W>(p, g, key);
+        if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
+        uint64_t F[W];
+        F[0] = __ldg(&p.grec[g].F0);
+#pragma unroll
+        for (int w = 1; w < W; ++w) F[w] = __ldg(p.gF + (size_t)w * p.G + g);
+        contribute(amp, F, __ldg(&p.grec[g].hF));
+    }
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            if (PREC == QSD_FP32_DOT2) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, as[j], o);
+                const float e2 = __shfl_xor_sync(0xffffffffu, ae[j], o);
+                dot2_merge(as[j], ae[j], s2, e2);
+            } else {
+                acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+            }
+        }
+    }
+    if (lane == 0) {
+        const double d = __ldg(p.diag + row);
+        const TIO *xr = x + row * p.ld + p.col0;
+        TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0;
+        if (PREC == QSD_FP32_DOT2) {
+            const float dh = (float)d, dl = (float)(d - (double)dh);
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
+                yr[j] = (TIO)(as[j] + ae[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
+        }
+    }
+}
+
+}  // namespace qsd

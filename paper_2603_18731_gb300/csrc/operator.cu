@@ -656,6 +656,7 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
             for (int w = 0; w < W; ++w) op->host_groups[(size_t)g * W + w] = gsoa[(size_t)w * G + g];
     }
     op->G = G;
+    build_excitation_index(ctx, op);
     qsd_op_info &I = op->info;
     I.n_qubits = n;
     I.n_words = W;
@@ -666,6 +667,8 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
     I.max_group_terms = (int64_t)h_stats[0];
     I.n_ladder_groups = (int64_t)h_stats[1];
     I.identity_coef = id_re;
+    I.n_excitation_groups = op->exc_ok ? op->G_exc : 0;
+    I.n_excitation_shapes = op->exc_ok ? op->n_shapes : 0;
     QSD_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -86,6 +86,8 @@ struct Binding;
 
 struct qsd_ctx_s {
     int device = 0;
+    int tune_mode = 0;    // product path: 0 auto, 1 per-row group scan, 2 excitation index
+    int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int num_sms = 0;
@@ -111,6 +113,7 @@ struct qsd_sub_s {
     qsd::DevBuf keys;   // uint64 [W][D]
     qsd::DevBuf tags;   // uint16 [8 * n_buckets], 0 = empty
     qsd::DevBuf sidx;   // uint32 [8 * n_buckets]
+    std::vector<uint64_t> key0;  // host copy of the first (smallest) string
 };
 
 struct qsd_op_s {
@@ -131,6 +134,17 @@ struct qsd_op_s {
     qsd::DevBuf amp;     // double [n_amp] matrix element per support pattern (table groups)
     qsd::DevBuf ampf;    // float2 [n_amp] the same split into FP32 (hi, lo)
     int64_t n_amp = 0, n_table_groups = 0;
+    // excitation index of the ladder groups (fermionic operators)
+    bool exc_ok = false;
+    int exc_split = 0, n_shapes = 0;
+    uint32_t shapes[16] = {0};
+    int64_t G_exc = 0, G_rest = 0;
+    qsd::DevBuf excF;      // uint64 [W][G_exc] flip masks of the indexed groups
+    qsd::DevBuf exc_gid;   // int32 [G_exc]
+    qsd::DevBuf rest_gid;  // int32 [G_rest]
+    qsd::DevBuf gtags, gsidx;
+    int64_t g_nbuckets = 0;
+    int g_shift = 31;
     qsd::DevBuf tP, tV, tZ;  // uint64 [W][T]
     qsd::DevBuf tphi;    // double [T] real phase * coefficient
     qsd::DevBuf tphi_im; // double [T]
@@ -342,6 +356,18 @@ int64_t unique_sorted(qsd_ctx ctx, const uint64_t *keys, int K, int64_t n, uint6
 void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_in, bool on_device);
 void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out);
 void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev);
+struct HashTable {
+    DevBuf tags, sidx;
+    int64_t n_buckets = 0;
+    int shift = 31;
+};
+// Hash table over n keys given as SoA words keys[w*n + i] (table layout of
+// the subspace index).
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n);
+void build_excitation_index(qsd_ctx ctx, qsd_op op);
+// Candidate flip masks per row of the excitation path for the subspace's
+// first string, or -1 when the operator has no excitation index.
+double excitation_candidates(qsd_op op, qsd_sub sub);
 inline HashView hash_view(qsd_sub sub) {
     return HashView{sub->tags.as<uint16_t>(), sub->sidx.as<uint32_t>(), sub->keys.as<uint64_t>(), sub->D,
                     (uint64_t)sub->n_buckets - 1, sub->bucket_shift};

@@ -141,37 +141,52 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     sub->keys.alloc((size_t)std::max<int64_t>(D, 1) * W * 8);
     if (D > 0) unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, sub->keys.as<uint64_t>(), D);
     soa.release();
+    HashTable t = build_hash(ctx, sub->keys.as<uint64_t>(), W, D);
+    sub->n_buckets = t.n_buckets;
+    sub->bucket_shift = t.shift;
+    sub->tags = std::move(t.tags);
+    sub->sidx = std::move(t.sidx);
+    sub->key0.assign(W, 0);
+    if (D > 0)
+        for (int w = 0; w < W; ++w)
+            QSD_CUDA(cudaMemcpyAsync(&sub->key0[w], sub->keys.as<uint64_t>() + (size_t)w * D, 8,
+                                     cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
+}
+
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D) {
+    cudaStream_t s = ctx->stream;
+    HashTable t;
     // load factor <= 1/4 over buckets of 8 slots: a bucket overflows into the
     // next one with probability ~1e-3, so probes almost never diverge
-    sub->n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (4 * D + kBucketSlots - 1) / kBucketSlots));
+    t.n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (4 * D + kBucketSlots - 1) / kBucketSlots));
     int lg = 0;
-    while ((1ll << lg) < sub->n_buckets) ++lg;
-    if (lg > 32) fail(QSD_ERR_CAPACITY, "build_subspace: hash table larger than 2^32 buckets");
-    sub->bucket_shift = 32 - lg;
-    const int shift = sub->bucket_shift;
-    const size_t cap = (size_t)sub->n_buckets * kBucketSlots;
-    sub->tags.alloc(cap * 2);
-    sub->sidx.alloc(cap * 4);
-    QSD_CUDA(cudaMemsetAsync(sub->tags.p, 0, cap * 2, s));
+    while ((1ll << lg) < t.n_buckets) ++lg;
+    if (lg > 32) fail(QSD_ERR_CAPACITY, "hash table larger than 2^32 buckets");
+    t.shift = 32 - lg;
+    const size_t cap = (size_t)t.n_buckets * kBucketSlots;
+    t.tags.alloc(cap * 2);
+    t.sidx.alloc(cap * 4);
+    QSD_CUDA(cudaMemsetAsync(t.tags.p, 0, cap * 2, s));
     if (D > 0) {
         QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
-        const uint64_t mask = (uint64_t)sub->n_buckets - 1;
-        auto *tg = sub->tags.as<unsigned short>();
-        auto *si = sub->sidx.as<uint32_t>();
+        const uint64_t mask = (uint64_t)t.n_buckets - 1;
+        auto *tg = t.tags.as<unsigned short>();
+        auto *si = t.sidx.as<uint32_t>();
         const uint64_t *nib = ctx->nib.as<uint64_t>();
         const int nb = blocks_for(D, 256);
-        const uint64_t *k = sub->keys.as<uint64_t>();
+        const int shift = t.shift;
         switch (W) {
-        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(k, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        default: k_hash_insert_dyn<<<nb, 256, 0, s>>>(k, W, D, nib, tg, si, mask, shift, ctx->d_err);
+        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        default: k_hash_insert_dyn<<<nb, 256, 0, s>>>(keys, W, D, nib, tg, si, mask, shift, ctx->d_err);
         }
         QSD_LAUNCH_CHECK();
-        if (take_device_error(ctx)) fail(QSD_ERR_INTERNAL, "build_subspace: hash table overflow");
+        if (take_device_error(ctx)) fail(QSD_ERR_INTERNAL, "hash table overflow");
     }
-    QSD_CUDA(cudaStreamSynchronize(s));
+    return t;
 }
 
 void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int64_t *out) {

@@ -167,6 +167,60 @@ def test_apply_deterministic_and_host_path(ctx):
     assert np.array_equal(yh, y1.cpu().numpy())
 
 
+@pytest.mark.parametrize("n_orb,na,k", [(4, 2, 1), (6, 3, 16), (7, 2, 4)])
+def test_excitation_path_matches_scan_and_oracle(ctx, n_orb, na, k):
+    import torch
+    import paper_2603_18731_gb300 as q
+    h1, eri = wl.chem_integrals(n_orb, seed=n_orb)
+    op = wl.molecular_qubit_operator(h1, eri)
+    strings = [v for v in range(1 << n_orb) if bin(v).count("1") == na]
+    words = wl.product_subspace(strings, strings, n_orb)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    info = h.info()
+    assert info["n_excitation_groups"] == info["n_groups"] and info["n_excitation_shapes"] == 5
+    sub = ctx.build_subspace(op.n_qubits, words)
+    rng = np.random.default_rng(n_orb)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    ref = oracle.apply(op, keys, x).real
+    x32 = x.astype(np.float32)
+    ref32 = oracle.apply(op, keys, x32.astype(np.float64)).real
+    outs = {}
+    for path in (1, 2):
+        ctx.set_tuning(1, path)
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        outs[path] = y.cpu().numpy()
+        assert rel_err(outs[path], ref) <= FP64_TOL, path
+        for prec in (q.QSD_FP32_MIXED, q.QSD_FP32_DOT2):
+            y32 = ctx.apply_H(h, sub, to_cuda(ctx, x32, torch.float32), precision=prec)
+            ctx.synchronize()
+            assert rel_err(y32.cpu().numpy().astype(np.float64), ref32) <= FP32_TOL, (path, prec)
+    ctx.set_tuning(1, 0)
+    assert rel_err(outs[1], outs[2]) <= FP64_TOL
+
+
+def test_excitation_path_with_rest_groups(ctx):
+    import torch
+    n = 10
+    h1, eri = wl.chem_integrals(5, seed=3)
+    op = wl.molecular_qubit_operator(h1, eri) + wl.random_extended(n, 15, max_weight=3, seed=4, letters="XYZ")
+    words = wl.random_subspace(n, 600, seed=5)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    info = h.info()
+    assert 0 < info["n_excitation_groups"] < info["n_groups"]
+    sub = ctx.build_subspace(n, words)
+    x = np.random.default_rng(1).normal(size=sub.dim)
+    ref = oracle.apply(op, keys, x).real
+    for path in (1, 2):
+        ctx.set_tuning(1, path)
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL, path
+    ctx.set_tuning(1, 0)
+
+
 # --------------------------------------------------------- integer tables
 @pytest.mark.parametrize("n,seed", [(10, 1), (70, 2), (200, 3)])
 def test_target_and_term_tables_exact(ctx, n, seed):
