@@ -56,6 +56,14 @@ def make_workload(name: str):
         op = wl.ising_heavy_hex(200, seed=4)
         words = wl.flip_subspace(200, 1_000_000, max_flips=20, seed=4)
         desc = "Ising 200 qubits heavy-hex-like graph, 1M strings = seeded reference with 1-20 bits flipped"
+    elif name == "chem":
+        h1, eri = wl.chem_integrals(32, seed=3)
+        op = wl.molecular_qubit_operator(h1, eri)
+        alpha = wl.excitation_strings(32, 8, 1500, 4, seed=3)
+        beta = wl.excitation_strings(32, 8, 1500, 4, seed=1003)
+        words = wl.product_subspace(alpha, beta, 32)
+        desc = ("fermionic 32 spatial orbitals (64 qubits, extended JW), h ~ N(0,0.1), (pq|rs) ~ N(0,0.05) "
+                "exp(-|p-q|-|r-s|), S = 1500 alpha x 1500 beta weight-8 strings (HF + 1-4 excitations), seed 3")
     else:
         raise SystemExit(f"unknown workload {name}")
     return op, words, desc
@@ -168,16 +176,24 @@ def run_gpu(args):
         xb64 = torch.as_tensor(rng.normal(size=(D, 16)), device=dev)
         xb32 = xb64.float()
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    # lookups / hits per product (integer target table, not timed)
+    # lookups / hits per product (integer target table, not timed); sampled
+    # rows, scaled to D, when the full table would exceed 2^31 entries
     lookups = hits = 0
     chunk = max(1, (1 << 27) // max(G, 1))
-    for r0 in range(0, D, chunk):
-        n = min(chunk, D - r0)
+    sampled = D * G > (1 << 31)
+    starts = (np.linspace(0, D - 1, 64).astype(int).tolist() if sampled else list(range(0, D, chunk)))
+    nrow = 0
+    for r0 in starts:
+        n = min(chunk if not sampled else max(1, (1 << 24) // max(G, 1)), D - r0)
         tt = ctx.target_table(h, sub, r0, n)
         ctx.synchronize()
         lookups += int((tt != -2).sum().item())
         hits += int((tt >= 0).sum().item())
+        nrow += n
         del tt
+    if sampled:
+        lookups = int(lookups * D / nrow)
+        hits = int(hits * D / nrow)
     ctx.synchronize()
 
     def time_variant(x, precision, steps, warmup):
@@ -202,11 +218,12 @@ def run_gpu(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         return float(np.mean(ms)), ms, wall
 
-    k1 = 1
     elems = D * (G + 1)
-    # headline: FP64, k = 1
+    # headline: FP64, k = 1 -- except the fermionic workload, whose
+    # configuration is the k = 16 block with FP32 storage and FP64 accumulation
+    head_x, head_prec, k1 = (xb32, q.QSD_FP32_MIXED, 16) if args.workload == "chem" else (x64, q.QSD_FP64, 1)
     with ClockSampler(local) as clk:
-        ms64, all64, wall64 = time_variant(x64, q.QSD_FP64, args.steps, args.warmup)
+        ms64, all64, wall64 = time_variant(head_x, head_prec, args.steps, args.warmup)
     t_max = ms64
     if dist:
         t = torch.tensor([ms64], device=dev, dtype=torch.float64)
@@ -215,17 +232,22 @@ def run_gpu(args):
     value = world * elems * k1 / (t_max * 1e-3) / 1e9
     variants = {}
     vsteps = max(3, min(args.steps, 20))
-    for name, x, prec, k in (("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp32_dot2_k1", x32, q.QSD_FP32_DOT2, 1),
-                             ("fp64_k16", xb64, q.QSD_FP64, 16), ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16),
-                             ("fp32_dot2_k16", xb32, q.QSD_FP32_DOT2, 16)):
+    vlist = [("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp32_dot2_k1", x32, q.QSD_FP32_DOT2, 1),
+             ("fp64_k16", xb64, q.QSD_FP64, 16), ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16),
+             ("fp32_dot2_k16", xb32, q.QSD_FP32_DOT2, 16)]
+    if args.workload == "chem":
+        vlist = [("fp64_k1", x64, q.QSD_FP64, 1), ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16),
+                 ("fp32_dot2_k16", xb32, q.QSD_FP32_DOT2, 16)]
+        vsteps = 3
+    for name, x, prec, k in vlist:
         m, _, _ = time_variant(x, prec, vsteps, 3)
         variants[name] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
-    fp64_1 = elems / (ms64 * 1e-3) / 1e9
+    fp64_1 = (variants["fp64_k1"]["gelem_s"] if args.workload == "chem" else elems / (ms64 * 1e-3) / 1e9)
     variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / fp64_1
     variants["dot2_block_over_fp64"] = variants["fp32_dot2_k16"]["gelem_s"] / fp64_1
 
-    # roofline of the product kernel (FP64, k = 1): algorithmic bytes
-    s_x = 8
+    # roofline of the headline product kernel: algorithmic bytes
+    s_x = 8 * k1 if head_prec == q.QSD_FP64 else 4 * k1
     b_alg = D * (W * 8 + 8 + s_x + s_x) + lookups * 8 + hits * (W * 8 + s_x)
     b_alg += info["n_terms"] * (3 * W * 8 + 8 + 1) + G * (W * 8 + 8 + 4 + 1 + 8 + 68)
     peak, peak_kind = load_peaks()
@@ -236,19 +258,20 @@ def run_gpu(args):
             "algorithmic_bytes_per_launch": b_alg, "lookups_per_launch": lookups, "hits_per_launch": hits}
 
     # end to end through the host-buffer ABI call (pinned host memory)
-    xh = torch.empty(D, dtype=torch.float64, pin_memory=True).numpy()
-    xh[:] = x64.cpu().numpy()
-    yh = torch.empty(D, dtype=torch.float64, pin_memory=True).numpy()
+    hdt = torch.float64 if head_prec == q.QSD_FP64 else torch.float32
+    xh = torch.empty(tuple(head_x.shape), dtype=hdt, pin_memory=True).numpy()
+    xh[:] = head_x.cpu().numpy()
+    yh = torch.empty(tuple(head_x.shape), dtype=hdt, pin_memory=True).numpy()
     for _ in range(args.warmup):
-        ctx.apply_H_host(h, sub, xh, q.QSD_FP64, out=yh)
+        ctx.apply_H_host(h, sub, xh, head_prec, out=yh)
     et = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        ctx.apply_H_host(h, sub, xh, q.QSD_FP64, out=yh)
+        ctx.apply_H_host(h, sub, xh, head_prec, out=yh)
         et.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(et))
-    e2e = {"value": world * elems / e2e_s / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": D * 8,
-           "d2h_bytes_per_step": D * 8, "ms_per_step": e2e_s * 1e3}
+    e2e = {"value": world * elems * k1 / e2e_s / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": int(xh.nbytes),
+           "d2h_bytes_per_step": int(yh.nbytes), "ms_per_step": e2e_s * 1e3}
 
     # one full ground-state solve per precision (not part of the timed steps)
     solve = {}
@@ -273,9 +296,12 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if head_prec == q.QSD_FP64 else "f32+f64acc", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "dim": D, "groups": G, "qubits": op.n_qubits,
-                       "k": 1, "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "k": k1, "precision": "fp64" if head_prec == q.QSD_FP64 else "fp32 storage, fp64 accumulation",
+                       "product_path": "excitation index" if (info["n_excitation_groups"] > 0 and
+                                                              args.workload == "chem") else "group scan",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
             "clocks": clk.summary(), "variants": variants, "solve": solve, "serve": serve,
@@ -469,7 +495,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="xxz", choices=["xxz", "tfim", "ising"])
+    ap.add_argument("--workload", default="xxz", choices=["xxz", "tfim", "ising", "chem"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-steps", type=int, default=300)
