@@ -418,6 +418,9 @@ static int64_t row_entries(int W, int64_t T, const int64_t *term_ptr, const int3
     buf[m].col = a; buf[m].re = 0.0; buf[m].im = 0.0; ++m;
     for (int64_t t = 0; t < T; ++t) {
         int p;
+        /* a word whose coefficient is exactly zero is not a term of H */
+        if (coef_re[t] == 0.0 && (!coef_im || coef_im[t] == 0.0))
+            continue;
         if (!word_element(op_qubit + term_ptr[t], op_code + term_ptr[t],
                           term_ptr[t + 1] - term_ptr[t], row, col, W, &p))
             continue;

@@ -158,6 +158,52 @@ def test_hermitian_csr_invariant():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
+def test_zero_coefficient_word_adds_no_structure():
+    # H = X_0 + 0 * X_1 on the full 2-qubit space: row 0 (00) reaches 01 only
+    op = wl.QubitOperator.from_terms(2, [(1.0, [(0, "X")]), (0.0, [(1, "X")])])
+    keys = _sorted_keys(wl.full_space(2))
+    indptr, indices, data = oracle.csr(op, keys)
+    assert list(indices[indptr[0]:indptr[1]]) == [0, 1]
+    assert np.allclose(oracle.dense(op, keys), brute.restricted(op, keys))
+
+
+def load_msob_example():
+    rows = []
+    with open(os.path.join(GOLDEN, "msob_example_s3.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            bits, inds, msob, tri = line.split()
+            rows.append((int(bits, 2), [int(i) for i in inds.split(",")], int(msob), tri))
+    return rows
+
+
+def test_msob_worked_example():
+    # Supplementary, "Most-significant off-diagonal bit": the row bit at the
+    # largest flipped index decides the triangle once S is indexed in
+    # integer order.  Checked on the oracle's CSR of the two flip groups.
+    ex = load_msob_example()
+    assert len(ex) == 2
+    n = 6
+    terms, words = [], []
+    for row, inds, msob, tri in ex:
+        assert msob == max(inds)
+        F = sum(1 << i for i in inds)
+        assert (((row >> msob) & 1) == 1) == (tri == "lower")
+        assert ((row ^ F) < row) == (tri == "lower")
+        terms.append((1.0, [(i, "X") for i in inds]))
+        words += [row, row ^ F]
+    op = wl.QubitOperator.from_terms(n, terms)
+    keys = _sorted_keys(wl.ints_to_words(words, n))
+    vals = [int(v) for v in wl.words_to_ints(keys)]
+    indptr, indices, data = oracle.csr(op, keys)
+    for row, inds, msob, tri in ex:
+        a = vals.index(row)
+        b = vals.index(row ^ sum(1 << i for i in inds))
+        assert b in indices[indptr[a]:indptr[a + 1]]
+        assert (b < a) == (tri == "lower")
+
+
 # ------------------------------------------------- closed forms / solvers --
 def tfim_closed_form(N, g):
     """Ground energy of the periodic chain H = -sum ZZ - g sum X, N even:
