@@ -39,6 +39,7 @@ import workloads as wl  # noqa: E402
 
 METRIC = "apply_H Gelem/s FP64 vs FP32-mixed block; served eigensolves/s, p50/p99 latency"
 L2_FLUSH_BYTES = 512 << 20
+PATH_NAMES = {0: "group scan, lane per row", 1: "group scan, 8 lanes per row", 2: "excitation index"}
 
 
 # ------------------------------------------------------------------ workloads
@@ -285,6 +286,25 @@ def run_gpu(args):
             solve[name] = {"seconds": time.perf_counter() - t0, "energy": e, "steps": inf["steps"],
                            "applies": inf["applies"], "residual": inf["residual"], "status": inf["status"]}
 
+    # explicit CSR build: lower triangle by MSOB and mirror, against every
+    # group of every row (two passes each, device sort of the entries)
+    csr = None
+    if not args.no_csr and args.workload != "chem":
+        csr = {}
+        for name, full in (("msob_lower", False), ("full", True)):
+            ts = []
+            for rep in range(4):
+                ctx.synchronize()
+                t0 = time.perf_counter()
+                ip, ind, dat = ctx.to_csr(h, sub, full=full)
+                ctx.synchronize()
+                if rep:
+                    ts.append(time.perf_counter() - t0)
+                nnz = int(ind.numel())
+                del ip, ind, dat
+            csr[name] = {"ms": 1e3 * float(np.mean(ts)), "nnz": nnz}
+        csr["msob_speedup"] = csr["full"]["ms"] / csr["msob_lower"]["ms"]
+
     serve = None
     if not args.no_serve:
         serve = run_serve(args, q, local)
@@ -299,12 +319,11 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f64" if head_prec == q.QSD_FP64 else "f32+f64acc", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "dim": D, "groups": G, "qubits": op.n_qubits,
                        "k": k1, "precision": "fp64" if head_prec == q.QSD_FP64 else "fp32 storage, fp64 accumulation",
-                       "product_path": "excitation index" if (info["n_excitation_groups"] > 0 and
-                                                              args.workload == "chem") else "group scan",
+                       "product_path": PATH_NAMES[ctx.product_path(h, sub, head_prec, k1)],
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "variants": variants, "solve": solve, "serve": serve,
+            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "serve": serve,
             "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
         }
         print(json.dumps(line))
@@ -502,6 +521,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=2.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-csr", action="store_true", help="skip the CSR build timing")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-slots", type=int, default=8)

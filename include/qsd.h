@@ -153,15 +153,61 @@ int qsd_subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n,
 
 int qsd_free_sub(qsd_sub sub);
 
+/* ------------------------------------------------------------------ CSR */
+/* Explicit CSR form of H_S by the two-pass build (Methods, "Matrix
+ * evaluation"): pass 1 counts each row's entries, pass 2 evaluates them again
+ * and writes them.  By default a row evaluates only its lower-triangle groups,
+ * those whose most significant flipped qubit is set in the row (Supplementary,
+ * "Lower / upper triangle evaluation" and "Most-significant off-diagonal
+ * bit"), and each lower entry h at (r, c) also fills (c, r) with conj(h); this
+ * needs a Hermitian operator.  QSD_CSR_FULL evaluates every group of every row
+ * instead (any real operator).
+ *
+ * Structure: row r holds its diagonal (always, even when zero) and every
+ * column c != r of S such that at least one term maps column c to row r with
+ * its projector tests passed; values are stored even when terms cancel.
+ * Columns ascend within a row.  Integer-exact; values are FP64 sums.
+ *
+ * Call once with indptr = indices = data_re = data_im = NULL: *nnz_out gets
+ * the number of entries and the pass-1 counts are kept in the context.  Then
+ * call with device arrays indptr int64 [D+1], indices int32 or int64
+ * (index_bits 32 | 64) [nnz], data_re double [nnz] and data_im double [nnz]
+ * (may be NULL for a real operator; required for a complex one, whose
+ * operator must be Hermitian).  The arrays are caller-owned device memory; the
+ * call is synchronous on the context's stream.  Errors: QSD_ERR_NOT_HERMITIAN
+ * (triangle evaluation of a non-Hermitian operator), QSD_ERR_CAPACITY (nnz
+ * >= 2^32 - 1), QSD_ERR_OOM (device temporaries: about 20 bytes per entry). */
+#define QSD_CSR_FULL 1
+int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_out,
+               int64_t *indptr, void *indices, int32_t index_bits,
+               double *data_re, double *data_im);
+
 /* ------------------------------------------------------------------ tuning */
 #define QSD_TUNE_APPLY_PATH     1  /* 0 auto; 1 per-row scan of all groups; 2 excitation
                                       index (ladder groups enumerated from each row's
                                       occupation; ignored when the operator has none) */
 #define QSD_TUNE_LANES_PER_ROW  2  /* per-row scan: 0 auto, 1 or 8 lanes per row */
+#define QSD_TUNE_AUTOTUNE       3  /* 1 (default): the first product of each (operator,
+                                      subspace, precision, block width) on a context times
+                                      the candidate paths on the stream and caches the
+                                      fastest; 0: heuristic choice */
 
 /* Set a product-path choice on a context (later products of this context
- * use it).  Results are identical up to summation order for every choice. */
+ * use it).  Results are identical up to summation order for every choice; a
+ * given choice is bitwise reproducible. */
 int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
+
+/* The product path that the next qsd_apply_H of (op, sub, precision) with k
+ * columns takes for its first column block (16, 4 or 1 columns wide), without
+ * timing anything: QSD_PATH_SCAN_1 (per-row group scan, one lane per row),
+ * QSD_PATH_SCAN_8 (eight lanes per row) or QSD_PATH_EXCITATION.  After a
+ * tuned product it is the cached measurement, else the forced choice or the
+ * heuristic.  No counterpart in the paper (its kernel has one launch shape). */
+#define QSD_PATH_SCAN_1     0
+#define QSD_PATH_SCAN_8     1
+#define QSD_PATH_EXCITATION 2
+int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
+                     int64_t k, int32_t *path_out);
 
 /* --------------------------------------------------------------- products */
 /* y = H_S x for k right-hand sides (Methods, "Matrix evaluation": the

@@ -80,6 +80,8 @@ SIGNATURES = [
     ("qsd_subspace_index", C.c_int, [_P, _P, _I64, _P, _P]),
     ("qsd_free_sub", C.c_int, [_P]),
     ("qsd_set_tuning", C.c_int, [_P, _I32, _I64]),
+    ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
+    ("qsd_product_path", C.c_int, [_P, _P, _P, _I32, _I64, C.POINTER(C.c_int32)]),
     ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
     ("qsd_apply_H_host", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
     ("qsd_diagonal", C.c_int, [_P, _P, _P, _P]),
@@ -216,8 +218,16 @@ class Context:
     # -- ABI calls
     def set_tuning(self, knob: int, value: int):
         """knob 1: product path (0 auto, 1 group scan, 2 excitation index);
-        knob 2: lanes per row of the group scan (0 auto, 1, 8)."""
+        knob 2: lanes per row of the group scan (0 auto, 1, 8); knob 3:
+        autotuning of the product path on first use (1 on, 0 off)."""
         self._check(lib().qsd_set_tuning(self.handle, int(knob), int(value)))
+
+    def product_path(self, op: "Operator", sub: "Subspace", precision: int = 0, k: int = 1) -> int:
+        """Path of the next product (0: scan, one lane per row; 1: scan, 8
+        lanes per row; 2: excitation index), without timing anything."""
+        out = C.c_int32(0)
+        self._check(lib().qsd_product_path(self.handle, op.handle, sub.handle, int(precision), int(k), C.byref(out)))
+        return int(out.value)
 
     def load_operator(self, op) -> Operator:
         """``op``: any object with n_qubits, term_ptr, op_qubit, op_code, coef
@@ -313,6 +323,27 @@ class Context:
         self._check(lib().qsd_rayleigh_quotient_noalloc(self.handle, op.handle, sub.handle, _t_ptr(u),
                                                         _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def to_csr(self, op: Operator, sub: Subspace, full: bool = False, index_bits: int = 32,
+               complex_data: bool = False):
+        """CSR arrays of H_S as CUDA tensors (indptr int64, indices int32/64,
+        data float64[, data_im float64]).  ``full``: evaluate every group of
+        every row instead of the lower triangle and its mirror."""
+        flags = 1 if full else 0
+        nnz = C.c_int64(0)
+        self._check(lib().qsd_to_csr(self.handle, op.handle, sub.handle, flags, C.byref(nnz), None, None,
+                                     int(index_bits), None, None))
+        t = self.torch
+        n = int(nnz.value)
+        indptr = self.empty((sub.dim + 1,), t.int64)
+        indices = self.empty((max(n, 1),), t.int32 if index_bits == 32 else t.int64)
+        data = self.empty((max(n, 1),), t.float64)
+        data_im = self.empty((max(n, 1),), t.float64) if complex_data else None
+        self._check(lib().qsd_to_csr(self.handle, op.handle, sub.handle, flags, C.byref(nnz), _t_ptr(indptr),
+                                     _t_ptr(indices), int(index_bits), _t_ptr(data),
+                                     _t_ptr(data_im) if data_im is not None else None))
+        out = (indptr, indices[:n], data[:n])
+        return out + (data_im[:n],) if complex_data else out
 
     def lanczos_ground_state(self, op: Operator, sub: Subspace, want_vector: bool = False,
                              check: bool = True, **params):

@@ -135,6 +135,14 @@ Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
 }
 
 void drop_bindings(qsd_ctx ctx, const void *handle) {
+    if (ctx->csr.op == handle || ctx->csr.sub == handle) ctx->csr.clear();
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        for (auto it = ctx->tune_cache.begin(); it != ctx->tune_cache.end();) {
+            if (std::get<0>(it->first) == handle || std::get<1>(it->first) == handle) it = ctx->tune_cache.erase(it);
+            else ++it;
+        }
+    }
     for (auto it = ctx->bindings.begin(); it != ctx->bindings.end();) {
         if (it->first.first == handle || it->first.second == handle) {
             delete it->second;
@@ -163,8 +171,9 @@ static bool use_excitation(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     return cand >= 0.0 && 4.0 * cand < (double)op->G;
 }
 
-void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
-             cudaStream_t stream) {
+namespace {
+
+ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y) {
     ApplyParams p{};
     p.keys = sub->keys.as<uint64_t>();
     p.D = sub->D;
@@ -191,34 +200,133 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     p.ld = k;
     p.err = ctx->d_err;
     p.num_sms = ctx->num_sms;
-    const int R = choose_lanes(ctx, sub->D, op->G);
-    const bool exc = use_excitation(ctx, op, sub);
+    return p;
+}
+
+ExcParams make_exc(qsd_op op) {
     ExcParams e{};
-    if (exc) {
-        e.ght = HashView{op->gtags.as<uint16_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
-                         (uint64_t)op->g_nbuckets - 1, op->g_shift};
-        e.exc_gid = op->exc_gid.as<int32_t>();
-        e.rest_gid = op->rest_gid.as<int32_t>();
-        e.n_rest = op->G_rest;
-        e.split = op->exc_split;
-        e.n_qubits = op->n_qubits;
-        e.n_shapes = op->n_shapes;
-        for (int i = 0; i < op->n_shapes; ++i) e.shapes[i] = op->shapes[i];
+    e.ght = HashView{op->gtags.as<uint16_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
+                     (uint64_t)op->g_nbuckets - 1, op->g_shift};
+    e.exc_gid = op->exc_gid.as<int32_t>();
+    e.rest_gid = op->rest_gid.as<int32_t>();
+    e.n_rest = op->G_rest;
+    e.split = op->exc_split;
+    e.n_qubits = op->n_qubits;
+    e.n_shapes = op->n_shapes;
+    for (int i = 0; i < op->n_shapes; ++i) e.shapes[i] = op->shapes[i];
+    return e;
+}
+
+// Product paths: 0 = per-row group scan with one lane per row, 1 = the same
+// with 8 lanes per row, 2 = excitation index (warp per row).
+void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int precision, int KB,
+                 cudaStream_t stream) {
+    if (path == 2) {
+        if (precision == QSD_FP64) launch_apply_exc<QSD_FP64>(p, e, W, KB, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_exc<QSD_FP32_MIXED>(p, e, W, KB, stream);
+        else launch_apply_exc<QSD_FP32_DOT2>(p, e, W, KB, stream);
+        return;
     }
+    const int R = path == 1 ? 8 : 1;
+    if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, W, R, KB, stream);
+    else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, W, R, KB, stream);
+    else launch_apply<QSD_FP32_DOT2>(p, W, R, KB, stream);
+}
+
+int heuristic_path(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    if (use_excitation(ctx, op, sub)) return 2;
+    return choose_lanes(ctx, sub->D, op->G) == 8 ? 1 : 0;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+// Path for (op, sub, precision, KB): a forced choice, the tuned choice in
+// the context's cache, a fresh measurement (when allowed), or the heuristic.
+int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int KB, const void *x,
+                 void *y, int64_t ld, int64_t col0, cudaStream_t stream, bool may_tune) {
+    if (ctx->tune_mode == 1) {
+        if (ctx->tune_lanes) return ctx->tune_lanes == 8 ? 1 : 0;
+        return choose_lanes(ctx, sub->D, op->G) == 8 ? 1 : 0;
+    }
+    if (ctx->tune_mode == 2 && op->exc_ok) return 2;
+    if (ctx->tune_lanes != 0 && !op->exc_ok) return ctx->tune_lanes == 8 ? 1 : 0;
+    const auto key = std::make_tuple((const void *)op, (const void *)sub, precision, KB);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tune_cache.find(key);
+        if (it != ctx->tune_cache.end()) return it->second;
+    }
+    const int guess = heuristic_path(ctx, op, sub);
+    if (!may_tune || !ctx->autotune || capturing(stream) || sub->D < 2048) return guess;
+    // Candidates: the excitation index only where a row reaches fewer flip
+    // masks than there are groups, the group scans only where the index does
+    // not reach 16x fewer.  The heuristic's guess runs first; each candidate
+    // runs up to three times and stops once it is 4x slower than the best.
+    const double cand = excitation_candidates(op, sub);
+    std::vector<int> cands;
+    if (guess == 2) cands.push_back(2);
+    if (!(cand >= 0.0 && 16.0 * cand < (double)op->G)) {
+        cands.push_back(guess == 1 ? 1 : 0);
+        cands.push_back(guess == 1 ? 0 : 1);
+    }
+    if (guess != 2 && cand >= 0.0 && cand < (double)op->G) cands.push_back(2);
+    if (cands.size() < 2) {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        ctx->tune_cache[key] = guess;
+        return guess;
+    }
+    ApplyParams p = make_params(ctx, op, sub, diag, (int)ld, x, y);
+    p.col0 = col0;
+    const ExcParams e = op->exc_ok ? make_exc(op) : ExcParams{};
+    cudaEvent_t a, b;
+    QSD_CUDA(cudaEventCreate(&a));
+    QSD_CUDA(cudaEventCreate(&b));
+    int best = guess;
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            QSD_CUDA(cudaEventRecord(a, stream));
+            launch_path(c, p, e, op->W, precision, KB, stream);
+            QSD_CUDA(cudaEventRecord(b, stream));
+            QSD_CUDA(cudaEventSynchronize(b));
+            float t = 0.f;
+            QSD_CUDA(cudaEventElapsedTime(&t, a, b));
+            ms = std::min(ms, t);
+            if (ms > 4.f * best_ms) break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tune_cache[key] = best;
+    return best;
+}
+
+void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
+             cudaStream_t stream, bool may_tune) {
+    ApplyParams p = make_params(ctx, op, sub, diag, k, x, y);
+    ExcParams e{};
+    bool have_e = false;
     int64_t c = 0;
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
         p.col0 = c;
-        if (exc) {
-            if (precision == QSD_FP64) launch_apply_exc<QSD_FP64>(p, e, op->W, KB, stream);
-            else if (precision == QSD_FP32_MIXED) launch_apply_exc<QSD_FP32_MIXED>(p, e, op->W, KB, stream);
-            else launch_apply_exc<QSD_FP32_DOT2>(p, e, op->W, KB, stream);
-            c += KB;
-            continue;
+        const int path = product_path(ctx, op, sub, diag, precision, KB, x, y, k, c, stream, may_tune);
+        if (path == 2 && !have_e) {
+            e = make_exc(op);
+            have_e = true;
         }
-        if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, op->W, R, KB, stream);
-        else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, op->W, R, KB, stream);
-        else launch_apply<QSD_FP32_DOT2>(p, op->W, R, KB, stream);
+        launch_path(path, p, e, op->W, precision, KB, stream);
         c += KB;
     }
 }
@@ -446,7 +554,7 @@ int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, c
         if (!x || !y) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H: NULL vector");
         set_device(ctx);
         Binding *b = get_binding(ctx, op, sub);
-        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, x, y, ctx->stream);
+        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, x, y, ctx->stream, true);
     });
 }
 
@@ -467,7 +575,7 @@ int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t
         Scratch &sx = ctx->scratch[0], &sy = ctx->scratch[1];
         void *dx = sx.get(bytes), *dy = sy.get(bytes);
         QSD_CUDA(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
-        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, dx, dy, ctx->stream);
+        apply_H(ctx, op, sub, b->diag.as<double>(), precision, k, dx, dy, ctx->stream, true);
         QSD_CUDA(cudaMemcpyAsync(y_host, dy, bytes, cudaMemcpyDeviceToHost, ctx->stream));
         QSD_CUDA(cudaStreamSynchronize(ctx->stream));
     });
@@ -535,9 +643,53 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
         if (value != 0 && value != 1 && value != 8) return QSD_ERR_INVALID_ARG;
         ctx->tune_lanes = (int)value;
         return QSD_OK;
+    case QSD_TUNE_AUTOTUNE:
+        if (value != 0 && value != 1) return QSD_ERR_INVALID_ARG;
+        ctx->autotune = (int)value;
+        if (!value) {
+            std::lock_guard<std::mutex> lk2(ctx->tune_mu);
+            ctx->tune_cache.clear();
+        }
+        return QSD_OK;
     default:
         return QSD_ERR_INVALID_ARG;
     }
+}
+
+int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_out, int64_t *indptr,
+               void *indices, int32_t index_bits, double *data_re, double *data_im) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (!nnz_out) fail(QSD_ERR_INVALID_ARG, "qsd_to_csr: NULL nnz_out");
+        if (flags & ~QSD_CSR_FULL) fail(QSD_ERR_INVALID_ARG, "qsd_to_csr: unknown flag bits");
+        if (index_bits != 32 && index_bits != 64) fail(QSD_ERR_INVALID_ARG, "qsd_to_csr: index_bits must be 32 or 64");
+        if (index_bits == 32 && sub->D > 0x7fffffffLL)
+            fail(QSD_ERR_INVALID_ARG, "qsd_to_csr: dimension needs 64-bit indices");
+        const bool sizing = !indptr && !indices && !data_re;
+        if (!sizing && (!indptr || !indices || !data_re))
+            fail(QSD_ERR_INVALID_ARG, "qsd_to_csr: indptr, indices and data_re must all be given (or all NULL)");
+        const bool lower = !(flags & QSD_CSR_FULL);
+        if (!op->info.is_hermitian && (lower || !op->info.is_real))
+            fail(QSD_ERR_NOT_HERMITIAN, "qsd_to_csr: the triangle evaluation (and complex data) needs a Hermitian operator");
+        if (!op->info.is_real && !sizing && !data_im)
+            fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_to_csr: complex operator needs data_im");
+        Binding *b = get_binding(ctx, op, sub);
+        *nnz_out = to_csr(ctx, op, sub, lower, indptr, indices, index_bits, data_re, data_im, b->diag.as<double>());
+    });
+}
+
+int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision, int64_t k, int32_t *path_out) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (!path_out || k < 1) fail(QSD_ERR_INVALID_ARG, "NULL path_out or k < 1");
+        if (precision < QSD_FP64 || precision > QSD_FP32_DOT2) fail(QSD_ERR_INVALID_ARG, "unknown precision");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        const int KB = k >= 16 ? 16 : (k >= 4 ? 4 : 1);
+        *path_out = product_path(ctx, op, sub, nullptr, precision, KB, nullptr, nullptr, k, 0, ctx->stream, false);
+    });
 }
 
 void qsd_lanczos_default_params(qsd_lanczos_params *p) {

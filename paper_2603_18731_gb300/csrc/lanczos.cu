@@ -558,6 +558,11 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
     // main phase: FP64, or FP32 until FP32 round-off limits the estimate
     LanczosJob J;
     J.init(ctx, op, sub, diag, p.precision, p.max_steps, p.check_every, s, false);
+    // pick the product paths now: graph capture must not time anything
+    QSD_CUDA(cudaMemsetAsync(J.vcur.p, 0, J.vcur.bytes, s));
+    QSD_CUDA(cudaMemsetAsync(u.p, 0, u.bytes, s));
+    product_path(ctx, op, sub, diag, p.precision, 1, J.vcur.p, J.hv.p, 1, 0, s, true);
+    if (p.precision != QSD_FP64) product_path(ctx, op, sub, diag, QSD_FP64, 1, u.p, R.hu.p, 1, 0, s, true);
     const double phase_tol = mixed ? std::max(tol, 1e-5) : tol;
     J.enqueue_start(p.v0, p.seed);
     while (J.steps_done < J.m) {

@@ -18,6 +18,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <stdexcept>
 #include <string>
 #include <utility>
@@ -84,10 +85,30 @@ struct Binding;
 
 }  // namespace qsd
 
+namespace qsd {
+// Pass-1 result of the CSR build, kept between the sizing and the filling call.
+struct CsrState {
+    const void *op = nullptr, *sub = nullptr;
+    bool lower = false;
+    int64_t L = 0, nnz = -1;
+    DevBuf cnt, off;  // uint32 [D] entries per row, first entry of each row
+    void clear() {
+        op = sub = nullptr;
+        L = 0;
+        nnz = -1;
+        cnt.release();
+        off.release();
+    }
+};
+}  // namespace qsd
+
 struct qsd_ctx_s {
     int device = 0;
     int tune_mode = 0;    // product path: 0 auto, 1 per-row group scan, 2 excitation index
     int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
+    int autotune = 1;     // measure the product paths on first use and cache the fastest
+    std::mutex tune_mu;
+    std::map<std::tuple<const void *, const void *, int, int>, int> tune_cache;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int num_sms = 0;
@@ -99,6 +120,7 @@ struct qsd_ctx_s {
     // device copy of the nibble tables of the prehash (see hash_prehash)
     qsd::DevBuf nib;
     int nib_words = 0;
+    qsd::CsrState csr;
     uint32_t *d_err = nullptr;   // device error word of the last kernels
     uint32_t *h_err = nullptr;   // pinned mirror
 };
@@ -149,6 +171,7 @@ struct qsd_op_s {
     qsd::DevBuf tphi;    // double [T] real phase * coefficient
     qsd::DevBuf tphi_im; // double [T]
     qsd::DevBuf tflag;   // uint8  [T] bit0: P != 0, bit1: Z != 0
+    qsd::DevBuf gmsob;   // uint16 [G] most significant flipped qubit (built by the first CSR call)
     // diagonal terms (Td)
     int64_t Td = 0;
     qsd::DevBuf dP, dV, dZ;  // uint64 [W][Td]
@@ -379,8 +402,19 @@ Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub);
 void drop_bindings(qsd_ctx ctx, const void *handle);
 void compute_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d);
 void compute_diagonal_on(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d, cudaStream_t s);
+// y = H_S x on `stream`.  may_tune: a product shape seen for the first time
+// may be timed on the stream to pick the fastest path (never while the
+// stream is being captured).
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k,
-             const void *x, void *y, cudaStream_t stream);
+             const void *x, void *y, cudaStream_t stream, bool may_tune = false);
+// Path of a product shape (see apply_H); measures it once when allowed.
+// CSR form of H_S (csr.cu).  Sizing call (indptr, indices, data_re NULL):
+// returns nnz and keeps the pass-1 counts; filling call: writes the arrays.
+int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr, void *indices, int index_bits,
+               double *data_re, double *data_im, const double *diag);
+
+int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int KB, const void *x,
+                 void *y, int64_t ld, int64_t col0, cudaStream_t stream, bool may_tune);
 void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out);
 void term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int8_t *out);
 void rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const double *u, double *out);

@@ -221,6 +221,46 @@ def test_excitation_path_with_rest_groups(ctx):
     ctx.set_tuning(1, 0)
 
 
+@pytest.mark.parametrize("kind,k", [("chem", 1), ("chem", 16), ("xxz", 1), ("xxz", 4)])
+def test_autotuned_product_matches_oracle(ctx, kind, k):
+    import torch
+    if kind == "chem":
+        h1, eri = wl.chem_integrals(8, seed=8)
+        op = wl.molecular_qubit_operator(h1, eri)
+        strings = [v for v in range(1 << 8) if bin(v).count("1") == 4]
+        words = wl.product_subspace(strings, strings, 8)  # 4900 rows
+    else:
+        op = wl.xxz_square(4, 4, 1.0, 0.5)
+        words = wl.xxz_walk_subspace(4, 4, 3000, seed=2)
+    keys = oracle.sort_unique(words)
+    assert keys.shape[0] >= 2048  # the tuner only measures subspaces this large
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(op.n_qubits, words)
+    rng = np.random.default_rng(k)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    ref = oracle.apply(op, keys, x).real
+    ctx.set_tuning(3, 0)
+    guess = ctx.product_path(h, sub, k=k)
+    y0 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+    ctx.set_tuning(3, 1)
+    y1 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))  # measures, then runs the winner
+    tuned = ctx.product_path(h, sub, k=k)
+    y2 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))  # cached choice
+    ctx.synchronize()
+    assert guess in (0, 1, 2) and tuned in (0, 1, 2)
+    for y in (y0, y1, y2):
+        assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
+    assert torch.equal(y1, y2)
+    ctx.set_tuning(1, 1 if tuned < 2 else 2)
+    if tuned < 2:
+        ctx.set_tuning(2, 8 if tuned == 1 else 1)
+    y3 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+    ctx.synchronize()
+    assert torch.equal(y2, y3)  # the cached path is the forced one, bit for bit
+    ctx.set_tuning(1, 0)
+    ctx.set_tuning(2, 0)
+
+
 # --------------------------------------------------------- integer tables
 @pytest.mark.parametrize("n,seed", [(10, 1), (70, 2), (200, 3)])
 def test_target_and_term_tables_exact(ctx, n, seed):
