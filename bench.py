@@ -243,6 +243,18 @@ def run_gpu(args):
     for name, x, prec, k in vlist:
         m, _, _ = time_variant(x, prec, vsteps, 3)
         variants[name] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
+    if info["is_hermitian"] and info["is_real"] and W <= 4:
+        # half evaluation: lower-triangle groups by MSOB, mirrored by FP64
+        # atomic adds (summation order varies between runs)
+        ctx.set_tuning(1, 3)
+        for name, x, k in (("fp64_k1_half", x64, 1), ("fp64_k16_half", xb64, 16)):
+            for lanes in (1, 8):
+                ctx.set_tuning(2, lanes)
+                m, _, _ = time_variant(x, q.QSD_FP64, vsteps, 3)
+                key = f"{name}_lanes{lanes}"
+                variants[key] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(2, 0)
     fp64_1 = (variants["fp64_k1"]["gelem_s"] if args.workload == "chem" else elems / (ms64 * 1e-3) / 1e9)
     variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / fp64_1
     variants["dot2_block_over_fp64"] = variants["fp32_dot2_k16"]["gelem_s"] / fp64_1

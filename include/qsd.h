@@ -185,27 +185,42 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
 /* ------------------------------------------------------------------ tuning */
 #define QSD_TUNE_APPLY_PATH     1  /* 0 auto; 1 per-row scan of all groups; 2 excitation
                                       index (ladder groups enumerated from each row's
-                                      occupation; ignored when the operator has none) */
+                                      occupation; ignored when the operator has none);
+                                      3 half evaluation (below; a plain scan where it
+                                      does not apply) */
 #define QSD_TUNE_LANES_PER_ROW  2  /* per-row scan: 0 auto, 1 or 8 lanes per row */
 #define QSD_TUNE_AUTOTUNE       3  /* 1 (default): the first product of each (operator,
                                       subspace, precision, block width) on a context times
                                       the candidate paths on the stream and caches the
                                       fastest; 0: heuristic choice */
+#define QSD_TUNE_HALF_EVALUATION 4 /* 1: the autotuner may also pick the half evaluation;
+                                      0 (default): it does not.  Half evaluation (real
+                                      Hermitian operator, QSD_FP64, n <= 256): a row
+                                      evaluates only its lower-triangle groups, those whose
+                                      most significant flipped qubit is set in the row
+                                      (Supplementary, "Lower / upper triangle evaluation"),
+                                      and each element h at (r, c) adds h x[c] to y[r] and
+                                      h x[r] to y[c] by FP64 atomic adds: half the element
+                                      evaluations and lookups, but a summation order (so
+                                      the last bits of y) that varies from run to run. */
 
 /* Set a product-path choice on a context (later products of this context
  * use it).  Results are identical up to summation order for every choice; a
- * given choice is bitwise reproducible. */
+ * given choice other than the half evaluation is bitwise reproducible. */
 int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
 
 /* The product path that the next qsd_apply_H of (op, sub, precision) with k
  * columns takes for its first column block (16, 4 or 1 columns wide), without
  * timing anything: QSD_PATH_SCAN_1 (per-row group scan, one lane per row),
- * QSD_PATH_SCAN_8 (eight lanes per row) or QSD_PATH_EXCITATION.  After a
+ * QSD_PATH_SCAN_8 (eight lanes per row), QSD_PATH_EXCITATION, or the half
+ * evaluation with one or eight lanes per row (QSD_PATH_HALF_1, _8).  After a
  * tuned product it is the cached measurement, else the forced choice or the
  * heuristic.  No counterpart in the paper (its kernel has one launch shape). */
 #define QSD_PATH_SCAN_1     0
 #define QSD_PATH_SCAN_8     1
 #define QSD_PATH_EXCITATION 2
+#define QSD_PATH_HALF_1     3
+#define QSD_PATH_HALF_8     4
 int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
                      int64_t k, int32_t *path_out);
 

@@ -218,9 +218,15 @@ ExcParams make_exc(qsd_op op) {
 }
 
 // Product paths: 0 = per-row group scan with one lane per row, 1 = the same
-// with 8 lanes per row, 2 = excitation index (warp per row).
+// with 8 lanes per row, 2 = excitation index (warp per row), 3 and 4 = the
+// half-evaluation scan (lower-triangle groups, mirrored by atomic adds) with
+// 1 or 8 lanes per row.
 void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int precision, int KB,
                  cudaStream_t stream) {
+    if (path == 3 || path == 4) {
+        launch_apply_sym(p, W, path == 4 ? 8 : 1, KB, stream);
+        return;
+    }
     if (path == 2) {
         if (precision == QSD_FP64) launch_apply_exc<QSD_FP64>(p, e, W, KB, stream);
         else if (precision == QSD_FP32_MIXED) launch_apply_exc<QSD_FP32_MIXED>(p, e, W, KB, stream);
@@ -249,12 +255,14 @@ bool capturing(cudaStream_t s) {
 // the context's cache, a fresh measurement (when allowed), or the heuristic.
 int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int KB, const void *x,
                  void *y, int64_t ld, int64_t col0, cudaStream_t stream, bool may_tune) {
-    if (ctx->tune_mode == 1) {
-        if (ctx->tune_lanes) return ctx->tune_lanes == 8 ? 1 : 0;
-        return choose_lanes(ctx, sub->D, op->G) == 8 ? 1 : 0;
-    }
+    // the half evaluation needs H = H^T (real Hermitian), FP64 storage and W <= 4
+    const bool sym_ok = op->info.is_hermitian && op->info.is_real && precision == QSD_FP64 &&
+                        op->W <= kMaxWordsStatic;
+    const int lanes_path = (ctx->tune_lanes ? ctx->tune_lanes : choose_lanes(ctx, sub->D, op->G)) == 8 ? 1 : 0;
+    if (ctx->tune_mode == 1 || (ctx->tune_mode == 3 && !sym_ok)) return lanes_path;
+    if (ctx->tune_mode == 3) return lanes_path + 3;
     if (ctx->tune_mode == 2 && op->exc_ok) return 2;
-    if (ctx->tune_lanes != 0 && !op->exc_ok) return ctx->tune_lanes == 8 ? 1 : 0;
+    if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym)) return lanes_path;
     const auto key = std::make_tuple((const void *)op, (const void *)sub, precision, KB);
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
@@ -271,8 +279,17 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     std::vector<int> cands;
     if (guess == 2) cands.push_back(2);
     if (!(cand >= 0.0 && 16.0 * cand < (double)op->G)) {
-        cands.push_back(guess == 1 ? 1 : 0);
-        cands.push_back(guess == 1 ? 0 : 1);
+        if (ctx->tune_lanes) {
+            cands.push_back(lanes_path);
+        } else {
+            cands.push_back(guess == 1 ? 1 : 0);
+            cands.push_back(guess == 1 ? 0 : 1);
+        }
+        if (sym_ok && ctx->allow_sym) {
+            const size_t m = cands.size();
+            for (size_t i = 0; i < m; ++i)
+                if (cands[i] < 2) cands.push_back(cands[i] + 3);
+        }
     }
     if (guess != 2 && cand >= 0.0 && cand < (double)op->G) cands.push_back(2);
     if (cands.size() < 2) {
@@ -636,12 +653,20 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     switch (knob) {
     case QSD_TUNE_APPLY_PATH:
-        if (value < 0 || value > 2) return QSD_ERR_INVALID_ARG;
+        if (value < 0 || value > 3) return QSD_ERR_INVALID_ARG;
         ctx->tune_mode = (int)value;
         return QSD_OK;
     case QSD_TUNE_LANES_PER_ROW:
         if (value != 0 && value != 1 && value != 8) return QSD_ERR_INVALID_ARG;
         ctx->tune_lanes = (int)value;
+        return QSD_OK;
+    case QSD_TUNE_HALF_EVALUATION:
+        if (value != 0 && value != 1) return QSD_ERR_INVALID_ARG;
+        ctx->allow_sym = (int)value;
+        {
+            std::lock_guard<std::mutex> lk2(ctx->tune_mu);
+            ctx->tune_cache.clear();
+        }
         return QSD_OK;
     case QSD_TUNE_AUTOTUNE:
         if (value != 0 && value != 1) return QSD_ERR_INVALID_ARG;

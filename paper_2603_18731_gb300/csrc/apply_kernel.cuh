@@ -30,6 +30,8 @@ namespace qsd {
 
 constexpr int kTableBitsMax = 5;
 constexpr uint32_t kGroupScan = 0x80u;
+constexpr int kMsobShift = 16;         // GroupRec::info bits 16..27: most significant flipped qubit
+constexpr uint32_t kMsobMask = 0xfffu;
 
 // Groups per batch (bucket loads in flight per lane) and the minimum resident
 // blocks of 256 threads per SM asked of the compiler, per key width W, for the
@@ -47,7 +49,7 @@ struct __align__(16) GroupRec {
     uint64_t hF;    // prehash of the flip mask F
     uint64_t pos;   // table groups: support qubits, 12 bits each, ascending
     uint32_t off;   // table groups: offset of the 2^nb amplitudes
-    uint32_t info;  // bits 0..2: nb; kGroupScan: scan group
+    uint32_t info;  // bits 0..2: nb; kGroupScan: scan group; bits 16..27: MSOB
     uint64_t F0;    // word 0 of F
 };
 
@@ -149,7 +151,15 @@ __device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e
 }
 
 // One output row; the R lanes of a row call this together.
-template <int W, int R, int KB, int PREC>
+//
+// SYM (Hermitian real operators, FP64 only): the row evaluates only the
+// groups whose most significant flipped qubit is set in it -- its
+// lower-triangle elements (Supplementary, "Lower / upper triangle
+// evaluation") -- and each element h found at (r, c) adds h x[c] to row r and
+// h x[r] to row c.  Both go to y by FP64 atomic adds into a zeroed y, so
+// every element is evaluated and looked up once instead of twice, at the
+// price of a summation order that varies from run to run.
+template <int W, int R, int KB, int PREC, bool SYM = false>
 __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t row) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     constexpr int U = ApplyShape<W, KB>::U;
@@ -161,11 +171,17 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + r);
     const uint64_t hr = prehash<W>(key, p.nib);
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
+    static_assert(!SYM || PREC == QSD_FP64, "half evaluation is FP64 only");
     // accumulators: FP64 (modes 0, 1) or FP32 (s, e) pairs (DOT2)
     double acc[KB];
     float as[KB], ae[KB];
 #pragma unroll
     for (int j = 0; j < KB; ++j) { acc[j] = 0.0; as[j] = 0.f; ae[j] = 0.f; }
+    double xr_own[SYM ? KB : 1];
+    if (SYM) {
+#pragma unroll
+        for (int j = 0; j < KB; ++j) xr_own[j] = (double)__ldg(x + r * p.ld + p.col0 + j);
+    }
 
     for (int64_t g0 = (int64_t)sub * U; g0 < p.G; g0 += (int64_t)R * U) {
         // phase 1: element of each of U groups, and its bucket load in flight
@@ -188,7 +204,14 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                 const uint64_t r1x = __ldg(reinterpret_cast<const unsigned long long *>(rp + 1));
                 hF = r0.x;
                 const uint32_t off = (uint32_t)r1x, info = (uint32_t)(r1x >> 32);
-                if (!(info & kGroupScan)) {
+                bool lower = true;
+                if (SYM) {
+                    const int qm = (int)((info >> kMsobShift) & kMsobMask);
+                    lower = (word_of<W>(key, qm) >> (qm & 63)) & 1;
+                }
+                if (!lower) {
+                    // upper-triangle element: reached from its column's row
+                } else if (!(info & kGroupScan)) {
                     // nb is uniform across the warp (lane per row): a real loop
                     const int nb = (int)(info & 7u);
                     int l = 0;
@@ -251,6 +274,11 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             } else {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) acc[j] = fma(a[u], (double)__ldg(xc + j), acc[j]);
+                if (SYM) {
+                    double *yc = static_cast<double *>(p.y) + idx * p.ld + p.col0;
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) atomicAdd(yc + j, a[u] * xr_own[j]);
+                }
             }
         }
     }
@@ -280,6 +308,9 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                 dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
                 yr[j] = (TIO)(as[j] + ae[j]);
             }
+        } else if (SYM) {
+#pragma unroll
+            for (int j = 0; j < KB; ++j) atomicAdd(reinterpret_cast<double *>(yr) + j, fma(d, xr_own[j], acc[j]));
         } else {
 #pragma unroll
             for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
@@ -288,9 +319,9 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
 }
 
 // One launch covers all rows: R lanes per row, rows past D inactive.
-template <int W, int R, int KB, int PREC>
+template <int W, int R, int KB, int PREC, bool SYM = false>
 __global__ void __launch_bounds__(256, (ApplyShape<W, KB>::MINB)) k_apply(const ApplyParams p) {
-    apply_row<W, R, KB, PREC>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
+    apply_row<W, R, KB, PREC, SYM>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
 }
 
 // Run-time W (W > kMaxWordsStatic): a lane per row, keys in local memory,
@@ -353,5 +384,8 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
 // Launch one (W, R, KB) variant of precision mode PREC.
 template <int PREC>
 void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
+// Half-evaluation product (FP64, Hermitian real operators, W <= 4); zeroes
+// the launch's columns of y first.
+void launch_apply_sym(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
 
 }  // namespace qsd

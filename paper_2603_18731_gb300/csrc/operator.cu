@@ -175,10 +175,15 @@ __global__ void k_group_records(int W, int64_t G, const int32_t *__restrict__ gr
     GroupRec R;
     R.hF = ghash[g];
     R.F0 = gF[g];
+    // most significant flipped qubit (the half-evaluation product's filter)
+    uint32_t msob = 0;
+    for (int w = 0; w < W; ++w)
+        if (gF[(size_t)w * G + g]) msob = (uint32_t)(64 * w + 63 - __clzll((long long)gF[(size_t)w * G + g]));
+    const uint32_t hi_info = (msob & kMsobMask) << kMsobShift;
     if (size[g] == 0) {
         R.pos = 0;
         R.off = 0;
-        R.info = kGroupScan;
+        R.info = kGroupScan | hi_info;
         rec[g] = R;
         return;
     }
@@ -186,7 +191,7 @@ __global__ void k_group_records(int W, int64_t G, const int32_t *__restrict__ gr
     const uint64_t pos = spos[g] & ((1ull << 60) - 1);
     R.pos = pos;
     R.off = off[g];
-    R.info = (uint32_t)nb;
+    R.info = (uint32_t)nb | hi_info;
     uint64_t rs[kMaxWordsDyn];
     for (uint32_t l = 0; l < size[g]; ++l) {
         for (int w = 0; w < W; ++w) rs[w] = 0;

@@ -104,8 +104,9 @@ struct CsrState {
 
 struct qsd_ctx_s {
     int device = 0;
-    int tune_mode = 0;    // product path: 0 auto, 1 per-row group scan, 2 excitation index
+    int tune_mode = 0;    // product path: 0 auto, 1 group scan, 2 excitation index, 3 half evaluation
     int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
+    int allow_sym = 0;    // the autotuner may pick the half-evaluation product
     int autotune = 1;     // measure the product paths on first use and cache the fastest
     std::mutex tune_mu;
     std::map<std::tuple<const void *, const void *, int, int>, int> tune_cache;

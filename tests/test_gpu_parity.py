@@ -261,6 +261,61 @@ def test_autotuned_product_matches_oracle(ctx, kind, k):
     ctx.set_tuning(2, 0)
 
 
+@pytest.mark.parametrize("n,T,wmax,count,k,lanes", [(12, 60, 4, 3000, 1, 1), (40, 80, 5, 4000, 4, 8),
+                                                     (100, 60, 4, 3000, 16, 1), (250, 40, 3, 2000, 1, 8)])
+def test_half_evaluation_matches_oracle(ctx, n, T, wmax, count, k, lanes):
+    import torch
+    op = wl.random_extended(n, T, max_weight=wmax, seed=n + k)
+    words = wl.random_subspace(n, count, seed=n)
+    keys0 = oracle.sort_unique(words)
+    words = np.concatenate([words] + [keys0[:200] ^ f for f in oracle.groups(op)[:30]])
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(n, words)
+    rng = np.random.default_rng(k)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    ref = oracle.apply(op, keys, x).real
+    ctx.set_tuning(1, 3)
+    ctx.set_tuning(2, lanes)
+    assert ctx.product_path(h, sub, k=k) == (4 if lanes == 8 else 3)
+    y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+    ctx.synchronize()
+    assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
+    # FP32 storage and non-Hermitian operators take the plain scan
+    assert ctx.product_path(h, sub, precision=1, k=k) in (0, 1)
+    ctx.set_tuning(1, 0)
+    ctx.set_tuning(2, 0)
+
+
+def test_half_evaluation_models_and_tuner(ctx):
+    import torch
+    cases = [(wl.xxz_square(4, 4, 1.0, 0.5), wl.xxz_walk_subspace(4, 4, 3000, seed=3)),
+             (wl.ising_heavy_hex(60, seed=4), wl.flip_subspace(60, 20000, max_flips=3, seed=4))]
+    nh = wl.random_extended(10, 30, max_weight=4, seed=5, hermitian=False, letters="01XZ+-")
+    for op, words in cases:
+        keys = oracle.sort_unique(words)
+        h = ctx.load_operator(op)
+        sub = ctx.build_subspace(op.n_qubits, words)
+        x = np.random.default_rng(2).normal(size=sub.dim)
+        ref = oracle.apply(op, keys, x).real
+        ctx.set_tuning(4, 1)  # the tuner may pick the half evaluation
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        assert ctx.product_path(h, sub) in (0, 1, 3, 4)
+        assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
+        ctx.set_tuning(1, 3)
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(4, 0)
+    h = ctx.load_operator(nh)
+    sub = ctx.build_subspace(10, wl.random_subspace(10, 500, seed=1))
+    ctx.set_tuning(1, 3)
+    assert ctx.product_path(h, sub) in (0, 1)
+    ctx.set_tuning(1, 0)
+
+
 # --------------------------------------------------------- integer tables
 @pytest.mark.parametrize("n,seed", [(10, 1), (70, 2), (200, 3)])
 def test_target_and_term_tables_exact(ctx, n, seed):
