@@ -90,13 +90,14 @@ namespace qsd {
 struct CsrState {
     const void *op = nullptr, *sub = nullptr;
     bool lower = false;
-    int64_t L = 0, nnz = -1;
-    DevBuf cnt, off;  // uint32 [D] entries per row, first entry of each row
+    int64_t nnz = -1;
+    DevBuf cnt, cnt_up, len, off;  // uint32 [D]: evaluated, mirrored, segment length and start
     void clear() {
         op = sub = nullptr;
-        L = 0;
         nnz = -1;
         cnt.release();
+        cnt_up.release();
+        len.release();
         off.release();
     }
 };

@@ -126,3 +126,22 @@ def test_csr_empty_and_diagonal_only(ctx):
     empty = ctx.build_subspace(n, np.zeros((0, 1), np.uint64))
     indptr, indices, data = ctx.to_csr(h, empty)
     assert indptr.cpu().tolist() == [0] and indices.numel() == 0
+
+
+def test_csr_rows_longer_than_a_block_sort(ctx):
+    # every row of the full 13-qubit space reaches 4100 columns (> 4096):
+    # the per-row sorts hand over to the device sort of all entries
+    n = 13
+    rng = np.random.default_rng(7)
+    masks = set()
+    while len(masks) < 4100:
+        masks.add(int(rng.integers(1, 1 << n)))
+    terms = [(float(rng.normal()), [(q, "X") for q in range(n) if (m >> q) & 1]) for m in sorted(masks)]
+    op = wl.QubitOperator.from_terms(n, terms)
+    words = wl.full_space(n)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(n, words)
+    ref = oracle.csr(op, keys)
+    for full in (False, True):
+        check_csr(ctx.to_csr(h, sub, full=full), ref)
