@@ -304,18 +304,27 @@ def run_gpu(args):
     if not args.no_csr and args.workload != "chem":
         csr = {}
         for name, full in (("msob_lower", False), ("full", True)):
-            ts = []
+            ts, tc = [], []
             for rep in range(4):
                 ctx.synchronize()
                 t0 = time.perf_counter()
+                nnz = ctx.csr_size(h, sub, full=full)  # pass 1 (kept for the fill)
+                t1 = time.perf_counter()
                 ip, ind, dat = ctx.to_csr(h, sub, full=full)
                 ctx.synchronize()
                 if rep:
                     ts.append(time.perf_counter() - t0)
-                nnz = int(ind.numel())
+                    tc.append(t1 - t0)
                 del ip, ind, dat
-            csr[name] = {"ms": 1e3 * float(np.mean(ts)), "nnz": nnz}
+            csr[name] = {"ms": 1e3 * float(np.mean(ts)), "count_pass_ms": 1e3 * float(np.mean(tc)), "nnz": nnz}
         csr["msob_speedup"] = csr["full"]["ms"] / csr["msob_lower"]["ms"]
+
+    # packed launches: many small products (64 walk subspaces of the
+    # workload's family, D log-uniform in [500, 5000]) as one launch against
+    # one launch per pair
+    packed = None
+    if not args.no_packed and W <= 4 and args.workload != "chem":
+        packed = run_packed(ctx, q, op, args.workload)
 
     serve = None
     if not args.no_serve:
@@ -335,7 +344,7 @@ def run_gpu(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "serve": serve,
+            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "packed": packed, "serve": serve,
             "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
         }
         print(json.dumps(line))
@@ -343,6 +352,50 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_packed(ctx, q, op, workload, n_pairs=64, reps=20):
+    import torch
+    rng = np.random.default_rng(11)
+    h = ctx.load_operator(op)
+    subs, xs = [], []
+    for i in range(n_pairs):
+        d = int(np.exp(rng.uniform(np.log(500), np.log(5000))))
+        if workload == "xxz":
+            words = wl.xxz_walk_words(6, 6, d, 12, 100 + i)
+        elif workload == "tfim":
+            words = wl.random_subspace(op.n_qubits, d, seed=100 + i)
+        else:
+            words = wl.flip_words(op.n_qubits, d, 20, 100 + i)
+        s_ = ctx.build_subspace(op.n_qubits, words)
+        subs.append(s_)
+        with torch.cuda.stream(ctx.stream):
+            xs.append(torch.as_tensor(rng.normal(size=s_.dim), device=ctx.device))
+    ops = [h] * n_pairs
+    ys = [ctx.empty((s_.dim,), torch.float64) for s_ in subs]
+    G = h.info()["n_groups"]
+    elems = sum(s_.dim for s_ in subs) * (G + 1)
+    ctx.set_tuning(1, 1)
+    ctx.set_tuning(2, 1)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(ctx.stream)
+            fn()
+            b.record(ctx.stream)
+        ctx.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    t_single = timed(lambda: [ctx.apply_H(h, s_, x, y) for s_, x, y in zip(subs, xs, ys)])
+    t_packed = timed(lambda: ctx.apply_H_batch(ops, subs, xs, ys))
+    ctx.set_tuning(1, 0)
+    ctx.set_tuning(2, 0)
+    return {"pairs": n_pairs, "rows": int(sum(s_.dim for s_ in subs)), "one_launch_per_pair_ms": t_single,
+            "packed_ms": t_packed, "packed_gelem_s": elems / (t_packed * 1e-3) / 1e9,
+            "one_launch_per_pair_gelem_s": elems / (t_single * 1e-3) / 1e9, "speedup": t_single / t_packed}
 
 
 # ------------------------------------------------------------------ serving
@@ -534,6 +587,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=2.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR build timing")
+    ap.add_argument("--no-packed", action="store_true", help="skip the packed-launch timing")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-slots", type=int, default=8)

@@ -241,6 +241,17 @@ int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
 int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k,
                 const void *x, void *y);
 
+/* Packed products: y_i = H_S(ops[i], subs[i]) x_i for i < n in one launch per
+ * key width (one grid over 256-row tiles of all pairs), for many small
+ * subspaces whose single products would each fill only a few blocks.  Each
+ * pair's result is bitwise that of qsd_apply_H on path QSD_PATH_SCAN_1.
+ * xs[i], ys[i]: device [D_i][k] in the precision's storage type; all pairs
+ * share precision and k; n <= 256 qubits per pair.  Asynchronous on the
+ * context's stream.  The paper evaluates one subspace at a time; this is the
+ * batching of many products into one launch. */
+int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *subs,
+                      int precision, int32_t k, const void *const *xs, void *const *ys);
+
 /* As qsd_apply_H with x and y in HOST memory: copies x to the device, applies,
  * copies y back and synchronises.  Pinned host buffers copy fastest. */
 int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision,

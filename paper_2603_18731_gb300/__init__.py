@@ -80,6 +80,7 @@ SIGNATURES = [
     ("qsd_subspace_index", C.c_int, [_P, _P, _I64, _P, _P]),
     ("qsd_free_sub", C.c_int, [_P]),
     ("qsd_set_tuning", C.c_int, [_P, _I32, _I64]),
+    ("qsd_apply_H_batch", C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P, _P]),
     ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
     ("qsd_product_path", C.c_int, [_P, _P, _P, _I32, _I64, C.POINTER(C.c_int32)]),
     ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
@@ -280,6 +281,25 @@ class Context:
         self._check(lib().qsd_apply_H(self.handle, op.handle, sub.handle, precision, k, _t_ptr(x), _t_ptr(y)))
         return y
 
+    def apply_H_batch(self, ops, subs, xs, ys=None, precision: int = QSD_FP64):
+        """Packed products y_i = H_S(ops[i], subs[i]) x_i in one launch (per key
+        width); xs: CUDA tensors [D_i] or [D_i, k] with a common k."""
+        dt = self.torch.float64 if precision == QSD_FP64 else self.torch.float32
+        n = len(ops)
+        if not (len(subs) == len(xs) == n):
+            raise ValueError("ops, subs and xs must have the same length")
+        ks = {1 if x.dim() == 1 else int(x.shape[1]) for x in xs}
+        if len(ks) > 1 or any(x.dtype != dt or not x.is_contiguous() for x in xs):
+            raise ValueError(f"xs must be contiguous {dt} tensors with one column count")
+        k = ks.pop() if ks else 1
+        if ys is None:
+            ys = [self.empty(tuple(x.shape), dt) for x in xs]
+        arr = C.c_void_p * max(n, 1)
+        self._check(lib().qsd_apply_H_batch(self.handle, n, arr(*[o.handle for o in ops]),
+                                            arr(*[s_.handle for s_ in subs]), precision, k,
+                                            arr(*[_t_ptr(x) for x in xs]), arr(*[_t_ptr(y) for y in ys])))
+        return ys
+
     def apply_H_host(self, op: Operator, sub: Subspace, x: np.ndarray, precision: int = QSD_FP64,
                      out: np.ndarray | None = None) -> np.ndarray:
         dt = np.float64 if precision == QSD_FP64 else np.float32
@@ -323,6 +343,14 @@ class Context:
         self._check(lib().qsd_rayleigh_quotient_noalloc(self.handle, op.handle, sub.handle, _t_ptr(u),
                                                         _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def csr_size(self, op: Operator, sub: Subspace, full: bool = False) -> int:
+        """Pass 1 of the CSR build: the number of stored entries (the counts
+        are kept in the context for the next ``to_csr`` of the same pair)."""
+        nnz = C.c_int64(0)
+        self._check(lib().qsd_to_csr(self.handle, op.handle, sub.handle, 1 if full else 0, C.byref(nnz), None,
+                                     None, 32, None, None))
+        return int(nnz.value)
 
     def to_csr(self, op: Operator, sub: Subspace, full: bool = False, index_bits: int = 32,
                complex_data: bool = False):

@@ -575,6 +575,59 @@ int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, c
     });
 }
 
+int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *subs, int precision, int32_t k,
+                      const void *const *xs, void *const *ys) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        if (n < 0 || (n > 0 && (!ops || !subs || !xs || !ys)) || k < 1 || precision < QSD_FP64 ||
+            precision > QSD_FP32_DOT2)
+            fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_batch: bad n, arrays, k or precision");
+        set_device(ctx);
+        // pairs by key width; empty subspaces need no work
+        std::map<int, std::vector<int>> by_w;
+        std::vector<const double *> diag(n);
+        for (int i = 0; i < n; ++i) {
+            check_pair(ctx, ops[i], subs[i]);
+            if (!ops[i]->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_apply_H_batch: complex operator");
+            if (ops[i]->W > kMaxWordsStatic) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_batch: more than 256 qubits");
+            if (subs[i]->D == 0) continue;
+            if (!xs[i] || !ys[i]) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_batch: NULL vector");
+            diag[i] = get_binding(ctx, ops[i], subs[i])->diag.as<double>();
+            by_w[ops[i]->W].push_back(i);
+        }
+        cudaStream_t s = ctx->stream;
+        for (auto &[W, idx] : by_w) {
+            const int m = (int)idx.size();
+            std::vector<ApplyParams> hp(m);
+            std::vector<int64_t> t0(m);
+            int64_t tiles = 0;
+            for (int j = 0; j < m; ++j) {
+                t0[j] = tiles;
+                tiles += (subs[idx[j]]->D + 255) / 256;
+            }
+            if (tiles >= (int64_t)0x7fffffff) fail(QSD_ERR_CAPACITY, "qsd_apply_H_batch: too many rows");
+            DevBuf dp, dt;
+            dp.alloc_async((size_t)m * sizeof(ApplyParams), s);
+            dt.alloc_async((size_t)m * 8, s);
+            QSD_CUDA(cudaMemcpyAsync(dt.p, t0.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+            for (int64_t c = 0; c < k;) {
+                const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
+                for (int j = 0; j < m; ++j) {
+                    const int i = idx[j];
+                    hp[j] = make_params(ctx, ops[i], subs[i], diag[i], k, xs[i], ys[i]);
+                    hp[j].col0 = c;
+                }
+                // pageable source: the copy is staged before the call returns
+                QSD_CUDA(cudaMemcpyAsync(dp.p, hp.data(), (size_t)m * sizeof(ApplyParams), cudaMemcpyHostToDevice,
+                                         s));
+                launch_apply_batch(dp.as<ApplyParams>(), dt.as<int64_t>(), m, tiles, W, KB, precision, s);
+                c += KB;
+            }
+        }
+    });
+}
+
 int qsd_apply_H_host(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, const void *x_host,
                      void *y_host) {
     if (!ctx) return QSD_ERR_INVALID_ARG;

@@ -32,6 +32,7 @@ constexpr int kTableBitsMax = 5;
 constexpr uint32_t kGroupScan = 0x80u;
 constexpr int kMsobShift = 16;         // GroupRec::info bits 16..27: most significant flipped qubit
 constexpr uint32_t kMsobMask = 0xfffu;
+constexpr uint32_t kNoTable = 0xffffffffu;
 
 // Groups per batch (bucket loads in flight per lane) and the minimum resident
 // blocks of 256 threads per SM asked of the compiler, per key width W, for the
@@ -50,7 +51,8 @@ struct __align__(16) GroupRec {
     uint64_t pos;   // table groups: support qubits, 12 bits each, ascending
     uint32_t off;   // table groups: offset of the 2^nb amplitudes
     uint32_t info;  // bits 0..2: nb; kGroupScan: scan group; bits 16..27: MSOB
-    uint64_t F0;    // word 0 of F
+    uint32_t nzmask;  // table groups: bit l set iff the amplitude of pattern l is nonzero
+    uint32_t pad;
 };
 
 struct ApplyParams {
@@ -190,20 +192,22 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
         uint4 tb[U];
         uint64_t bidx[U];
         uint32_t tag[U];
+        uint32_t aidx[U];  // table groups: amplitude index; kNoTable: a[u] holds the element
         bool need[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t g = g0 + u;
             bool nz = false;
+            aidx[u] = kNoTable;
             a[u] = 0.0;
             ah[u] = al[u] = 0.f;
             uint64_t hF = 0;
             if (g < p.G) {
                 const ulonglong2 *rp = reinterpret_cast<const ulonglong2 *>(p.grec + g);
                 const ulonglong2 r0 = __ldg(rp);
-                const uint64_t r1x = __ldg(reinterpret_cast<const unsigned long long *>(rp + 1));
+                const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(rp + 1));
                 hF = r0.x;
-                const uint32_t off = (uint32_t)r1x, info = (uint32_t)(r1x >> 32);
+                const uint32_t off = r1.x, info = r1.y, nzm = r1.z;
                 bool lower = true;
                 if (SYM) {
                     const int qm = (int)((info >> kMsobShift) & kMsobMask);
@@ -227,11 +231,17 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                             }
                         }
                     }
-                    if (PREC == QSD_FP32_DOT2) {
+                    if (KB > 1) {
+                        // block products: the pattern's nonzero bit decides
+                        // the lookup and the amplitude is read only for a hit
+                        // (k = 1 keeps the load here: fewer live registers)
+                        nz = (nzm >> l) & 1u;
+                        aidx[u] = off + (uint32_t)l;
+                    } else if (PREC == QSD_FP32_DOT2) {
                         const float2 f = __ldg(p.ampf + off + l);
                         ah[u] = f.x;
                         al[u] = f.y;
-                        nz = (__float_as_uint(f.x) << 1) != 0u;
+                        nz = (nzm >> l) & 1u;
                     } else {
                         a[u] = __ldg(p.amp + off + l);
                         nz = ((uint64_t)__double_as_longlong(a[u]) << 1) != 0ull;
@@ -244,8 +254,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                         al[u] = (float)(a[u] - (double)ah[u]);
                     }
                 }
-            }
-            need[u] = active && nz;
+            }            need[u] = active && nz;
             if (need[u]) {
                 bidx[u] = hash_bucket(hr ^ hF, p.hv.shift, tag[u]);
                 tb[u] = load_tags(p.hv.tags, bidx[u]);
@@ -259,14 +268,22 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             const bool full = bucket_full(tb[u]);
             if (!tag_any(tb[u], tag[u]) && !full) continue;  // absent: the common case
             const uint32_t match = tag_match(tb[u], tag[u]);
-            const GroupRec *rp = p.grec + g;
             uint64_t c[W];
-            c[0] = key[0] ^ __ldg(&rp->F0);
+            c[0] = key[0] ^ __ldg(p.gF + g);
 #pragma unroll
             for (int w = 1; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
             int64_t idx = verify_matches<W>(p.hv, bidx[u], match, c);
             if (idx < 0 && full) idx = probe_from<W>(p.hv, bidx[u], tag[u], c, p.err);
             if (idx < 0) continue;
+            if (KB > 1 && aidx[u] != kNoTable) {
+                if (PREC == QSD_FP32_DOT2) {
+                    const float2 f = __ldg(p.ampf + aidx[u]);
+                    ah[u] = f.x;
+                    al[u] = f.y;
+                } else {
+                    a[u] = __ldg(p.amp + aidx[u]);
+                }
+            }
             const TIO *xc = x + idx * p.ld + p.col0;
             if (PREC == QSD_FP32_DOT2) {
 #pragma unroll
@@ -384,6 +401,11 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
 // Launch one (W, R, KB) variant of precision mode PREC.
 template <int PREC>
 void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
+// Packed group-scan products of n pairs (W <= 4, one lane per row): params
+// and tile0 (first tile of each pair, ascending, tile0[0] = 0) in device
+// memory; `tiles` blocks of 256 rows in total.
+void launch_apply_batch(const ApplyParams *params, const int64_t *tile0, int n, int64_t tiles, int W, int KB,
+                        int precision, cudaStream_t s);
 // Half-evaluation product (FP64, Hermitian real operators, W <= 4); zeroes
 // the launch's columns of y first.
 void launch_apply_sym(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);

@@ -343,7 +343,9 @@ template <typename IDX>
 void sort_rows(qsd_ctx ctx, int64_t D, int64_t nnz, const uint32_t *off, const uint32_t *len, IDX *ind, double *re,
                double *im) {
     cudaStream_t s = ctx->stream;
-    DevBuf rows((size_t)D * 4), n_long(4);
+    DevBuf rows, n_long;
+    rows.alloc_async((size_t)D * 4, s);
+    n_long.alloc_async(4, s);
     QSD_CUDA(cudaMemsetAsync(n_long.p, 0, 4, s));
     k_sort_short<IDX><<<blocks_for(D, 256), 256, 0, s>>>(D, off, len, ind, re, im, rows.as<uint32_t>(),
                                                          n_long.as<uint32_t>());
@@ -388,10 +390,11 @@ static void csr_count(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower) {
         QSD_LAUNCH_CHECK();
     }
     const size_t n4 = (size_t)std::max<int64_t>(D, 1) * 4;
-    st.cnt.alloc(n4);
-    st.cnt_up.alloc(n4);
-    st.len.alloc(n4);
-    st.off.alloc(n4);
+    // stream-ordered: no device-wide synchronisation for the temporaries
+    st.cnt.alloc_async(n4, s);
+    st.cnt_up.alloc_async(n4, s);
+    st.len.alloc_async(n4, s);
+    st.off.alloc_async(n4, s);
     int64_t nnz = 0;
     if (D > 0) {
         QSD_CUDA(cudaMemsetAsync(st.cnt.p, 0, n4, s));
@@ -436,7 +439,8 @@ int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr,
     c.cnt = st.cnt.as<uint32_t>();
     c.cnt_up = st.cnt_up.as<uint32_t>();
     c.off = st.off.as<uint32_t>();
-    DevBuf cursor((size_t)D * 4);
+    DevBuf cursor;
+    cursor.alloc_async((size_t)D * 4, s);
     QSD_CUDA(cudaMemsetAsync(cursor.p, 0, (size_t)D * 4, s));
     c.cursor = cursor.as<uint32_t>();
     c.indices = indices;

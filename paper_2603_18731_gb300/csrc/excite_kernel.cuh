@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
         const double amp = scan_amp<W>(p, g, key);
         if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
         uint64_t F[W];
-        F[0] = __ldg(&p.grec[g].F0);
+        F[0] = __ldg(p.gF + g);
 #pragma unroll
         for (int w = 1; w < W; ++w) F[w] = __ldg(p.gF + (size_t)w * p.G + g);
         contribute(amp, F, __ldg(&p.grec[g].hF));

@@ -174,7 +174,8 @@ __global__ void k_group_records(int W, int64_t G, const int32_t *__restrict__ gr
     if (g >= G) return;
     GroupRec R;
     R.hF = ghash[g];
-    R.F0 = gF[g];
+    R.nzmask = 0;
+    R.pad = 0;
     // most significant flipped qubit (the half-evaluation product's filter)
     uint32_t msob = 0;
     for (int w = 0; w < W; ++w)
@@ -210,6 +211,7 @@ __global__ void k_group_records(int W, int64_t G, const int32_t *__restrict__ gr
             if (ok) a += (par & 1) ? -tphi[t] : tphi[t];
         }
         amp[R.off + l] = a;
+        if (((uint64_t)__double_as_longlong(a) << 1) != 0ull) R.nzmask |= 1u << l;
         const float hi = (float)a;
         ampf[R.off + l] = make_float2(hi, (float)(a - (double)hi));
     }
