@@ -150,6 +150,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is none)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Units processed by all ranks (each does the same work) per second of
+    the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def run_gpu(args):
     import torch
     import paper_2603_18731_gb300 as q
@@ -225,12 +242,9 @@ def run_gpu(args):
     head_x, head_prec, k1 = (xb32, q.QSD_FP32_MIXED, 16) if args.workload == "chem" else (x64, q.QSD_FP64, 1)
     with ClockSampler(local) as clk:
         ms64, all64, wall64 = time_variant(head_x, head_prec, args.steps, args.warmup)
-    t_max = ms64
-    if dist:
-        t = torch.tensor([ms64], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * elems * k1 / (t_max * 1e-3) / 1e9
+    # replicas: the job takes as long as its slowest rank
+    t_max = max_over_ranks(ms64, dist, dev)
+    value = whole_job_rate(elems * k1, t_max * 1e-3, world) / 1e9
     variants = {}
     vsteps = max(3, min(args.steps, 20))
     vlist = [("fp32_mixed_k1", x32, q.QSD_FP32_MIXED, 1), ("fp32_dot2_k1", x32, q.QSD_FP32_DOT2, 1),
@@ -282,8 +296,9 @@ def run_gpu(args):
         t0 = time.perf_counter()
         ctx.apply_H_host(h, sub, xh, head_prec, out=yh)
         et.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(et))
-    e2e = {"value": world * elems * k1 / e2e_s / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": int(xh.nbytes),
+    e2e_s = max_over_ranks(float(np.mean(et)), dist, dev)
+    e2e = {"value": whole_job_rate(elems * k1, e2e_s, world) / 1e9, "unit": "Gelem/s",
+           "h2d_bytes_per_step": int(xh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes), "ms_per_step": e2e_s * 1e3}
 
     # one full ground-state solve per precision (not part of the timed steps)
@@ -471,6 +486,9 @@ def run_serve(args, q, local):
         for k, t in enumerate(tickets):
             r = srv.wait(t)
             r["latency_s"] = host_t0 + r["t_done"] - t_arr[k]
+            r["build_s"] = host_t0 + r["t_submit"] - t_arr[k]
+            r["queue_s"] = r["t_admit"] - r["t_submit"]
+            r["run_s"] = r["t_done"] - r["t_admit"]
             r["family"] = pool[order[k]][0]
             res.append(r)
         wall = time.perf_counter() - start
@@ -489,6 +507,8 @@ def run_serve(args, q, local):
         st = srv.stats()
     lat = np.array([r["latency_s"] for r in res]) * 1e3
     ok = [r for r in res if r["status"] == "OK"]
+    phases = {f"{ph}_p50_ms": float(np.percentile([r[f"{ph}_s"] for r in res], 50)) * 1e3
+              for ph in ("build", "queue", "run")}
     fams = {}
     for r in res:
         fams.setdefault(r["family"], []).append(r["latency_s"] * 1e3)
@@ -498,6 +518,8 @@ def run_serve(args, q, local):
            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
            "max_active": args.serve_slots, "budget_bytes": budget, "peak_bytes": st["peak_bytes"],
            "per_family_p50_ms": {k: float(np.percentile(v, 50)) for k, v in fams.items()},
+           "phases": phases,
+           "packed_requests": st["packed_requests"], "packed_chunks": st["packed_chunks"],
            "candidate_dims_min_max": [int(min(dims)), int(max(dims))],
            "precision": "fp32_dot2 + fp64 refinement", "tol": params["tol"],
            "note": "latency = arrival to energy ready, including the request's device subspace build "
