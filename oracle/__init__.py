@@ -65,6 +65,8 @@ def lib():
             L.orc_groups.restype = i64
             L.orc_groups.argtypes = [i32, i64, p, p, p, p, p, i64, p]
             L.orc_target_table.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, i64, p, i64, i64, p]
+            L.orc_row_elements.restype = i64
+            L.orc_row_elements.argtypes = [i32, i32, i64, p, p, p, p, p, p, p, p, p]
             L.orc_csr_count.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, p]
             L.orc_csr_fill.argtypes = [i32, i32, i64, p, p, p, p, p, i64, p, p, p, p, p]
             L.orc_tridiag_min.restype = C.c_double
@@ -204,6 +206,23 @@ def target_table(op, keys: np.ndarray, row0: int = 0, nrows: int | None = None) 
     _check(lib().orc_target_table(op.n_qubits, W, op.n_terms, _ptr(tp), _ptr(oq), _ptr(oc), _ptr(cr),
                                   _ptr(ci), D, _ptr(keys), g.shape[0], _ptr(g), row0, nrows, _ptr(out)))
     return out
+
+
+def row_elements(op, row: np.ndarray):
+    """Row ``row`` ([W] uint64, any bit-string) of H over the whole Hilbert
+    space: (cols [m, W] ascending, elements [m] complex); the diagonal is
+    always listed."""
+    row = np.ascontiguousarray(row, np.uint64)
+    W = row.shape[0]
+    tp, oq, oc, cr, ci = _op_arrays(op)
+    T = op.n_terms
+    cols = np.zeros((T + 1, W), np.uint64)
+    re, im = np.zeros(T + 1), np.zeros(T + 1)
+    m = lib().orc_row_elements(op.n_qubits, W, T, _ptr(tp), _ptr(oq), _ptr(oc), _ptr(cr), _ptr(ci), _ptr(row),
+                               _ptr(cols), _ptr(re), _ptr(im))
+    if m < 0:
+        _check(int(-m))
+    return cols[:m].copy(), re[:m] + 1j * im[:m]
 
 
 def csr(op, keys: np.ndarray):

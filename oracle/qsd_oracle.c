@@ -397,6 +397,66 @@ int orc_target_table(int n, int W, int64_t T, const int64_t *term_ptr,
     return ORC_OK;
 }
 
+/* ------------------------------------------------ one row, any bit-string */
+/* Row `row` of H over the whole Hilbert space (not a subspace): every
+ * distinct column reached by a term with a nonzero coefficient and a nonzero
+ * element, with the summed element, in ascending integer order; the diagonal
+ * (column == row) is always listed.  cols is [T + 1][W], re/im [T + 1].
+ * Returns the number of entries. */
+typedef struct { const uint64_t *col; double re, im; } rowent_t;
+static int rowent_W;
+
+static int rowent_cmp(const void *a, const void *b)
+{
+    const uint64_t *x = ((const rowent_t *)a)->col, *y = ((const rowent_t *)b)->col;
+    for (int w = rowent_W - 1; w >= 0; --w)
+        if (x[w] != y[w]) return x[w] < y[w] ? -1 : 1;
+    return 0;
+}
+
+int64_t orc_row_elements(int n, int W, int64_t T, const int64_t *term_ptr, const int32_t *op_qubit,
+                         const uint8_t *op_code, const double *coef_re, const double *coef_im,
+                         const uint64_t *row, uint64_t *cols, double *re, double *im)
+{
+    int rc = orc_check_operator(n, T, term_ptr, op_qubit, op_code);
+    if (rc) return -(int64_t)rc;
+    uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(T + 1) * (size_t)W);
+    rowent_t *ent = (rowent_t *)malloc(sizeof(rowent_t) * (size_t)(T + 1));
+    int64_t m = 0;
+    memcpy(tmp, row, sizeof(uint64_t) * (size_t)W);
+    ent[m].col = tmp; ent[m].re = 0.0; ent[m].im = 0.0; ++m;
+    for (int64_t t = 0; t < T; ++t) {
+        int p;
+        if (coef_re[t] == 0.0 && (!coef_im || coef_im[t] == 0.0)) continue;
+        uint64_t *c = tmp + (size_t)m * W;
+        if (!word_element(op_qubit + term_ptr[t], op_code + term_ptr[t], term_ptr[t + 1] - term_ptr[t],
+                          row, c, W, &p))
+            continue;
+        mul_ipow(coef_re[t], coef_im ? coef_im[t] : 0.0, p, &ent[m].re, &ent[m].im);
+        ent[m].col = c;
+        ++m;
+    }
+    rowent_W = W;
+    qsort(ent, (size_t)m, sizeof(rowent_t), rowent_cmp);
+    int64_t u = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (u > 0 && rowent_cmp(&ent[u - 1], &ent[i]) == 0) {
+            ent[u - 1].re += ent[i].re;
+            ent[u - 1].im += ent[i].im;
+        } else {
+            ent[u++] = ent[i];
+        }
+    }
+    for (int64_t i = 0; i < u; ++i) {
+        memcpy(cols + (size_t)i * W, ent[i].col, sizeof(uint64_t) * (size_t)W);
+        re[i] = ent[i].re;
+        im[i] = ent[i].im;
+    }
+    free(ent);
+    free(tmp);
+    return u;
+}
+
 /* --------------------------------------------------------------- CSR form */
 /* Entries of row a: the diagonal (always), plus every column in S that at
  * least one term reaches with a nonzero element.  Columns ascending; values

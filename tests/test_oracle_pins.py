@@ -321,3 +321,66 @@ def test_operator_errors():
         oracle.apply(bad_repeat, keys, np.zeros(8))
     with pytest.raises(oracle.OracleError):
         oracle.apply(bad_range, keys, np.zeros(8))
+
+
+# ------------------------------------------------------------------ RAMPS --
+def test_row_elements_match_kronecker():
+    for seed in range(4):
+        n = 7
+        op = wl.random_extended(n, 25, max_weight=4, seed=40 + seed, hermitian=False, real=False)
+        H = brute.full_matrix(op)
+        rng = np.random.default_rng(seed)
+        for r in rng.integers(0, 1 << n, size=6):
+            cols, els = oracle.row_elements(op, np.array([int(r)], np.uint64))
+            got = np.zeros(1 << n, np.complex128)
+            got[cols[:, 0].astype(np.int64)] = els
+            assert int(r) in set(cols[:, 0].tolist())
+            assert np.allclose(got, H[int(r)], atol=1e-13)
+
+
+def _chain_operator(h, d):
+    """Four states 00 -> 01 -> 11 -> 10 (qubit 0 is the low bit) coupled in a
+    chain by controlled flips, diagonals d[0..3]: a tridiagonal H."""
+    terms = [(h[0], [(0, "X"), (1, "0")]),   # 00 <-> 01
+             (h[1], [(1, "X"), (0, "1")]),   # 01 <-> 11
+             (h[2], [(0, "X"), (1, "1")])]   # 11 <-> 10
+    for bits, e in zip(("00", "01", "11", "10"), d):
+        # bits[1] is qubit 0, bits[0] is qubit 1
+        terms.append((e, [(0, bits[1]), (1, bits[0])]))
+    return wl.QubitOperator.from_terms(2, terms)
+
+
+def test_ramps_reproduces_equation_s2():
+    # Supplementary Eq. S2: starting from row 0 with E = H00, the levels of
+    # the recursion are the three printed terms of delta / H00
+    from oracle import ramps
+    h = (0.3, -0.2, 0.25)
+    d = (-5.0, -1.0, 0.5, 2.0)
+    op = _chain_operator(h, d)
+    H00, H11, H22, H33 = d
+    t1 = h[0] ** 2 / (H00 * (H00 - H11))
+    t2 = 1.0 / (H00 * (H00 - H11)) * (h[0] ** 2 / (H00 - H11) * h[1] ** 2 / (H00 - H22))
+    t3 = (1.0 / (H00 * (H00 - H11) * (H00 - H22))
+          * (h[0] ** 2 / (H00 - H11) * h[1] ** 2 / (H00 - H22) * h[2] ** 2 / (H00 - H33)))
+    start = np.array([[0b00]], np.uint64)
+    keys, levels = ramps.ramps(op, start, H00, 0.0)
+    assert [list(lv) for lv in levels[:3]] == [[0b01], [0b11], [0b10]]
+    assert levels[0][0b01] == pytest.approx(t1, rel=1e-14)
+    assert levels[1][0b11] == pytest.approx(t2, rel=1e-14)
+    assert levels[2][0b10] == pytest.approx(t3, rel=1e-14)
+    assert keys[:, 0].tolist() == [0, 1, 2, 3]
+    # the tolerance cuts the chain after the last level above it
+    keys, levels = ramps.ramps(op, start, H00, 0.5 * (abs(t2) + abs(t3)))
+    assert keys[:, 0].tolist() == [0b00, 0b01, 0b11]
+    keys, _ = ramps.ramps(op, start, H00, 2 * abs(t1))
+    assert keys[:, 0].tolist() == [0]
+
+
+def test_ramps_restricted_and_level_limit():
+    from oracle import ramps
+    op = _chain_operator((0.3, -0.2, 0.25), (-5.0, -1.0, 0.5, 2.0))
+    start = np.array([[0]], np.uint64)
+    keys, _ = ramps.ramps(op, start, -5.0, 0.0, restrict=np.array([[0], [1], [2]], np.uint64))
+    assert keys[:, 0].tolist() == [0, 1]  # 11 (= 3) is outside the allowed set, so 10 is never reached
+    keys, levels = ramps.ramps(op, start, -5.0, 0.0, max_levels=2)
+    assert len(levels) == 2 and keys[:, 0].tolist() == [0, 1, 3]
