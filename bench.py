@@ -334,6 +334,12 @@ def run_gpu(args):
             csr[name] = {"ms": 1e3 * float(np.mean(ts)), "count_pass_ms": 1e3 * float(np.mean(tc)), "nnz": nnz}
         csr["msob_speedup"] = csr["full"]["ms"] / csr["msob_lower"]["ms"]
 
+    # RAMPS refinement from one reference bit-string (the lowest-diagonal
+    # row of the workload's subspace), E = its diagonal, unrestricted
+    ramps_out = None
+    if not args.no_ramps and W <= 4 and args.workload != "chem":
+        ramps_out = run_ramps(ctx, h, sub, op, args.ramps_tau)
+
     # packed launches: many small products (64 walk subspaces of the
     # workload's family, D log-uniform in [500, 5000]) as one launch against
     # one launch per pair
@@ -344,6 +350,9 @@ def run_gpu(args):
     serve = None
     if not args.no_serve:
         serve = run_serve(args, q, local)
+        if args.serve_compare:
+            other = 0 if args.serve_pack_rows else 32768
+            serve["compare_pack_rows_%d" % other] = run_serve(args, q, local, pack_rows=other)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -359,7 +368,7 @@ def run_gpu(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "packed": packed, "serve": serve,
+            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "ramps": ramps_out, "packed": packed, "serve": serve,
             "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
         }
         print(json.dumps(line))
@@ -367,6 +376,38 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_ramps(ctx, h, sub, op, tau, max_levels=8, reps=3):
+    import torch
+    d = ctx.diagonal(h, sub)
+    r0 = int(torch.argmin(d).item())
+    E = float(d[r0].item())
+    keys = ctx.subspace_keys(sub)[r0:r0 + 1]
+    start = ctx.build_subspace(op.n_qubits, keys)
+    ts, out, info = [], None, None
+    for rep in range(reps + 1):
+        ctx.synchronize()
+        t0 = time.perf_counter()
+        out, info = ctx.ramps(h, start, E, tau, max_levels=max_levels, max_rows=4_000_000)
+        ctx.synchronize()
+        if rep:
+            ts.append(time.perf_counter() - t0)
+        if rep < reps:
+            out.free()
+    G = h.info()["n_groups"]
+    # rows expanded: the start row and every level's rows, except the last
+    # level's when the level or row limit ended the recursion
+    lr = info["level_rows"]
+    pairs = 1 + sum(lr) - (lr[-1] if lr and (info["stopped_by_limit"] or info["truncated"]) else 0)
+    ms = 1e3 * float(np.mean(ts))
+    res = {"tau": tau, "E": E, "ms": ms, "rows_out": info["rows_out"], "levels": info["levels"],
+           "level_rows": info["level_rows"], "candidates": info["candidates"],
+           "stopped_by_limit": info["stopped_by_limit"], "truncated": info["truncated"],
+           "row_group_pairs_per_s": pairs * G / (ms * 1e-3)}
+    out.free()
+    start.free()
+    return res
 
 
 def run_packed(ctx, q, op, workload, n_pairs=64, reps=20):
@@ -446,10 +487,11 @@ def serve_pool(n_pool: int, seed: int, dmin: float, dmax: float):
     return pool
 
 
-def run_serve(args, q, local):
+def run_serve(args, q, local, pack_rows=None):
     """512 Poisson arrivals at 0.8x the measured closed-loop capacity; latency
     from arrival to energy ready, including the request's device build."""
     import torch
+    pack_rows = args.serve_pack_rows if pack_rows is None else pack_rows
     rng = np.random.default_rng(args.serve_seed)
     pool = serve_pool(args.serve_pool, args.serve_seed, 1e3, 2e6)
     client = q.create(local)
@@ -495,6 +537,7 @@ def run_serve(args, q, local):
         return res, wall
 
     with q.Server(srvctx, budget_bytes=budget, max_active=args.serve_slots) as srv:
+        srv.set_pack_rows(pack_rows)
         host_t0 = time.perf_counter()
         # closed-loop capacity: every pool item submitted at once
         burst, t_burst = run(list(range(len(pool))), [0.0] * len(pool), srv, host_t0)
@@ -518,7 +561,7 @@ def run_serve(args, q, local):
            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
            "max_active": args.serve_slots, "budget_bytes": budget, "peak_bytes": st["peak_bytes"],
            "per_family_p50_ms": {k: float(np.percentile(v, 50)) for k, v in fams.items()},
-           "phases": phases,
+           "phases": phases, "pack_rows": pack_rows,
            "packed_requests": st["packed_requests"], "packed_chunks": st["packed_chunks"],
            "candidate_dims_min_max": [int(min(dims)), int(max(dims))],
            "precision": "fp32_dot2 + fp64 refinement", "tol": params["tol"],
@@ -610,9 +653,15 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR build timing")
     ap.add_argument("--no-packed", action="store_true", help="skip the packed-launch timing")
+    ap.add_argument("--no-ramps", action="store_true", help="skip the RAMPS timing")
+    ap.add_argument("--ramps-tau", type=float, default=1e-7)
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-pack-rows", type=int, default=0,
+                    help="requests up to this many rows run in packed chunks (0: never)")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="also run the served stream with packing switched the other way")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-seed", type=int, default=5)
     args = ap.parse_args()

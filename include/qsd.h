@@ -182,6 +182,37 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
                int64_t *indptr, void *indices, int32_t index_bits,
                double *data_re, double *data_im);
 
+/* ------------------------------------------------------------------ RAMPS */
+/* Subspace refinement RAMPS (Supplementary, "Recursive algorithm for a
+ * minimal perturbative subspace", Algorithm S1; expansion Eq. S2), run level
+ * by level on the device with every (row, group) pair of a level in parallel
+ * (the paper's implementation is serial).  From the rows of `start` with
+ * prefactor 1/E, each level adds every column b_k reached from a level row
+ * b_j through an off-diagonal group with |amp| > tau, amp = pre_j
+ * |H_jk|^2 / (E - H_kk), H_kk the diagonal of b_k; the added rows carry
+ * prefactor amp / (E - H_kk) into the next level.  Rows already in the
+ * output are not revisited; a column reached from several rows of a level
+ * keeps its largest |amp|; a column with H_kk = E is added and not expanded.
+ * restrict_to (may be NULL): only its rows may be added (the restricted
+ * variant, Supplementary).  max_levels ends the recursion (the paper's
+ * maximum number of recursions); max_rows > 0 stops after the level that
+ * reaches that many output rows.  *out receives a new subspace handle with
+ * the start rows and every added row (caller frees it).  Elements may be
+ * complex (|H_jk|^2 uses the modulus).  Errors: QSD_ERR_INVALID_ARG (E == 0
+ * or not finite, tau < 0, n > 256 qubits), QSD_ERR_CAPACITY (2^32 candidate
+ * columns in one level). */
+typedef struct {
+    int32_t levels;            /* levels run */
+    int32_t stopped_by_limit;  /* 1: max_levels ended a recursion that had rows left */
+    int32_t truncated;         /* 1: max_rows was reached */
+    int32_t reserved;
+    int64_t rows_out;          /* rows of *out */
+    int64_t candidates;        /* columns above tau over all levels, before merging */
+    int64_t level_rows[64];    /* rows added by each of the first 64 levels */
+} qsd_ramps_info;
+int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32_t max_levels,
+              qsd_sub restrict_to, int64_t max_rows, qsd_sub *out, qsd_ramps_info *info);
+
 /* ------------------------------------------------------------------ tuning */
 #define QSD_TUNE_APPLY_PATH     1  /* 0 auto; 1 per-row scan of all groups; 2 excitation
                                       index (ladder groups enumerated from each row's
@@ -347,7 +378,8 @@ int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub,
  * diagonal and work vectors; the subspace and operator tables are the
  * caller's) fits in `budget_bytes` next to the admitted ones (a request
  * larger than the budget runs alone).  Each admitted request has its own
- * stream and advances asynchronously -- graph-captured chunks of Lanczos
+ * stream (small requests: a shared stream and packed launches, see
+ * qsd_server_set_pack_rows) and advances asynchronously -- graph-captured chunks of Lanczos
  * steps, Ritz vector and FP64 residual, FP64 refinement restarts -- so the
  * work of all admitted requests overlaps on the device and requests that
  * arrive while others run start as soon as a slot and memory free up.
@@ -359,6 +391,8 @@ typedef struct qsd_server_s *qsd_server;
 typedef struct {
     int64_t queued, active, completed, failed, admitted;
     uint64_t bytes_in_use, peak_bytes, budget_bytes;
+    int64_t packed_requests;  /* requests admitted into a pack of small requests */
+    int64_t packed_chunks;    /* packed chunks enqueued (each serves every waiting member) */
 } qsd_server_stats;
 
 int qsd_server_create(qsd_ctx ctx, size_t budget_bytes, int32_t max_active, qsd_server *out);
@@ -379,6 +413,15 @@ int qsd_server_cancel(qsd_server srv, uint64_t ticket);
 /* Forget a finished request (QSD_PENDING while it is not retired yet). */
 int qsd_server_release(qsd_server srv, uint64_t ticket);
 int qsd_server_get_stats(qsd_server srv, qsd_server_stats *stats);
+/* Requests with at most `rows` rows (and n <= 256 qubits) join the packs of
+ * small requests: they share one stream and their Lanczos chunks run as
+ * packed launches (one launch per kernel for all waiting members, the
+ * product on the one-lane group scan).  0 (the default) disables packing.
+ * Packed chunks are plain launches that advance every member together, so
+ * they pay only when many more small requests are active than the device
+ * runs concurrently; with a few slots the per-request streams replaying
+ * captured graphs are faster.  Applies to requests admitted afterwards. */
+int qsd_server_set_pack_rows(qsd_server srv, int64_t rows);
 const char *qsd_server_last_error(qsd_server srv);
 /* Cancel what is queued or running, wait for the scheduler, free everything. */
 int qsd_server_destroy(qsd_server srv);

@@ -55,10 +55,16 @@ class LanczosInfo(C.Structure):
                 ("energy_unrefined", C.c_double), ("status", C.c_int32), ("applies", C.c_int32)]
 
 
+class RampsInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("stopped_by_limit", C.c_int32), ("truncated", C.c_int32),
+                ("reserved", C.c_int32), ("rows_out", C.c_int64), ("candidates", C.c_int64),
+                ("level_rows", C.c_int64 * 64)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("admitted", C.c_int64), ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64),
-                ("budget_bytes", C.c_uint64)]
+                ("budget_bytes", C.c_uint64), ("packed_requests", C.c_int64), ("packed_chunks", C.c_int64)]
 
 
 _lib = None
@@ -82,6 +88,7 @@ SIGNATURES = [
     ("qsd_set_tuning", C.c_int, [_P, _I32, _I64]),
     ("qsd_apply_H_batch", C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P, _P]),
     ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
+    ("qsd_ramps", C.c_int, [_P, _P, _P, _D, _D, _I32, _P, _I64, C.POINTER(_P), C.POINTER(RampsInfo)]),
     ("qsd_product_path", C.c_int, [_P, _P, _P, _I32, _I64, C.POINTER(C.c_int32)]),
     ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
     ("qsd_apply_H_host", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
@@ -100,6 +107,7 @@ SIGNATURES = [
     ("qsd_server_cancel", C.c_int, [_P, _U64]),
     ("qsd_server_release", C.c_int, [_P, _U64]),
     ("qsd_server_get_stats", C.c_int, [_P, C.POINTER(ServerStats)]),
+    ("qsd_server_set_pack_rows", C.c_int, [_P, _I64]),
     ("qsd_server_last_error", C.c_char_p, [_P]),
     ("qsd_server_destroy", C.c_int, [_P]),
 ]
@@ -344,6 +352,18 @@ class Context:
                                                         _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
 
+    def ramps(self, op: Operator, start: Subspace, E: float, tau: float, max_levels: int = 16,
+              restrict: Subspace | None = None, max_rows: int = 0):
+        """RAMPS refinement from the rows of ``start``: (new Subspace, info)."""
+        h = C.c_void_p()
+        info = RampsInfo()
+        self._check(lib().qsd_ramps(self.handle, op.handle, start.handle, float(E), float(tau), int(max_levels),
+                                    restrict.handle if restrict is not None else None, int(max_rows), C.byref(h),
+                                    C.byref(info)))
+        d = {f: getattr(info, f) for f, _ in RampsInfo._fields_ if f not in ("level_rows", "reserved")}
+        d["level_rows"] = [int(info.level_rows[i]) for i in range(min(info.levels, 64))]
+        return Subspace(self, h, start.n_qubits, int(info.rows_out)), d
+
     def csr_size(self, op: Operator, sub: Subspace, full: bool = False) -> int:
         """Pass 1 of the CSR build: the number of stored entries (the counts
         are kept in the context for the next ``to_csr`` of the same pair)."""
@@ -448,6 +468,13 @@ class Server:
 
     def release(self, ticket: int) -> bool:
         return lib().qsd_server_release(self.handle, ticket) == QSD_OK
+
+    def set_pack_rows(self, rows: int):
+        """Requests with at most ``rows`` rows join the packs of small requests
+        (packed launches); 0 disables packing."""
+        rc = lib().qsd_server_set_pack_rows(self.handle, int(rows))
+        if rc != QSD_OK:
+            self._err(rc)
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -2,6 +2,7 @@
 // error translation, and the host side of the product dispatch.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 
 #include "excite.cuh"
@@ -250,6 +251,10 @@ bool capturing(cudaStream_t s) {
 }
 
 }  // namespace
+
+ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y) {
+    return make_params(ctx, op, sub, diag, k, x, y);
+}
 
 // Path for (op, sub, precision, KB): a forced choice, the tuned choice in
 // the context's cache, a fresh measurement (when allowed), or the heuristic.
@@ -755,6 +760,32 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
             fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_to_csr: complex operator needs data_im");
         Binding *b = get_binding(ctx, op, sub);
         *nnz_out = to_csr(ctx, op, sub, lower, indptr, indices, index_bits, data_re, data_im, b->diag.as<double>());
+    });
+}
+
+int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32_t max_levels,
+              qsd_sub restrict_to, int64_t max_rows, qsd_sub *out, qsd_ramps_info *info) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, start);
+        if (restrict_to) check_pair(ctx, op, restrict_to);
+        if (!out || !info) fail(QSD_ERR_INVALID_ARG, "qsd_ramps: NULL out or info");
+        if (!(E != 0.0 && std::isfinite(E)) || !(tau >= 0.0) || max_levels < 0)
+            fail(QSD_ERR_INVALID_ARG, "qsd_ramps: E must be finite and nonzero, tau >= 0, max_levels >= 0");
+        if (op->W > kMaxWordsStatic) fail(QSD_ERR_INVALID_ARG, "qsd_ramps: more than 256 qubits");
+        set_device(ctx);
+        auto *sub = new qsd_sub_s();
+        sub->ctx = ctx;
+        sub->n_qubits = op->n_qubits;
+        sub->W = op->W;
+        try {
+            ramps(ctx, op, start, E, tau, max_levels, restrict_to, max_rows, sub, info);
+        } catch (...) {
+            delete sub;
+            throw;
+        }
+        *out = sub;
     });
 }
 

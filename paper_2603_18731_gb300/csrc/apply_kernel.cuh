@@ -401,6 +401,9 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
 // Launch one (W, R, KB) variant of precision mode PREC.
 template <int PREC>
 void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
+// Product parameters of one (operator, subspace) pair with x, y of row
+// stride k (column 0 first).
+ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y);
 // Packed group-scan products of n pairs (W <= 4, one lane per row): params
 // and tile0 (first tile of each pair, ascending, tile0[0] = 0) in device
 // memory; `tiles` blocks of 256 rows in total.

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
+#include <map>
 #include <memory>
 
 #include "lanczos.cuh"
@@ -63,31 +65,36 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
     w[i] = v0 ? v0[i] : uniform_pm1(seed, (uint64_t)i);
 }
 
+// Kernel bodies take their block index `vb` and block count `vg` as
+// arguments, so that a packed launch (below) can run the same arithmetic for
+// several jobs in one grid.
+
 // partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j
 template <typename TV, typename TU>
-__global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                         const TU *__restrict__ u, double *partial) {
-    __shared__ double sh[32];
-    const int nvec = *jdev + 1;
-    const int B = gridDim.x;
+__device__ void gemv_t_body(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u,
+                            double *partial, int vb, int B, double *sh) {
     const int64_t chunk = (D + B - 1) / B;
-    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(D, r0 + chunk);
+    const int64_t r0 = (int64_t)vb * chunk, r1 = min(D, r0 + chunk);
     for (int i = 0; i < nvec; ++i) {
         const TV *vi = V + (size_t)i * D;
         double s = 0.0;
         for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) s = fma((double)vi[r], (double)u[r], s);
         s = block_sum(s, sh);
-        if (threadIdx.x == 0) partial[(size_t)i * B + blockIdx.x] = s;
+        if (threadIdx.x == 0) partial[(size_t)i * B + vb] = s;
     }
+}
+
+template <typename TV, typename TU>
+__global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
+                         const TU *__restrict__ u, double *partial) {
+    __shared__ double sh[32];
+    gemv_t_body<TV, TU>(V, D, *jdev + 1, u, partial, blockIdx.x, gridDim.x, sh);
 }
 
 // h[i] = sum_b partial[i][b] in fixed order (block i; blocks past j exit);
 // alpha[j] += h[j]
-__global__ void k_reduce_rows(const double *__restrict__ partial, const int *__restrict__ jdev, int B, double *h,
-                              double *alpha) {
-    __shared__ double sh[32];
-    const int j = *jdev;
-    const int i = blockIdx.x;
+__device__ void reduce_rows_body(const double *__restrict__ partial, int j, int B, double *h, double *alpha, int i,
+                                 double *sh) {
     if (i > j) return;
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += partial[(size_t)i * B + b];
@@ -98,50 +105,75 @@ __global__ void k_reduce_rows(const double *__restrict__ partial, const int *__r
     }
 }
 
+__global__ void k_reduce_rows(const double *__restrict__ partial, const int *__restrict__ jdev, int B, double *h,
+                              double *alpha) {
+    __shared__ double sh[32];
+    reduce_rows_body(partial, *jdev, B, h, alpha, blockIdx.x, sh);
+}
+
 // w[r] = u[r] - sum_{i<=j} V[i][r] h[i]
 template <typename TV, typename TU>
-__global__ void k_gemv_sub(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                           const double *__restrict__ h, const TU *u, double *w) {
-    extern __shared__ double hs[];
-    const int nvec = *jdev + 1;
+__device__ void gemv_sub_body(const TV *__restrict__ V, int64_t D, int nvec, const double *__restrict__ h,
+                              const TU *u, double *w, int vb, double *hs) {
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)vb * blockDim.x + threadIdx.x;
     if (r >= D) return;
     double acc = (double)u[r];
     for (int i = 0; i < nvec; ++i) acc = fma(-(double)V[(size_t)i * D + r], hs[i], acc);
     w[r] = acc;
 }
 
-__global__ void k_sq_partial(const double *__restrict__ w, int64_t D, double *partial) {
-    __shared__ double sh[32];
+template <typename TV, typename TU>
+__global__ void k_gemv_sub(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
+                           const double *__restrict__ h, const TU *u, double *w) {
+    extern __shared__ double hs[];
+    gemv_sub_body<TV, TU>(V, D, *jdev + 1, h, u, w, blockIdx.x, hs);
+}
+
+__device__ void sq_partial_body(const double *__restrict__ w, int64_t D, double *partial, int vb, int vg,
+                                double *sh) {
     double s = 0.0;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t r = (int64_t)vb * blockDim.x + threadIdx.x; r < D; r += (int64_t)vg * blockDim.x)
         s = fma(w[r], w[r], s);
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[vb] = s;
+}
+
+__global__ void k_sq_partial(const double *__restrict__ w, int64_t D, double *partial) {
+    __shared__ double sh[32];
+    sq_partial_body(w, D, partial, blockIdx.x, gridDim.x, sh);
 }
 
 // out[jdev ? *jdev + 1 : 0] = sqrt(sum partial)
-__global__ void k_sqrt_sum(const double *__restrict__ partial, int B, double *out, const int *__restrict__ jdev) {
-    __shared__ double sh[32];
+__device__ void sqrt_sum_body(const double *__restrict__ partial, int B, double *out, double *sh) {
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += partial[b];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[jdev ? *jdev + 1 : 0] = sqrt(s);
+    if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void k_sqrt_sum(const double *__restrict__ partial, int B, double *out, const int *__restrict__ jdev) {
+    __shared__ double sh[32];
+    sqrt_sum_body(partial, B, out + (jdev ? *jdev + 1 : 0), sh);
 }
 
 // v = w / nrm[jdev ? *jdev + 1 : 0] into V[j+1] (when j + 1 <= m) and vcur
 template <typename TV>
-__global__ void k_next(const double *__restrict__ w, const double *__restrict__ nrm, const int *__restrict__ jdev,
-                       int64_t D, int m, TV *V, TV *vcur) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void next_body(const double *__restrict__ w, double s, int j1, int64_t D, int m, TV *V, TV *vcur,
+                          int vb) {
+    const int64_t r = (int64_t)vb * blockDim.x + threadIdx.x;
     if (r >= D) return;
-    const int j1 = jdev ? *jdev + 1 : 0;
-    const double s = nrm[j1];
     const TV v = (TV)(s > 0.0 ? w[r] / s : 0.0);
     if (V && j1 <= m) V[(size_t)j1 * D + r] = v;
     if (vcur) vcur[r] = v;
+}
+
+template <typename TV>
+__global__ void k_next(const double *__restrict__ w, const double *__restrict__ nrm, const int *__restrict__ jdev,
+                       int64_t D, int m, TV *V, TV *vcur) {
+    const int j1 = jdev ? *jdev + 1 : 0;
+    next_body<TV>(w, nrm[j1], j1, D, m, V, vcur, blockIdx.x);
 }
 
 __global__ void k_incr(int *jdev) { *jdev += 1; }
@@ -194,10 +226,17 @@ __device__ int sturm(const double *a, const double *b, int m, double x) {
 // One CTA, m = *jdev steps.  out[0] = theta (lowest eigenvalue), out[1] =
 // |beta_m s_{m-1}| (residual estimate), out[2] = beta_m, out[3] = m,
 // out[4..4+m) = unit eigenvector s.
+__device__ void tridiag_body(const double *__restrict__ alpha, const double *__restrict__ beta, int m, double *out,
+                             double *sm);
+
 __global__ void k_tridiag(const double *__restrict__ alpha, const double *__restrict__ beta,
                           const int *__restrict__ jdev, double *out) {
     extern __shared__ double sm[];
-    const int m = *jdev;
+    tridiag_body(alpha, beta, *jdev, out, sm);
+}
+
+__device__ void tridiag_body(const double *__restrict__ alpha, const double *__restrict__ beta, int m, double *out,
+                             double *sm) {
     if (m <= 0) return;
     double *a = sm, *b = sm + m, *s = sm + 2 * m;
     __shared__ double lo_hi[2];
@@ -319,7 +358,232 @@ __global__ void k_ritz(const TV *__restrict__ V, int64_t D, const int *__restric
 
 size_t tri_smem(int m) { return (size_t)8 * m * 8 + 64; }
 
+// ---------------------------------------------------------------- packed
+// One launch per kernel of the Lanczos step serves every job of a pack: the
+// blocks of all jobs form one grid, each block finds its job by binary search
+// over the jobs' first blocks (`first[n + 1]`, ascending) and runs the same
+// body as the single-job kernel with the job's own block index and count, so
+// a packed job computes bitwise what it computes alone.  A job takes part in
+// the steps of a chunk until its step counter reaches `jstop`.
+struct PackJob {
+    const void *V;
+    void *vcur, *hv;
+    double *w, *h, *part, *alpha, *beta, *tri;
+    int *jdev;
+    int64_t D;
+    int m, B, nbD, jstop;
+};
+
+__device__ __forceinline__ int find_job(const int *__restrict__ first, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// which = 0: u = hv (type TV); 1: u = w (double)
+template <typename TV, typename TU>
+__global__ void kp_gemv_t(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n, int which) {
+    __shared__ double sh[32];
+    const int i = find_job(first, n, blockIdx.x);
+    const PackJob &J = jobs[i];
+    const int j = *J.jdev;
+    if (j >= J.jstop) return;  // block-uniform
+    const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
+    gemv_t_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, u, J.part, blockIdx.x - first[i], J.B, sh);
+}
+
+__global__ void kp_reduce_rows(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
+    __shared__ double sh[32];
+    const int i = find_job(first, n, blockIdx.x);
+    const PackJob &J = jobs[i];
+    const int j = *J.jdev;
+    if (j >= J.jstop) return;
+    reduce_rows_body(J.part, j, J.B, J.h, J.alpha, blockIdx.x - first[i], sh);
+}
+
+template <typename TV, typename TU>
+__global__ void kp_gemv_sub(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n, int which) {
+    extern __shared__ double hs[];
+    const int i = find_job(first, n, blockIdx.x);
+    const PackJob &J = jobs[i];
+    const int j = *J.jdev;
+    if (j >= J.jstop) return;
+    const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
+    gemv_sub_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, J.h, u, J.w, blockIdx.x - first[i], hs);
+}
+
+__global__ void kp_sq_partial(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
+    __shared__ double sh[32];
+    const int i = find_job(first, n, blockIdx.x);
+    const PackJob &J = jobs[i];
+    if (*J.jdev >= J.jstop) return;
+    sq_partial_body(J.w, J.D, J.part, blockIdx.x - first[i], J.B, sh);
+}
+
+// one block per job
+__global__ void kp_sqrt_sum(const PackJob *__restrict__ jobs) {
+    __shared__ double sh[32];
+    const PackJob &J = jobs[blockIdx.x];
+    const int j = *J.jdev;
+    if (j >= J.jstop) return;
+    sqrt_sum_body(J.part, J.B, J.beta + j + 1, sh);
+}
+
+template <typename TV>
+__global__ void kp_next(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
+    const int i = find_job(first, n, blockIdx.x);
+    const PackJob &J = jobs[i];
+    const int j = *J.jdev;
+    if (j >= J.jstop) return;
+    next_body<TV>(J.w, J.beta[j + 1], j + 1, J.D, J.m, static_cast<TV *>(const_cast<void *>(J.V)),
+                  static_cast<TV *>(J.vcur), blockIdx.x - first[i]);
+}
+
+__global__ void kp_incr(const PackJob *__restrict__ jobs, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && *jobs[i].jdev < jobs[i].jstop) *jobs[i].jdev += 1;
+}
+
+__global__ void kp_tridiag(const PackJob *__restrict__ jobs) {
+    extern __shared__ double sm[];
+    const PackJob &J = jobs[blockIdx.x];
+    tridiag_body(J.alpha, J.beta, *J.jdev, J.tri, sm);
+}
+
 }  // namespace
+
+// Layout of the pack's device block: jobs, then the first-block arrays
+// (B tiles, m+1 tiles, 256-row tiles), then per key width the product
+// parameters and their tile starts.
+void enqueue_packed_chunk(qsd_ctx ctx, const std::vector<LanczosJob *> &jobs, cudaStream_t s, PackBuffers &pb) {
+    const int n = (int)jobs.size();
+    if (n == 0) return;
+    const bool fp32 = jobs[0]->fp32;
+    const int prec = jobs[0]->prec;
+    int steps = 0, maxm = 0;
+    std::vector<PackJob> pj(n);
+    std::vector<int> fB(n + 1), fM(n + 1), fD(n + 1);
+    fB[0] = fM[0] = fD[0] = 0;
+    std::map<int, std::vector<int>> by_w;
+    for (int i = 0; i < n; ++i) {
+        LanczosJob &J = *jobs[i];
+        if (J.fp32 != fp32 || J.prec != prec) fail(QSD_ERR_INTERNAL, "packed chunk: mixed precisions");
+        const int len = std::min(J.check_every, J.m - J.steps_done);
+        steps = std::max(steps, len);
+        maxm = std::max(maxm, J.m);
+        PackJob &P = pj[i];
+        P.V = J.V.p;
+        P.vcur = J.vcur.p;
+        P.hv = J.hv.p;
+        P.w = J.w.as<double>();
+        P.h = J.h.as<double>();
+        P.part = J.part.as<double>();
+        P.alpha = J.alpha.as<double>();
+        P.beta = J.beta.as<double>();
+        P.tri = J.tri.as<double>();
+        P.jdev = J.jdev.as<int>();
+        P.D = J.D;
+        P.m = J.m;
+        P.B = J.B;
+        P.nbD = J.nbD;
+        P.jstop = J.steps_done + std::max(len, 0);
+        fB[i + 1] = fB[i] + J.B;
+        fM[i + 1] = fM[i] + J.m + 1;
+        fD[i + 1] = fD[i] + J.nbD;
+        by_w[J.op->W].push_back(i);
+    }
+    if (steps <= 0) return;
+    // host staging (pinned, reused once the previous chunk of this pack has
+    // passed), one copy to the device block
+    const size_t o_jobs = 0, o_f = align_up((size_t)n * sizeof(PackJob), 256);
+    const size_t o_params = align_up(o_f + (size_t)3 * (n + 1) * sizeof(int), 256);
+    size_t bytes = o_params;
+    for (auto &kv : by_w) bytes += align_up(kv.second.size() * (sizeof(ApplyParams) + 8), 256) + 256;
+    pb.reserve(bytes, s);
+    unsigned char *h = pb.host, *d = static_cast<unsigned char *>(pb.dev.p);
+    std::memcpy(h + o_jobs, pj.data(), (size_t)n * sizeof(PackJob));
+    int *hf = reinterpret_cast<int *>(h + o_f);
+    std::memcpy(hf, fB.data(), (size_t)(n + 1) * 4);
+    std::memcpy(hf + (n + 1), fM.data(), (size_t)(n + 1) * 4);
+    std::memcpy(hf + 2 * (n + 1), fD.data(), (size_t)(n + 1) * 4);
+    struct WLaunch { int W, m; int64_t tiles; size_t o_p, o_t; };
+    std::vector<WLaunch> wl;
+    size_t o = o_params;
+    for (auto &[W, idx] : by_w) {
+        const int m = (int)idx.size();
+        WLaunch L{W, m, 0, o, align_up(o + (size_t)m * sizeof(ApplyParams), 256)};
+        ApplyParams *hp = reinterpret_cast<ApplyParams *>(h + L.o_p);
+        int64_t *ht = reinterpret_cast<int64_t *>(h + L.o_t);
+        for (int k = 0; k < m; ++k) {
+            LanczosJob &J = *jobs[idx[k]];
+            hp[k] = product_params(ctx, J.op, J.sub, J.diag, 1, J.vcur.p, J.hv.p);
+            ht[k] = L.tiles;
+            L.tiles += (J.D + 255) / 256;
+        }
+        o = align_up(L.o_t + (size_t)m * 8, 256);
+        wl.push_back(L);
+    }
+    QSD_CUDA(cudaMemcpyAsync(d, h, o, cudaMemcpyHostToDevice, s));
+    const PackJob *dj = reinterpret_cast<const PackJob *>(d + o_jobs);
+    const int *dfB = reinterpret_cast<const int *>(d + o_f), *dfM = dfB + (n + 1), *dfD = dfB + 2 * (n + 1);
+    const size_t hsm = (size_t)(maxm + 1) * 8;
+    for (int t = 0; t < steps; ++t) {
+        for (const WLaunch &L : wl)
+            launch_apply_batch(reinterpret_cast<const ApplyParams *>(d + L.o_p),
+                               reinterpret_cast<const int64_t *>(d + L.o_t), L.m, L.tiles, L.W, 1, prec, s);
+        if (fp32) {
+            kp_gemv_t<float, float><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 0);
+            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
+            kp_gemv_sub<float, float><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 0);
+            kp_gemv_t<float, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 1);
+            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
+            kp_gemv_sub<float, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 1);
+        } else {
+            kp_gemv_t<double, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 0);
+            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
+            kp_gemv_sub<double, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 0);
+            kp_gemv_t<double, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 1);
+            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
+            kp_gemv_sub<double, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 1);
+        }
+        kp_sq_partial<<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n);
+        kp_sqrt_sum<<<n, kLanczosThreads, 0, s>>>(dj);
+        if (fp32) kp_next<float><<<fD[n], 256, 0, s>>>(dj, dfD, n);
+        else kp_next<double><<<fD[n], 256, 0, s>>>(dj, dfD, n);
+        kp_incr<<<(n + 127) / 128, 128, 0, s>>>(dj, n);
+    }
+    kp_tridiag<<<n, kLanczosThreads, tri_smem(maxm), s>>>(dj);
+    QSD_LAUNCH_CHECK();
+    for (int i = 0; i < n; ++i) {
+        LanczosJob &J = *jobs[i];
+        QSD_CUDA(cudaMemcpyAsync(J.hpin, J.tri.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        J.steps_done = pj[i].jstop;
+        ++J.chunks;
+    }
+}
+
+void PackBuffers::reserve(size_t bytes, cudaStream_t s) {
+    if (bytes <= cap) return;
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    cap = 0;
+    dev.alloc_async(bytes, s);
+    QSD_CUDA(cudaMallocHost(reinterpret_cast<void **>(&host), bytes));
+    cap = bytes;
+}
+
+void PackBuffers::release() {
+    dev.release();
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    cap = 0;
+}
+
+PackBuffers::~PackBuffers() { release(); }
 
 // ---------------------------------------------------------------- job
 LanczosJob::~LanczosJob() {

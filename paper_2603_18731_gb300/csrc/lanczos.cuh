@@ -1,7 +1,7 @@
 // Lanczos state shared by the synchronous solver and the request server.
 #pragma once
 
-#include "qsd_internal.cuh"
+#include "apply_kernel.cuh"
 
 namespace qsd {
 
@@ -40,6 +40,27 @@ struct LanczosJob {
     void read(double &theta, double &est, double &beta_last, int &nvec) const;
     bool converged(double tol) const;
 };
+
+// Device block and pinned staging of a pack's descriptors (grown on demand;
+// reused once the stream has passed the previous chunk that used them).
+struct PackBuffers {
+    DevBuf dev;
+    unsigned char *host = nullptr;
+    size_t cap = 0;
+    PackBuffers() = default;
+    PackBuffers(const PackBuffers &) = delete;
+    PackBuffers &operator=(const PackBuffers &) = delete;
+    ~PackBuffers();
+    void reserve(size_t bytes, cudaStream_t s);
+    void release();  // before the stream of `dev` is destroyed
+};
+
+// One chunk of steps for every job of a pack with packed launches on stream
+// s: the product of all jobs (group scan, one launch per key width) and each
+// Lanczos kernel once for all jobs.  Jobs share the basis type and product
+// precision and have W <= 4; each advances min(check_every, m - steps_done)
+// steps and its tridiagonal results reach its hpin as after enqueue_chunk.
+void enqueue_packed_chunk(qsd_ctx ctx, const std::vector<LanczosJob *> &jobs, cudaStream_t s, PackBuffers &pb);
 
 // FP64 Rayleigh quotient and residual of a vector, enqueued on a stream.
 struct ResidJob {

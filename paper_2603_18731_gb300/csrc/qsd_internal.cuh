@@ -415,6 +415,11 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
 int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr, void *indices, int index_bits,
                double *data_re, double *data_im, const double *diag);
 
+// RAMPS refinement from the rows of `start` (ramps.cu); `out` is a fresh
+// subspace handle (ctx, n_qubits, W set) that receives the output rows.
+void ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int max_levels, qsd_sub allowed,
+           int64_t max_rows, qsd_sub out, qsd_ramps_info *info);
+
 int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int KB, const void *x,
                  void *y, int64_t ld, int64_t col0, cudaStream_t stream, bool may_tune);
 void target_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0, int64_t nrows, int64_t *out);
@@ -427,5 +432,6 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
 uint32_t take_device_error(qsd_ctx ctx);
 
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace qsd

@@ -13,7 +13,15 @@
 // The scheduler enqueues the next piece of a request as soon as its previous
 // piece has passed (cudaEventQuery), so the work of all admitted requests
 // overlaps on the device and a request arriving while others run starts as
-// soon as a slot and memory free up.  All device memory of a request is
+// soon as a slot and memory free up.
+//
+// Small requests (at most `pack_rows` rows, W <= 4) share one stream and are
+// packed: whenever a pack's previous chunk has passed, one chunk of Lanczos
+// steps is enqueued for all its members that wait for one, with one launch
+// per kernel for all of them (enqueue_packed_chunk), so many small solves
+// cost the launches of one.  Requests join and leave a pack at chunk
+// boundaries; their other pieces (start, Ritz vector, residual) run on the
+// same stream between chunks.  All device memory of a request is
 // stream-ordered (cudaMallocAsync / cudaFreeAsync), so admitting and retiring
 // requests never synchronises the device.
 #include <algorithm>
@@ -51,6 +59,8 @@ struct Request {
     bool inflight = false;
     bool cancel = false;
     bool admitted = false;
+    bool packed = false;             // small request: chunks run in packed launches
+    LanczosJob *want = nullptr;      // packed: job waiting for the pack's next chunk
     std::unique_ptr<LanczosJob> J, K;
     std::unique_ptr<ResidJob> R;
     DevBuf diag, u, start;
@@ -90,6 +100,13 @@ struct qsd_server_s {
     qsd::Clock::time_point t0;
     std::string last_error;
     double *pinned = nullptr;  // 16 doubles of pinned host memory per slot
+    // packs of small requests, one per product precision
+    int64_t pack_rows = 0;  // packing off unless asked for (qsd_server_set_pack_rows)
+    cudaStream_t pack_stream = nullptr;
+    qsd::PackBuffers pack_buf[3];
+    cudaEvent_t pack_ev[3] = {nullptr, nullptr, nullptr};
+    bool pack_inflight[3] = {false, false, false};
+    int64_t packed_requests = 0, packed_chunks = 0;
 };
 
 namespace qsd {
@@ -98,7 +115,11 @@ namespace {
 
 double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
+// Called with S->mu held.  The counters move here, not at retirement, so
+// that a waiter that sees the result also sees it counted.
 void finish(qsd_server_s *S, Request *r, int status) {
+    if (status == QSD_OK) ++S->completed;
+    else ++S->failed;
     r->status = status;
     r->state = RState::Done;
     r->t_done = Clock::now();
@@ -126,6 +147,9 @@ void advance(qsd_server_s *S, Request *r) {
             r->J->enqueue_ritz(r->u.as<double>());
             r->R->enqueue(r->op, r->sub, r->diag.as<double>(), r->u.as<double>());
             r->state = RState::ResidMain;
+        } else if (r->packed) {
+            r->want = r->J.get();
+            return;  // the pack's next chunk records the event
         } else {
             r->J->enqueue_chunk(graphs);
         }
@@ -163,17 +187,20 @@ void advance(qsd_server_s *S, Request *r) {
         }
         QSD_CUDA(cudaMemcpyAsync(r->start.p, r->u.p, (size_t)r->sub->D * 8, cudaMemcpyDeviceToDevice, r->s));
         r->K->enqueue_start(r->start.as<double>(), p.seed);
-        r->K->enqueue_chunk(graphs);
         r->state = RState::Refine;
-        break;
+        if (!r->packed) r->K->enqueue_chunk(graphs);
+        break;  // packed: the first chunk follows once the start has passed
     }
     case RState::Refine: {
-        if (r->K->converged(tol) || r->K->steps_done >= r->K->m) {
+        if (r->K->chunks > 0 && (r->K->converged(tol) || r->K->steps_done >= r->K->m)) {
             r->info.steps += r->K->steps_done;
             r->info.applies += r->K->steps_done + 1;
             r->K->enqueue_ritz(r->u.as<double>());
             r->R->enqueue(r->op, r->sub, r->diag.as<double>(), r->u.as<double>());
             r->state = RState::ResidRefine;
+        } else if (r->packed) {
+            r->want = r->K.get();
+            return;
         } else {
             r->K->enqueue_chunk(graphs);
         }
@@ -206,6 +233,12 @@ void start_request(qsd_server_s *S, Request *r) {
     r->R->init(S->ctx, D, r->s, true);
     r->J->enqueue_start(r->p.v0, r->p.seed);
     r->state = RState::Main;
+    if (r->packed) {
+        // the chunks run on the pack stream: join one once the start has passed
+        QSD_CUDA(cudaEventRecord(r->ev, r->s));
+        r->inflight = true;
+        return;
+    }
     advance(S, r);
 }
 
@@ -233,7 +266,6 @@ void scheduler(qsd_server_s *S) {
                 if (r->cancel) {
                     S->queue.pop_front();
                     finish(S, r, QSD_ERR_CANCELLED);
-                    ++S->failed;
                     S->cv_done.notify_all();
                     continue;
                 }
@@ -241,7 +273,9 @@ void scheduler(qsd_server_s *S) {
                 S->queue.pop_front();
                 r->slot = S->free_slots.back();
                 S->free_slots.pop_back();
+                r->packed = r->sub->D <= S->pack_rows && r->op->W <= kMaxWordsStatic;
                 r->s = S->streams[r->slot];
+                if (r->packed) ++S->packed_requests;
                 S->used += r->footprint;
                 S->peak = std::max(S->peak, S->used);
                 r->t_admit = Clock::now();
@@ -291,14 +325,61 @@ void scheduler(qsd_server_s *S) {
                 }
             }
         }
+        // packed chunks: every pack whose previous chunk has passed takes all
+        // its members that wait for a chunk.  A member's own stream is idle
+        // here (its last piece has passed), and its next piece follows only
+        // once the chunk has passed, so the host orders the two streams.
+        // Only this thread touches the members, so the launches are
+        // enqueued without holding the lock.
+        for (int k = 0; k < 3; ++k) {
+            if (S->pack_inflight[k]) {
+                if (cudaEventQuery(S->pack_ev[k]) == cudaErrorNotReady) continue;
+                S->pack_inflight[k] = false;
+            }
+            std::vector<Request *> members;
+            std::vector<LanczosJob *> jobs;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (Request *r : S->active)
+                    if (r->want && r->state != RState::Done && r->want->prec == k) {
+                        members.push_back(r);
+                        jobs.push_back(r->want);
+                    }
+            }
+            if (jobs.empty()) continue;
+            std::string err;
+            int code = QSD_OK;
+            try {
+                enqueue_packed_chunk(S->ctx, jobs, S->pack_stream, S->pack_buf[k]);
+                QSD_CUDA(cudaEventRecord(S->pack_ev[k], S->pack_stream));
+                for (Request *r : members) QSD_CUDA(cudaEventRecord(r->ev, S->pack_stream));
+            } catch (const Error &e) {
+                err = e.what();
+                code = e.code;
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (code == QSD_OK) {
+                S->pack_inflight[k] = true;
+                ++S->packed_chunks;
+                for (Request *r : members) {
+                    r->want = nullptr;
+                    r->inflight = true;
+                }
+            } else {
+                S->last_error = err;
+                for (Request *r : members) {
+                    r->want = nullptr;
+                    finish(S, r, code);
+                }
+            }
+            progressed = true;
+        }
         for (Request *r : done) {
             release_request(S, r);
             std::lock_guard<std::mutex> lk(S->mu);
             S->active.erase(std::find(S->active.begin(), S->active.end(), r));
             S->free_slots.push_back(r->slot);
             S->used -= r->footprint;
-            if (r->status == QSD_OK) ++S->completed;
-            else ++S->failed;
             S->cv_done.notify_all();
             progressed = true;
         }
@@ -323,6 +404,9 @@ int qsd_server_create(qsd_ctx ctx, size_t budget_bytes, int32_t max_active, qsd_
         S->max_active = max_active;
         S->t0 = Clock::now();
         QSD_CUDA(cudaSetDevice(ctx->device));
+        // requests may come from other contexts with any key width: the hash
+        // tables of every width, allocated once before any request runs
+        ensure_nibble_tables(ctx, kMaxWordsDyn);
         QSD_CUDA(cudaMallocHost(&S->pinned, (size_t)max_active * 16 * sizeof(double)));
         // keep memory freed by retired requests in the stream-ordered pool
         cudaMemPool_t pool;
@@ -335,10 +419,15 @@ int qsd_server_create(qsd_ctx ctx, size_t budget_bytes, int32_t max_active, qsd_
             S->streams.push_back(s);
             S->free_slots.push_back(max_active - 1 - i);
         }
+        QSD_CUDA(cudaStreamCreateWithFlags(&S->pack_stream, cudaStreamNonBlocking));
+        for (auto &e : S->pack_ev) QSD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         S->th = std::thread(scheduler, S);
     } catch (const Error &e) {
         ctx->last_error = e.what();
         for (auto s : S->streams) cudaStreamDestroy(s);
+        if (S->pack_stream) cudaStreamDestroy(S->pack_stream);
+        for (auto e2 : S->pack_ev)
+            if (e2) cudaEventDestroy(e2);
         if (S->pinned) cudaFreeHost(S->pinned);
         delete S;
         return e.code;
@@ -445,6 +534,15 @@ int qsd_server_get_stats(qsd_server S, qsd_server_stats *st) {
     st->bytes_in_use = S->used;
     st->peak_bytes = S->peak;
     st->budget_bytes = S->budget;
+    st->packed_requests = S->packed_requests;
+    st->packed_chunks = S->packed_chunks;
+    return QSD_OK;
+}
+
+int qsd_server_set_pack_rows(qsd_server S, int64_t rows) {
+    if (!S || rows < 0) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->pack_rows = rows;
     return QSD_OK;
 }
 
@@ -471,6 +569,16 @@ int qsd_server_destroy(qsd_server S) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
+    if (S->pack_stream) {
+        // the packs' device blocks are stream-ordered on the pack stream:
+        // free them while it exists
+        cudaStreamSynchronize(S->pack_stream);
+        for (auto &pb : S->pack_buf) pb.release();
+        cudaStreamSynchronize(S->pack_stream);
+        cudaStreamDestroy(S->pack_stream);
+    }
+    for (auto e : S->pack_ev)
+        if (e) cudaEventDestroy(e);
     if (S->pinned) cudaFreeHost(S->pinned);
     delete S;
     return QSD_OK;

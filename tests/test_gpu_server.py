@@ -90,3 +90,35 @@ def test_server_rejects_bad_requests(ctx):
         with pytest.raises(q.QsdError) as e:
             srv.submit(nonherm, sub)
         assert e.value.status == "NOT_HERMITIAN"
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_server_packs_small_requests(ctx, precision):
+    # with packing on, every request below 32768 rows joins a pack: its chunks
+    # share packed launches with the other members; results equal the
+    # request alone
+    import paper_2603_18731_gb300 as q
+    cases = _mix(ctx)
+    params = dict(precision=precision, max_steps=300, tol=1e-10, check_every=10)
+    alone = {name: ctx.lanczos_ground_state(h, sub, **params)[0] for name, h, sub, _ in cases}
+    for rows in (32768, 0):
+        with q.Server(ctx, budget_bytes=1 << 30, max_active=16) as srv:
+            srv.set_pack_rows(rows)
+            tickets = [(name, srv.submit(h, sub, **params), e) for name, h, sub, e in cases for _ in range(3)]
+            steps = 0
+            for name, t, e_ref in tickets:
+                r = srv.wait(t, timeout_s=120)
+                assert r["status"] == "OK", (name, r)
+                tol = 1e-10 if precision == 0 else 1e-7
+                assert abs(r["energy"] - e_ref) <= tol * abs(e_ref), (name, r["energy"], e_ref)
+                assert abs(r["energy"] - alone[name]) <= 1e-12 * abs(e_ref), (name, r["energy"], alone[name])
+                steps += r["info"]["steps"]
+            st = srv.stats()
+            assert st["completed"] == len(tickets) and st["failed"] == 0
+            if rows:
+                assert st["packed_requests"] == len(tickets)
+                # a chunk serves every waiting member: far fewer chunks than
+                # the members' chunks together
+                assert 0 < st["packed_chunks"] < steps // params["check_every"]
+            else:
+                assert st["packed_requests"] == 0 and st["packed_chunks"] == 0
