@@ -91,6 +91,20 @@ __device__ __forceinline__ uint64_t word_of(const uint64_t (&x)[W], int q) {
     return v;
 }
 
+// Bit q of a multi-word key with 32-bit operations only (the word's high or
+// low half, then a 32-bit shift).
+template <int W>
+__device__ __forceinline__ uint32_t bit_of(const uint64_t (&x)[W], int q) {
+    const uint64_t v = word_of<W>(x, q);
+    const uint32_t h = (q & 32) ? (uint32_t)(v >> 32) : (uint32_t)v;
+    return (h >> (q & 31)) & 1u;
+}
+
+// a != 0 (either sign of zero counts as zero), on the two 32-bit halves.
+__device__ __forceinline__ bool nonzero_f64(double a) {
+    return ((uint32_t)(__double2hiint(a) & 0x7fffffff) | (uint32_t)__double2loint(a)) != 0u;
+}
+
 // Matrix element of a scan group at the row (0 when no term survives).
 template <int W>
 __device__ __noinline__ double scan_amp(const ApplyParams &p, int64_t g, const uint64_t (&key)[W]) {
@@ -101,7 +115,7 @@ __device__ __noinline__ double scan_amp(const ApplyParams &p, int64_t g, const u
         int l = 0;
         for (int i = 0; i < L; ++i) {
             const int q = (int)((pos >> (16 * i)) & 0xffff);
-            l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+            l |= (int)bit_of<W>(key, q) << i;
         }
         b = __ldg(p.gptr + g * 17 + l);
         e = __ldg(p.gptr + g * 17 + l + 1);
@@ -185,7 +199,8 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
         for (int j = 0; j < KB; ++j) xr_own[j] = (double)__ldg(x + r * p.ld + p.col0 + j);
     }
 
-    for (int64_t g0 = (int64_t)sub * U; g0 < p.G; g0 += (int64_t)R * U) {
+    const int64_t G = p.G;
+    for (int64_t g0 = (int64_t)sub * U; g0 < G; g0 += (int64_t)R * U) {
         // phase 1: element of each of U groups, and its bucket load in flight
         double a[U];
         float ah[U], al[U];
@@ -202,7 +217,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             a[u] = 0.0;
             ah[u] = al[u] = 0.f;
             uint64_t hF = 0;
-            if (g < p.G) {
+            if (g < G) {
                 const ulonglong2 *rp = reinterpret_cast<const ulonglong2 *>(p.grec + g);
                 const ulonglong2 r0 = __ldg(rp);
                 const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(rp + 1));
@@ -211,7 +226,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                 bool lower = true;
                 if (SYM) {
                     const int qm = (int)((info >> kMsobShift) & kMsobMask);
-                    lower = (word_of<W>(key, qm) >> (qm & 63)) & 1;
+                    lower = bit_of<W>(key, qm);
                 }
                 if (!lower) {
                     // upper-triangle element: reached from its column's row
@@ -221,13 +236,13 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                     int l = 0;
                     if (nb > 0) {
                         const int q0 = (int)(r0.y & 0xfff);
-                        l = (int)((word_of<W>(key, q0) >> (q0 & 63)) & 1);
+                        l = (int)bit_of<W>(key, q0);
                         if (nb > 1) {
                             const int q1 = (int)((r0.y >> 12) & 0xfff);
-                            l |= (int)((word_of<W>(key, q1) >> (q1 & 63)) & 1) << 1;
+                            l |= (int)bit_of<W>(key, q1) << 1;
                             for (int i = 2; i < nb; ++i) {
                                 const int q = (int)((r0.y >> (12 * i)) & 0xfff);
-                                l |= (int)((word_of<W>(key, q) >> (q & 63)) & 1) << i;
+                                l |= (int)bit_of<W>(key, q) << i;
                             }
                         }
                     }
@@ -244,11 +259,11 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
                         nz = (nzm >> l) & 1u;
                     } else {
                         a[u] = __ldg(p.amp + off + l);
-                        nz = ((uint64_t)__double_as_longlong(a[u]) << 1) != 0ull;
+                        nz = nonzero_f64(a[u]);
                     }
                 } else if (active) {
                     a[u] = scan_amp<W>(p, g, key);
-                    nz = ((uint64_t)__double_as_longlong(a[u]) << 1) != 0ull;
+                    nz = nonzero_f64(a[u]);
                     if (PREC == QSD_FP32_DOT2) {
                         ah[u] = (float)a[u];
                         al[u] = (float)(a[u] - (double)ah[u]);
@@ -257,7 +272,8 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             }            need[u] = active && nz;
             if (need[u]) {
                 bidx[u] = hash_bucket(hr ^ hF, p.hv.shift, tag[u]);
-                tb[u] = load_tags(p.hv.tags, bidx[u]);
+                // bucket counts stay below 2^32: a 32-bit index into 16-byte buckets
+                tb[u] = __ldg(reinterpret_cast<const uint4 *>(p.hv.tags) + (uint32_t)bidx[u]);
             }
         }
         // phase 2: resolve the lookups and accumulate
