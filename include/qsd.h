@@ -272,6 +272,16 @@ int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
 int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k,
                 const void *x, void *y);
 
+/* Complex product y = H_S x for any operator, including complex matrix
+ * elements and non-Hermitian operators (Methods, "Qubit Hamiltonians":
+ * complex coefficients c_i), FP64.  x, y: device complex128 [dim][k], each
+ * entry (re, im) interleaved (the layout of C99 double complex and of
+ * torch.complex128).  Every group is evaluated term by term; one lookup per
+ * group with a passing term; deterministic.  n <= 256 qubits.  Asynchronous
+ * on the context's stream. */
+int qsd_apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t k,
+                        const void *x, void *y);
+
 /* Packed products: y_i = H_S(ops[i], subs[i]) x_i for i < n in one launch per
  * key width (one grid over 256-row tiles of all pairs), for many small
  * subspaces whose single products would each fill only a few blocks.  Each

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("qsd_free_sub", C.c_int, [_P]),
     ("qsd_set_tuning", C.c_int, [_P, _I32, _I64]),
     ("qsd_apply_H_batch", C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P, _P]),
+    ("qsd_apply_H_complex", C.c_int, [_P, _P, _P, _I32, _P, _P]),
     ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
     ("qsd_ramps", C.c_int, [_P, _P, _P, _D, _D, _I32, _P, _I64, C.POINTER(_P), C.POINTER(RampsInfo)]),
     ("qsd_product_path", C.c_int, [_P, _P, _P, _I32, _I64, C.POINTER(C.c_int32)]),
@@ -287,6 +288,17 @@ class Context:
         if y is None:
             y = self.empty(tuple(x.shape), dt)
         self._check(lib().qsd_apply_H(self.handle, op.handle, sub.handle, precision, k, _t_ptr(x), _t_ptr(y)))
+        return y
+
+    def apply_H_complex(self, op: Operator, sub: Subspace, x, y=None):
+        """y = H_S x for CUDA complex128 tensors of shape [D] or [D, k] (any
+        operator, complex elements allowed)."""
+        if x.dtype != self.torch.complex128 or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex128 tensor")
+        k = 1 if x.dim() == 1 else int(x.shape[1])
+        if y is None:
+            y = self.empty(tuple(x.shape), self.torch.complex128)
+        self._check(lib().qsd_apply_H_complex(self.handle, op.handle, sub.handle, k, _t_ptr(x), _t_ptr(y)))
         return y
 
     def apply_H_batch(self, ops, subs, xs, ys=None, precision: int = QSD_FP64):

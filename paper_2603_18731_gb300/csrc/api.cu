@@ -580,6 +580,20 @@ int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k, c
     });
 }
 
+int qsd_apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t k, const void *x, void *y) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (k < 1) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_complex: k < 1");
+        if (op->W > kMaxWordsStatic) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_complex: more than 256 qubits");
+        if (sub->D == 0) return QSD_OK;
+        if (!x || !y) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_complex: NULL vector");
+        set_device(ctx);
+        apply_H_complex(ctx, op, sub, k, x, y);
+    });
+}
+
 int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *subs, int precision, int32_t k,
                       const void *const *xs, void *const *ys) {
     if (!ctx) return QSD_ERR_INVALID_ARG;

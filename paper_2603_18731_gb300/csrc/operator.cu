@@ -482,6 +482,7 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
     }
     op->T_in = Ti;
     op->identity = id_re;
+    op->identity_im = id_im;
     if (Ti > 0) {
         op->iF.alloc(iF.size() * 8); op->iP.alloc(iP.size() * 8); op->iV.alloc(iV.size() * 8); op->iZ.alloc(iZ.size() * 8);
         op->iY.alloc(Ti);
@@ -581,11 +582,13 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
     if (Td > 0) {
         op->dP.alloc((size_t)W * Td * 8); op->dV.alloc((size_t)W * Td * 8); op->dZ.alloc((size_t)W * Td * 8);
         op->dphi.alloc((size_t)Td * 8);
+        op->dphi_im.alloc((size_t)Td * 8);
         const int nb = blocks_for(Td, 256);
         k_slice_rows<<<nb, 256, 0, s>>>(ukeys.as<uint64_t>(), Tu, 2 * W, W, 0, Td, op->dP.as<uint64_t>());
         k_slice_rows<<<nb, 256, 0, s>>>(ukeys.as<uint64_t>(), Tu, W, W, 0, Td, op->dV.as<uint64_t>());
         k_slice_rows<<<nb, 256, 0, s>>>(ukeys.as<uint64_t>(), Tu, 0, W, 0, Td, op->dZ.as<uint64_t>());
         QSD_CUDA(cudaMemcpyAsync(op->dphi.p, ure.p, (size_t)Td * 8, cudaMemcpyDeviceToDevice, s));
+        QSD_CUDA(cudaMemcpyAsync(op->dphi_im.p, uim.p, (size_t)Td * 8, cudaMemcpyDeviceToDevice, s));
         QSD_LAUNCH_CHECK();
     }
 

@@ -146,6 +146,7 @@ struct qsd_op_s {
     int W = 1;
     qsd_op_info info{};
     double identity = 0.0;
+    double identity_im = 0.0;
     // off-diagonal groups (G) and terms (T), group order
     int64_t G = 0, T = 0;
     qsd::DevBuf gF;      // uint64 [W][G]
@@ -178,6 +179,7 @@ struct qsd_op_s {
     int64_t Td = 0;
     qsd::DevBuf dP, dV, dZ;  // uint64 [W][Td]
     qsd::DevBuf dphi;        // double [Td]
+    qsd::DevBuf dphi_im;     // double [Td] imaginary parts (complex operators)
     // input terms as masks, for the term table
     int64_t T_in = 0;
     qsd::DevBuf iF, iP, iV, iZ;  // uint64 [W][T_in]
@@ -414,6 +416,9 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
 // returns nnz and keeps the pass-1 counts; filling call: writes the arrays.
 int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr, void *indices, int index_bits,
                double *data_re, double *data_im, const double *diag);
+
+// Complex product (apply_complex.cu): x, y complex128 [D][k] interleaved.
+void apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int k, const void *x, void *y);
 
 // RAMPS refinement from the rows of `start` (ramps.cu); `out` is a fresh
 // subspace handle (ctx, n_qubits, W set) that receives the output rows.
