@@ -334,6 +334,20 @@ def run_gpu(args):
             csr[name] = {"ms": 1e3 * float(np.mean(ts)), "count_pass_ms": 1e3 * float(np.mean(tc)), "nnz": nnz}
         csr["msob_speedup"] = csr["full"]["ms"] / csr["msob_lower"]["ms"]
 
+    # block LOBPCG (shifted Jacobi preconditioner, the paper's spiked start),
+    # 4 lowest eigenpairs
+    lob = None
+    if not args.no_solve and args.workload != "chem":
+        lob = {}
+        for pre in (1, 0):
+            ctx.synchronize()
+            t0 = time.perf_counter()
+            ev, inf = ctx.lobpcg(h, sub, k=4, tol=1e-8, precondition=pre, max_iters=600, check=False)
+            ctx.synchronize()
+            lob["jacobi" if pre else "none"] = {"seconds": time.perf_counter() - t0, "evals": ev.tolist(),
+                                                "iters": inf["iters"], "status": inf["status"],
+                                                "max_residual": inf["max_residual"]}
+
     # RAMPS refinement from one reference bit-string (the lowest-diagonal
     # row of the workload's subspace), E = its diagonal, unrestricted
     ramps_out = None
@@ -368,7 +382,7 @@ def run_gpu(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "variants": variants, "solve": solve, "csr_build": csr, "ramps": ramps_out, "packed": packed, "serve": serve,
+            "clocks": clk.summary(), "variants": variants, "solve": solve, "lobpcg_k4": lob, "csr_build": csr, "ramps": ramps_out, "packed": packed, "serve": serve,
             "step_ms_min_max": [float(np.min(all64)), float(np.max(all64))],
         }
         print(json.dumps(line))

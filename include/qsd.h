@@ -182,6 +182,39 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
                int64_t *indptr, void *indices, int32_t index_bits,
                double *data_re, double *data_im);
 
+/* ---------------------------------------------------------------- LOBPCG */
+/* The k lowest eigenpairs of the real symmetric H_S by LOBPCG with a shifted
+ * Jacobi (diagonal) preconditioner -- the eigensolver the paper uses for its
+ * chemistry results (Results: PRIMME's LOBPCG from a vector spiked at the
+ * lowest diagonal, diagonal preconditioner shifted by the current eigenvalue
+ * estimate).  Directions W = R / max(|d - theta|, 1e-8 max|d|) column by
+ * column; the basis [X, W, P] is kept orthonormal; FP64 block products (one
+ * lookup per group serves the k columns); Rayleigh-Ritz with the small
+ * eigenproblem solved on the host; reproducible (fixed reduction orders).
+ * Requires a real Hermitian operator, 1 <= k <= 16 and dim >= 3k.  evals:
+ * host double [k] ascending; evecs: device double [dim][k] (row-major,
+ * orthonormal columns) or NULL.  Returns QSD_OK when every pair meets tol,
+ * else QSD_ERR_NOT_CONVERGED with the last estimates. */
+typedef struct {
+    int32_t k;             /* eigenpairs wanted (block width), 1..16 */
+    int32_t max_iters;     /* iteration limit */
+    double tol;            /* max over pairs of |H x - theta x| / |theta|, unit x */
+    uint64_t seed;         /* random entries U(-1,1) from SplitMix64(seed xor index) */
+    const double *x0;      /* optional device [dim][k] start block (NULL: see start) */
+    int32_t precondition;  /* 1: shifted Jacobi; 0: none */
+    int32_t start;         /* 0: unit spikes at the k lowest diagonal entries plus
+                              1e-3 random entries (the paper's start); 1: random */
+} qsd_lobpcg_params;
+typedef struct {
+    int32_t iters, converged;
+    double max_residual;
+    int32_t status, reserved;
+} qsd_lobpcg_info;
+/* k 1, 500 iterations, tol 1e-9, seed 0, precondition 1, start 0 */
+void qsd_lobpcg_default_params(qsd_lobpcg_params *p);
+int qsd_lobpcg(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lobpcg_params *p, double *evals,
+               double *evecs, qsd_lobpcg_info *info);
+
 /* ------------------------------------------------------------------ RAMPS */
 /* Subspace refinement RAMPS (Supplementary, "Recursive algorithm for a
  * minimal perturbative subspace", Algorithm S1; expansion Eq. S2), run level

@@ -55,6 +55,16 @@ class LanczosInfo(C.Structure):
                 ("energy_unrefined", C.c_double), ("status", C.c_int32), ("applies", C.c_int32)]
 
 
+class LobpcgParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("max_iters", C.c_int32), ("tol", C.c_double), ("seed", C.c_uint64),
+                ("x0", C.c_void_p), ("precondition", C.c_int32), ("start", C.c_int32)]
+
+
+class LobpcgInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("max_residual", C.c_double),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
 class RampsInfo(C.Structure):
     _fields_ = [("levels", C.c_int32), ("stopped_by_limit", C.c_int32), ("truncated", C.c_int32),
                 ("reserved", C.c_int32), ("rows_out", C.c_int64), ("candidates", C.c_int64),
@@ -89,6 +99,8 @@ SIGNATURES = [
     ("qsd_apply_H_batch", C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P, _P]),
     ("qsd_apply_H_complex", C.c_int, [_P, _P, _P, _I32, _P, _P]),
     ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
+    ("qsd_lobpcg_default_params", None, [C.POINTER(LobpcgParams)]),
+    ("qsd_lobpcg", C.c_int, [_P, _P, _P, C.POINTER(LobpcgParams), _P, _P, C.POINTER(LobpcgInfo)]),
     ("qsd_ramps", C.c_int, [_P, _P, _P, _D, _D, _I32, _P, _I64, C.POINTER(_P), C.POINTER(RampsInfo)]),
     ("qsd_product_path", C.c_int, [_P, _P, _P, _I32, _I64, C.POINTER(C.c_int32)]),
     ("qsd_apply_H", C.c_int, [_P, _P, _P, C.c_int, _I32, _P, _P]),
@@ -363,6 +375,29 @@ class Context:
         self._check(lib().qsd_rayleigh_quotient_noalloc(self.handle, op.handle, sub.handle, _t_ptr(u),
                                                         _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def lobpcg(self, op: Operator, sub: Subspace, k: int = 1, want_vectors: bool = False, check: bool = True,
+               **params):
+        """The k lowest eigenpairs: (evals numpy [k], info dict[, vectors tensor
+        [D, k]]).  Keyword arguments set fields of qsd_lobpcg_params."""
+        p = LobpcgParams()
+        lib().qsd_lobpcg_default_params(C.byref(p))
+        p.k = int(k)
+        x0 = params.pop("x0", None)
+        for key, v in params.items():
+            setattr(p, key, v)
+        if x0 is not None:
+            p.x0 = C.c_void_p(x0.data_ptr())
+        ev = np.zeros(k)
+        info = LobpcgInfo()
+        vec = self.empty((sub.dim, k), self.torch.float64) if want_vectors else None
+        rc = lib().qsd_lobpcg(self.handle, op.handle, sub.handle, C.byref(p), _np_ptr(ev),
+                              _t_ptr(vec) if vec is not None else None, C.byref(info))
+        d = {f: getattr(info, f) for f, _ in LobpcgInfo._fields_ if f != "reserved"}
+        if check and rc not in (QSD_OK, 7):
+            self._check(rc)
+        d["status"] = STATUS.get(rc, rc)
+        return (ev, d, vec) if want_vectors else (ev, d)
 
     def ramps(self, op: Operator, start: Subspace, E: float, tau: float, max_levels: int = 16,
               restrict: Subspace | None = None, max_rows: int = 0):

@@ -777,6 +777,39 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
     });
 }
 
+void qsd_lobpcg_default_params(qsd_lobpcg_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->k = 1;
+    p->max_iters = 500;
+    p->tol = 1e-9;
+    p->precondition = 1;
+}
+
+int qsd_lobpcg(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lobpcg_params *p, double *evals, double *evecs,
+               qsd_lobpcg_info *info) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int status = QSD_OK;
+    const int rc = [&]() -> int {
+        QSD_GUARD(ctx, {
+            check_pair(ctx, op, sub);
+            if (!p || !evals || !info) fail(QSD_ERR_INVALID_ARG, "qsd_lobpcg: NULL params, evals or info");
+            if (p->k < 1 || p->k > 16 || sub->D < 3 * (int64_t)p->k)
+                fail(QSD_ERR_INVALID_ARG, "qsd_lobpcg: need 1 <= k <= 16 and dim >= 3k");
+            if (p->start != 0 && p->start != 1) fail(QSD_ERR_INVALID_ARG, "qsd_lobpcg: start must be 0 or 1");
+            if (!op->info.is_real) fail(QSD_ERR_COMPLEX_UNSUPPORTED, "qsd_lobpcg: complex operator");
+            if (!op->info.is_hermitian) fail(QSD_ERR_NOT_HERMITIAN, "qsd_lobpcg: operator is not Hermitian");
+            set_device(ctx);
+            Binding *b = get_binding(ctx, op, sub);
+            status = lobpcg(ctx, op, sub, b->diag.as<double>(), *p, evals, evecs, info);
+        });
+    }();
+    if (rc != QSD_OK) return rc;
+    if (status != QSD_OK) ctx->last_error = "qsd_lobpcg: not converged";
+    return status;
+}
+
 int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32_t max_levels,
               qsd_sub restrict_to, int64_t max_rows, qsd_sub *out, qsd_ramps_info *info) {
     if (!ctx) return QSD_ERR_INVALID_ARG;

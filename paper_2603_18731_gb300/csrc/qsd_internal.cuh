@@ -417,6 +417,10 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
 int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr, void *indices, int index_bits,
                double *data_re, double *data_im, const double *diag);
 
+// Block eigensolver (lobpcg.cu); returns the status it also stores in info.
+int lobpcg(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const qsd_lobpcg_params &p, double *evals,
+           double *evecs, qsd_lobpcg_info *info);
+
 // Complex product (apply_complex.cu): x, y complex128 [D][k] interleaved.
 void apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int k, const void *x, void *y);
 
