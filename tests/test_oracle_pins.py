@@ -384,3 +384,26 @@ def test_ramps_restricted_and_level_limit():
     assert keys[:, 0].tolist() == [0, 1]  # 11 (= 3) is outside the allowed set, so 10 is never reached
     keys, levels = ramps.ramps(op, start, -5.0, 0.0, max_levels=2)
     assert len(levels) == 2 and keys[:, 0].tolist() == [0, 1, 3]
+
+
+# ------------------------------------------------------------- trimming --
+def test_trim_hand_example():
+    # 3 qubits, diagonal -1.0 Z0 - 0.5 Z1 - 0.25 Z2 over the full space: the
+    # lowest diagonal is -1.75 (000), the next -1.25 (100): splitting 0.5.
+    # Flip groups: X0 (0.3) -> 0.6, X1 (1e-4) -> 2e-4, X0 X2 (0.02 + 0.01 via
+    # two words) -> 0.06, X1 X2 with words 0.1 and -0.1 (combined: 0) -> 0.
+    from oracle import trim
+    terms = [(1.0, [(0, "Z")]), (0.5, [(1, "Z")]), (0.25, [(2, "Z")]),
+             (0.3, [(0, "X")]), (1e-4, [(1, "X")]),
+             (0.02, [(0, "X"), (2, "X")]), (0.01, [(0, "Y"), (2, "Y")]),
+             (0.1, [(1, "X"), (2, "X")]), (-0.1, [(2, "X"), (1, "X")])]
+    op = wl.QubitOperator.from_terms(3, [(-c if i < 3 else c, w) for i, (c, w) in enumerate(terms)])
+    keys = _sorted_keys(wl.full_space(3))
+    kept, idx, split = trim.trim(op, keys, 0.01)
+    assert split == 0.5
+    assert kept == {(0b001,), (0b101,)}  # 0.6 and 0.06 pass 0.01, 2e-4 and 0 do not
+    assert idx == [0, 1, 2, 3, 5, 6]
+    kept, idx, _ = trim.trim(op, keys, 0.0)
+    assert kept == {(0b001,), (0b010,), (0b101,), (0b110,)}
+    kept, idx, _ = trim.trim(op, keys, 2.0)
+    assert kept == set() and idx == [0, 1, 2]
