@@ -215,6 +215,23 @@ void qsd_lobpcg_default_params(qsd_lobpcg_params *p);
 int qsd_lobpcg(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lobpcg_params *p, double *evals,
                double *evecs, qsd_lobpcg_info *info);
 
+/* -------------------------------------------------------------- trimming */
+/* Operator group trimming (Results, chemistry: groups whose matrix elements
+ * are small against the smallest diagonal energy splitting of the subspace
+ * are removed before matrix evaluation).  A group's elements are bounded by
+ * m_g = sum of |phi_t| over its terms (equal words combined); the splitting is
+ * Delta = min over rows of sub with d_r > d_min of (d_r - d_min).  Groups with
+ * m_g / Delta < tol are removed; diagonal words and the identity are kept
+ * (everything is kept when all diagonal entries of sub are equal).  *out gets
+ * a new operator loaded from the kept input words (caller frees it); info
+ * (may be NULL) reports the counts, d_min and Delta. */
+typedef struct {
+    int64_t groups_in, groups_kept;
+    int64_t terms_in, terms_kept;  /* input words */
+    double d_min, splitting;
+} qsd_trim_info;
+int qsd_trim_operator(qsd_ctx ctx, qsd_op op, qsd_sub sub, double tol, qsd_op *out, qsd_trim_info *info);
+
 /* ------------------------------------------------------------------ RAMPS */
 /* Subspace refinement RAMPS (Supplementary, "Recursive algorithm for a
  * minimal perturbative subspace", Algorithm S1; expansion Eq. S2), run level

@@ -65,6 +65,11 @@ class LobpcgInfo(C.Structure):
                 ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
+class TrimInfo(C.Structure):
+    _fields_ = [("groups_in", C.c_int64), ("groups_kept", C.c_int64), ("terms_in", C.c_int64),
+                ("terms_kept", C.c_int64), ("d_min", C.c_double), ("splitting", C.c_double)]
+
+
 class RampsInfo(C.Structure):
     _fields_ = [("levels", C.c_int32), ("stopped_by_limit", C.c_int32), ("truncated", C.c_int32),
                 ("reserved", C.c_int32), ("rows_out", C.c_int64), ("candidates", C.c_int64),
@@ -99,6 +104,7 @@ SIGNATURES = [
     ("qsd_apply_H_batch", C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P, _P]),
     ("qsd_apply_H_complex", C.c_int, [_P, _P, _P, _I32, _P, _P]),
     ("qsd_to_csr", C.c_int, [_P, _P, _P, _I32, C.POINTER(C.c_int64), _P, _P, _I32, _P, _P]),
+    ("qsd_trim_operator", C.c_int, [_P, _P, _P, _D, C.POINTER(_P), C.POINTER(TrimInfo)]),
     ("qsd_lobpcg_default_params", None, [C.POINTER(LobpcgParams)]),
     ("qsd_lobpcg", C.c_int, [_P, _P, _P, C.POINTER(LobpcgParams), _P, _P, C.POINTER(LobpcgInfo)]),
     ("qsd_ramps", C.c_int, [_P, _P, _P, _D, _D, _I32, _P, _I64, C.POINTER(_P), C.POINTER(RampsInfo)]),
@@ -375,6 +381,15 @@ class Context:
         self._check(lib().qsd_rayleigh_quotient_noalloc(self.handle, op.handle, sub.handle, _t_ptr(u),
                                                         _np_ptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def trim_operator(self, op: Operator, sub: Subspace, tol: float):
+        """Operator without the groups whose element bound over the subspace's
+        smallest diagonal splitting is below ``tol``: (Operator, info dict)."""
+        h = C.c_void_p()
+        info = TrimInfo()
+        self._check(lib().qsd_trim_operator(self.handle, op.handle, sub.handle, float(tol), C.byref(h),
+                                            C.byref(info)))
+        return Operator(self, h, op.n_qubits), {f: getattr(info, f) for f, _ in TrimInfo._fields_}
 
     def lobpcg(self, op: Operator, sub: Subspace, k: int = 1, want_vectors: bool = False, check: bool = True,
                **params):

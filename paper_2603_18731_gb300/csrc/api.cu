@@ -777,6 +777,29 @@ int qsd_to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t flags, int64_t *nnz_
     });
 }
 
+int qsd_trim_operator(qsd_ctx ctx, qsd_op op, qsd_sub sub, double tol, qsd_op *out, qsd_trim_info *info) {
+    if (!ctx) return QSD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    QSD_GUARD(ctx, {
+        check_pair(ctx, op, sub);
+        if (!out || !(tol >= 0.0)) fail(QSD_ERR_INVALID_ARG, "qsd_trim_operator: NULL out or tol < 0");
+        set_device(ctx);
+        Binding *b = get_binding(ctx, op, sub);
+        auto *o = new qsd_op_s();
+        o->ctx = ctx;
+        o->n_qubits = op->n_qubits;
+        o->W = op->W;
+        qsd_trim_info local{};
+        try {
+            trim_operator(ctx, op, sub, b->diag.as<double>(), tol, o, info ? info : &local);
+        } catch (...) {
+            delete o;
+            throw;
+        }
+        *out = o;
+    });
+}
+
 void qsd_lobpcg_default_params(qsd_lobpcg_params *p) {
     if (!p) return;
     std::memset(p, 0, sizeof(*p));

@@ -435,6 +435,16 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
         if (term_ptr[t + 1] < term_ptr[t]) fail(QSD_ERR_INVALID_ARG, "load_operator: term_ptr not non-decreasing");
     if (term_ptr[n_terms] > 0 && (!op_qubit || !op_code)) fail(QSD_ERR_INVALID_ARG, "load_operator: missing factors");
     if (n_terms >= (int64_t)0x7fffffff) fail(QSD_ERR_CAPACITY, "load_operator: too many terms");
+    {
+        // keep the input words for operators derived from this one (trimming)
+        const int64_t nf = term_ptr[n_terms];
+        op->in_term_ptr.assign(term_ptr, term_ptr + n_terms + 1);
+        op->in_qubit.assign(op_qubit, op_qubit + (nf > 0 ? nf : 0));
+        op->in_code.assign(op_code, op_code + (nf > 0 ? nf : 0));
+        op->in_re.assign(coef_re, coef_re + n_terms);
+        if (coef_im) op->in_im.assign(coef_im, coef_im + n_terms);
+        else op->in_im.assign((size_t)n_terms, 0.0);
+    }
 
     // ---- host: words -> masks (input order), validation
     const int64_t Ti = n_terms;

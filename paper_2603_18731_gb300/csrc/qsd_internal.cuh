@@ -185,6 +185,11 @@ struct qsd_op_s {
     qsd::DevBuf iF, iP, iV, iZ;  // uint64 [W][T_in]
     qsd::DevBuf iY;              // uint8 [T_in] number of Y letters mod 4
     std::vector<uint64_t> host_groups;  // [G][W]
+    // the input words as given (host), for operators derived from this one
+    std::vector<int64_t> in_term_ptr;
+    std::vector<int32_t> in_qubit;
+    std::vector<uint8_t> in_code;
+    std::vector<double> in_re, in_im;
 };
 
 namespace qsd {
@@ -420,6 +425,11 @@ int64_t to_csr(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lower, int64_t *indptr,
 // Block eigensolver (lobpcg.cu); returns the status it also stores in info.
 int lobpcg(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, const qsd_lobpcg_params &p, double *evals,
            double *evecs, qsd_lobpcg_info *info);
+
+// Group trimming (trim.cu): `out` is a fresh operator handle (ctx, n_qubits,
+// W set) loaded from the kept input words of `op`.
+void trim_operator(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, double tol, qsd_op out,
+                   qsd_trim_info *info);
 
 // Complex product (apply_complex.cu): x, y complex128 [D][k] interleaved.
 void apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int k, const void *x, void *y);
