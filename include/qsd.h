@@ -132,7 +132,7 @@ int qsd_free_op(qsd_op op);
  * when words_on_device == 0, else device memory), any order, duplicates
  * allowed (Methods, "Subspace data structure").  The strings are sorted by
  * integer value on the device, duplicates dropped, and an open-addressing
- * hash table (load factor <= 1/4, buckets of eight 16-bit tags with a 32-bit
+ * hash table (load factor <= 1/4, buckets of eight 8-bit tags with a 32-bit
  * row index per slot) is built for lookups.  *dim_out receives D.  Synchronises.
  * Errors: QSD_ERR_CAPACITY when D would exceed 2^32 - 2. */
 int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,

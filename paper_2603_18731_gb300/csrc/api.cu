@@ -206,7 +206,7 @@ ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag,
 
 ExcParams make_exc(qsd_op op) {
     ExcParams e{};
-    e.ght = HashView{op->gtags.as<uint16_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
+    e.ght = HashView{op->gtags.as<uint8_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
                      (uint64_t)op->g_nbuckets - 1, op->g_shift};
     e.exc_gid = op->exc_gid.as<int32_t>();
     e.rest_gid = op->rest_gid.as<int32_t>();

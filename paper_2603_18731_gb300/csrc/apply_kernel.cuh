@@ -204,7 +204,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
         // phase 1: element of each of U groups, and its bucket load in flight
         double a[U];
         float ah[U], al[U];
-        uint4 tb[U];
+        uint2 tb[U];
         uint64_t bidx[U];
         uint32_t tag[U];
         uint32_t aidx[U];  // table groups: amplitude index; kNoTable: a[u] holds the element
@@ -272,8 +272,8 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             }            need[u] = active && nz;
             if (need[u]) {
                 bidx[u] = hash_bucket(hr ^ hF, p.hv.shift, tag[u]);
-                // bucket counts stay below 2^32: a 32-bit index into 16-byte buckets
-                tb[u] = __ldg(reinterpret_cast<const uint4 *>(p.hv.tags) + (uint32_t)bidx[u]);
+                // bucket counts stay below 2^32: a 32-bit index into 8-byte buckets
+                tb[u] = __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + (uint32_t)bidx[u]);
             }
         }
         // phase 2: resolve the lookups and accumulate

@@ -206,10 +206,10 @@ struct Binding {
 // group costs one xor.  (2) One multiplicative step (multiply-shift hashing,
 // Dietzfelbinger et al. 1997, with the golden-ratio multiplier of Fibonacci
 // hashing) on a 32-bit fold of h gives the bucket (top bits of the product)
-// and a second product gives a 16-bit tag (never 0).
+// and a second product gives an 8-bit tag (never 0).
 //
-// Table layout: buckets of 8 slots.  tags: uint16 [8 * n_buckets], 0 = empty,
-// one 16-byte load per bucket; sidx: uint32 [8 * n_buckets], the row index of
+// Table layout: buckets of 8 slots.  tags: uint8 [8 * n_buckets], 0 = empty,
+// one 8-byte load per bucket; sidx: uint32 [8 * n_buckets], the row index of
 // each occupied slot, read only when its tag matches.  Slots of a bucket fill
 // in order, so a bucket whose last slot is empty ends the probe.  Tag
 // collisions only cost a key comparison: every hit is verified against the
@@ -228,7 +228,7 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
 // 16 bits of a second, xorshifted multiply.
 __host__ __device__ __forceinline__ uint64_t hash_bucket(uint64_t h, int shift, uint32_t &tag) {
     const uint32_t x = (uint32_t)h ^ ((uint32_t)(h >> 32) * 0x9E3779B1u);
-    const uint32_t t = ((x ^ (x >> 15)) * 0xC2B2AE3Du) >> 16;
+    const uint32_t t = ((x ^ (x >> 15)) * 0xC2B2AE3Du) >> 24;
     tag = t ? t : 1u;
     return (uint64_t)((x * 0x85EBCA77u) >> shift);
 }
@@ -262,39 +262,37 @@ uint64_t host_prehash(const uint64_t *x, int W);
 const std::vector<uint64_t> &host_nibble_tables(int W);
 void ensure_nibble_tables(qsd_ctx ctx, int W);
 
-// The 8 tags of bucket b.
-__device__ __forceinline__ uint4 load_tags(const uint16_t *__restrict__ tags, uint64_t b) {
-    return __ldg(reinterpret_cast<const uint4 *>(tags + b * kBucketSlots));
+// The 8 one-byte tags of bucket b (slot i in byte i of the 8-byte word).
+__device__ __forceinline__ uint2 load_tags(const uint8_t *__restrict__ tags, uint64_t b) {
+    return __ldg(reinterpret_cast<const uint2 *>(tags) + b);
 }
 
-// For v = (tags of two slots) xor (tag, tag): nonzero iff one halfword of v
-// is zero, i.e. one of the two slots matches (the "has a zero element" test of
-// Hacker's Delight, section 6-1, on 16-bit lanes; exact as an existence test).
-__device__ __forceinline__ uint32_t zero_half(uint32_t v) { return (v - 0x00010001u) & ~v & 0x80008000u; }
+// Nonzero iff some byte of v is zero (the "has a zero byte" test of Hacker's
+// Delight, section 6-1; exact as an existence test).
+__device__ __forceinline__ uint32_t zero_byte(uint32_t v) { return (v - 0x01010101u) & ~v & 0x80808080u; }
 
 // Bit i set when tag i of the bucket equals `tag` (exact per slot).
-__device__ __forceinline__ uint32_t tag_match(const uint4 t, uint32_t tag) {
-    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+__device__ __forceinline__ uint32_t tag_match(const uint2 t, uint32_t tag) {
     uint32_t m = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        m |= (((w[i] & 0xffffu) == tag) ? 1u : 0u) << (2 * i);
-        m |= (((w[i] >> 16) == tag) ? 1u : 0u) << (2 * i + 1);
+        m |= ((((t.x >> (8 * i)) & 0xffu) == tag) ? 1u : 0u) << i;
+        m |= ((((t.y >> (8 * i)) & 0xffu) == tag) ? 1u : 0u) << (i + 4);
     }
     return m;
 }
 
 // Some tag of the bucket equals `tag`.
-__device__ __forceinline__ bool tag_any(const uint4 t, uint32_t tag) {
-    const uint32_t tt = tag | (tag << 16);
-    return (zero_half(t.x ^ tt) | zero_half(t.y ^ tt) | zero_half(t.z ^ tt) | zero_half(t.w ^ tt)) != 0u;
+__device__ __forceinline__ bool tag_any(const uint2 t, uint32_t tag) {
+    const uint32_t tt = tag * 0x01010101u;
+    return (zero_byte(t.x ^ tt) | zero_byte(t.y ^ tt)) != 0u;
 }
 
 // The bucket's last slot is occupied: the probe continues in the next bucket.
-__device__ __forceinline__ bool bucket_full(const uint4 t) { return (t.w >> 16) != 0u; }
+__device__ __forceinline__ bool bucket_full(const uint2 t) { return (t.y >> 24) != 0u; }
 
 struct HashView {
-    const uint16_t *tags;
+    const uint8_t *tags;
     const uint32_t *sidx;
     const uint64_t *keys;  // [W][D]
     int64_t D;
@@ -323,7 +321,7 @@ template <int W>
 __device__ int64_t probe_from(const HashView &hv, uint64_t b, uint32_t tag, const uint64_t (&c)[W], uint32_t *err) {
     for (uint64_t step = 1; step <= hv.bmask; ++step) {
         b = (b + 1) & hv.bmask;
-        const uint4 t = load_tags(hv.tags, b);
+        const uint2 t = load_tags(hv.tags, b);
         const int64_t idx = verify_matches<W>(hv, b, tag_match(t, tag), c);
         if (idx >= 0) return idx;
         if (!bucket_full(t)) return -1;
@@ -338,7 +336,7 @@ template <int W>
 __device__ __forceinline__ int64_t probe(const uint64_t (&c)[W], uint64_t hc, const HashView &hv, uint32_t *err) {
     uint32_t tag;
     const uint64_t b = hash_bucket(hc, hv.shift, tag);
-    const uint4 t = load_tags(hv.tags, b);
+    const uint2 t = load_tags(hv.tags, b);
     const int64_t idx = verify_matches<W>(hv, b, tag_match(t, tag), c);
     if (idx >= 0 || !bucket_full(t)) return idx;
     return probe_from<W>(hv, b, tag, c, err);
@@ -349,7 +347,7 @@ __device__ __forceinline__ int64_t probe_dyn(const uint64_t *c, int W, uint64_t 
     uint32_t tag;
     uint64_t b = hash_bucket(hc, hv.shift, tag);
     for (uint64_t step = 0; step <= hv.bmask; ++step) {
-        const uint4 t = load_tags(hv.tags, b);
+        const uint2 t = load_tags(hv.tags, b);
         uint32_t match = tag_match(t, tag);
         while (match) {
             const int i = __ffs(match) - 1;
@@ -401,7 +399,7 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op);
 // first string, or -1 when the operator has no excitation index.
 double excitation_candidates(qsd_op op, qsd_sub sub);
 inline HashView hash_view(qsd_sub sub) {
-    return HashView{sub->tags.as<uint16_t>(), sub->sidx.as<uint32_t>(), sub->keys.as<uint64_t>(), sub->D,
+    return HashView{sub->tags.as<uint8_t>(), sub->sidx.as<uint32_t>(), sub->keys.as<uint64_t>(), sub->D,
                     (uint64_t)sub->n_buckets - 1, sub->bucket_shift};
 }
 void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_ptr,

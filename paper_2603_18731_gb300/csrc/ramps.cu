@@ -243,7 +243,7 @@ void ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int max_
     int level = 0;
     while (nF > 0 && level < max_levels && op->G > 0) {
         HashTable ht = build_hash(ctx, okeys.as<uint64_t>(), W, n_out);
-        p.out = HashView{ht.tags.as<uint16_t>(), ht.sidx.as<uint32_t>(), okeys.as<uint64_t>(), n_out,
+        p.out = HashView{ht.tags.as<uint8_t>(), ht.sidx.as<uint32_t>(), okeys.as<uint64_t>(), n_out,
                          (uint64_t)ht.n_buckets - 1, ht.shift};
         p.fkeys = fkeys.as<uint64_t>();
         p.fpre = fpre.as<double>();

@@ -4,8 +4,8 @@
 // occupancy bit-set for fast rejection of empty buckets.  Here the strings are
 // sorted by integer value on the device (index = rank, the order the MSOB
 // triangle test needs) and stored as coalesced SoA words; a separate open
-// addressing table of 8-slot buckets (16-bit tags, 32-bit row indices)
-// serves lookups: one 16-byte load of eight 16-bit tags rejects almost every
+// addressing table of 8-slot buckets (8-bit tags, 32-bit row indices)
+// serves lookups: one 8-byte load of eight one-byte tags rejects almost every
 // absent key, as the occupancy bit-set did, and the load factor is kept
 // <= 1/4 because D is known before the table is built.
 #include <algorithm>
@@ -15,6 +15,10 @@
 namespace qsd {
 
 namespace {
+
+// Load factor <= 1/4 (measured on GB300: 1/8 gained 4 % on the 200-qubit
+// Ising product and lost 11 % on the fermionic block product).
+constexpr int64_t kLoadDiv = 4;
 
 __global__ void k_aos_to_soa(const uint64_t *__restrict__ in, int W, int64_t n, uint64_t *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,15 +38,23 @@ __global__ void k_mask_top(uint64_t *words, int W, int64_t n, uint64_t top_mask,
     if (words[(size_t)i * W + W - 1] & ~top_mask) atomicOr(err, 2u);
 }
 
-// One thread per key.  The slots of a bucket are claimed in order with a
-// 16-bit CAS on the tag, then the row index is stored; so in the finished
-// table every probe that would reach a later slot passes an occupied one.
-__device__ __forceinline__ bool claim_slot(unsigned short *tags, uint32_t *sidx, uint64_t b, uint32_t tag,
-                                           uint32_t i) {
+// One thread per key.  The slots of a bucket are claimed in order, each by a
+// compare-and-swap on the 32-bit word holding its tag byte; then the row
+// index is stored.  So in the finished table every probe that would reach a
+// later slot passes an occupied one.
+__device__ __forceinline__ bool claim_slot(uint8_t *tags, uint32_t *sidx, uint64_t b, uint32_t tag, uint32_t i) {
+    unsigned int *words = reinterpret_cast<unsigned int *>(tags + b * kBucketSlots);
     for (int s = 0; s < kBucketSlots; ++s) {
-        if (atomicCAS(tags + b * kBucketSlots + s, (unsigned short)0, (unsigned short)tag) == 0) {
-            sidx[b * kBucketSlots + s] = i;
-            return true;
+        unsigned int *w = words + (s >> 2);
+        const int sh = 8 * (s & 3);
+        unsigned int old = *reinterpret_cast<volatile unsigned int *>(w);
+        while (((old >> sh) & 0xffu) == 0u) {
+            const unsigned int prev = atomicCAS(w, old, old | (tag << sh));
+            if (prev == old) {
+                sidx[b * kBucketSlots + s] = i;
+                return true;
+            }
+            old = prev;  // another byte of the word changed, or this slot was taken
         }
     }
     return false;
@@ -50,7 +62,7 @@ __device__ __forceinline__ bool claim_slot(unsigned short *tags, uint32_t *sidx,
 
 template <int W>
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ nib,
-                              unsigned short *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint32_t *err) {
+                              uint8_t *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     uint64_t x[W];
@@ -66,7 +78,7 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, cons
 }
 
 __global__ void k_hash_insert_dyn(const uint64_t *__restrict__ keys, int W, int64_t D,
-                                  const uint64_t *__restrict__ nib, unsigned short *tags, uint32_t *sidx,
+                                  const uint64_t *__restrict__ nib, uint8_t *tags, uint32_t *sidx,
                                   uint64_t bucket_mask, int shift, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
@@ -159,19 +171,19 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D) {
     HashTable t;
     // load factor <= 1/4 over buckets of 8 slots: a bucket overflows into the
     // next one with probability ~1e-3, so probes almost never diverge
-    t.n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (4 * D + kBucketSlots - 1) / kBucketSlots));
+    t.n_buckets = (int64_t)next_pow2((uint64_t)std::max<int64_t>(2, (kLoadDiv * D + kBucketSlots - 1) / kBucketSlots));
     int lg = 0;
     while ((1ll << lg) < t.n_buckets) ++lg;
     if (lg > 32) fail(QSD_ERR_CAPACITY, "hash table larger than 2^32 buckets");
     t.shift = 32 - lg;
     const size_t cap = (size_t)t.n_buckets * kBucketSlots;
-    t.tags.alloc(cap * 2);
+    t.tags.alloc(cap);
     t.sidx.alloc(cap * 4);
-    QSD_CUDA(cudaMemsetAsync(t.tags.p, 0, cap * 2, s));
+    QSD_CUDA(cudaMemsetAsync(t.tags.p, 0, cap, s));
     if (D > 0) {
         QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
         const uint64_t mask = (uint64_t)t.n_buckets - 1;
-        auto *tg = t.tags.as<unsigned short>();
+        auto *tg = t.tags.as<uint8_t>();
         auto *si = t.sidx.as<uint32_t>();
         const uint64_t *nib = ctx->nib.as<uint64_t>();
         const int nb = blocks_for(D, 256);
