@@ -39,7 +39,10 @@ import workloads as wl  # noqa: E402
 
 METRIC = "apply_H Gelem/s FP64 vs FP32-mixed block; served eigensolves/s, p50/p99 latency"
 L2_FLUSH_BYTES = 512 << 20
-PATH_NAMES = {0: "group scan, lane per row", 1: "group scan, 8 lanes per row", 2: "excitation index"}
+PATH_NAMES = {0: "group scan, lane per row", 1: "group scan, 8 lanes per row", 2: "excitation index",
+              3: "half evaluation, lane per row", 4: "half evaluation, 8 lanes per row",
+              5: "group scan, lane per row, rows in hash order",
+              6: "half evaluation, lane per row, rows in hash order"}
 
 
 # ------------------------------------------------------------------ workloads
@@ -262,13 +265,26 @@ def run_gpu(args):
         # atomic adds (summation order varies between runs)
         ctx.set_tuning(1, 3)
         for name, x, k in (("fp64_k1_half", x64, 1), ("fp64_k16_half", xb64, 16)):
-            for lanes in (1, 8):
+            for lanes, order, tag in ((1, 1, "lanes1"), (8, 1, "lanes8"), (1, 2, "hash_order")):
                 ctx.set_tuning(2, lanes)
+                ctx.set_tuning(5, order)
                 m, _, _ = time_variant(x, q.QSD_FP64, vsteps, 3)
-                key = f"{name}_lanes{lanes}"
-                variants[key] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
+                variants[f"{name}_{tag}"] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
         ctx.set_tuning(1, 0)
         ctx.set_tuning(2, 0)
+        ctx.set_tuning(5, 0)
+    if args.workload != "chem" and W <= 4:
+        # every group-scan launch shape, forced (the tuner picks among these)
+        ctx.set_tuning(1, 1)
+        for name, x, prec, k in (("fp64_k1", x64, q.QSD_FP64, 1), ("fp32_mixed_k16", xb32, q.QSD_FP32_MIXED, 16)):
+            for lanes, order, tag in ((1, 1, "lanes1"), (8, 1, "lanes8"), (1, 2, "hash_order")):
+                ctx.set_tuning(2, lanes)
+                ctx.set_tuning(5, order)
+                m, _, _ = time_variant(x, prec, vsteps, 3)
+                variants[f"{name}_scan_{tag}"] = {"ms": m, "gelem_s": elems * k / (m * 1e-3) / 1e9}
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(2, 0)
+        ctx.set_tuning(5, 0)
     fp64_1 = (variants["fp64_k1"]["gelem_s"] if args.workload == "chem" else elems / (ms64 * 1e-3) / 1e9)
     variants["mixed_block_over_fp64"] = variants["fp32_mixed_k16"]["gelem_s"] / fp64_1
     variants["dot2_block_over_fp64"] = variants["fp32_dot2_k16"]["gelem_s"] / fp64_1

@@ -133,7 +133,10 @@ int qsd_free_op(qsd_op op);
  * allowed (Methods, "Subspace data structure").  The strings are sorted by
  * integer value on the device, duplicates dropped, and an open-addressing
  * hash table (load factor <= 1/4, buckets of eight 8-bit tags with a 32-bit
- * row index per slot) is built for lookups.  *dim_out receives D.  Synchronises.
+ * row index per slot, bucket and tag taken from one GF(2)-linear hash of the
+ * string) is built for lookups; for n <= 256 the rows are also listed in
+ * bucket order (4 + 8 W bytes per row) for the hash-order product.  *dim_out
+ * receives D.  Synchronises.
  * Errors: QSD_ERR_CAPACITY when D would exceed 2^32 - 2. */
 int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,
                        const uint64_t *words, int words_on_device,
@@ -284,6 +287,15 @@ int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32
                                       h x[r] to y[c] by FP64 atomic adds: half the element
                                       evaluations and lookups, but a summation order (so
                                       the last bits of y) that varies from run to run. */
+#define QSD_TUNE_ROW_ORDER      5  /* lane-per-row scans (n <= 256): 0 auto (the autotuner
+                                      also times hash order), 1 index order, 2 hash order.
+                                      Hash order takes the rows in the order of the
+                                      subspace's hash buckets instead of by index: the key
+                                      hash is GF(2)-linear, so the column r xor F of every
+                                      row of a warp falls in a few neighbouring buckets and
+                                      each group's 32 lookups share cache lines.  Per row
+                                      the result is bitwise that of index order (same
+                                      groups, same order).  No counterpart in the paper. */
 
 /* Set a product-path choice on a context (later products of this context
  * use it).  Results are identical up to summation order for every choice; a
@@ -294,7 +306,8 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
  * columns takes for its first column block (16, 4 or 1 columns wide), without
  * timing anything: QSD_PATH_SCAN_1 (per-row group scan, one lane per row),
  * QSD_PATH_SCAN_8 (eight lanes per row), QSD_PATH_EXCITATION, or the half
- * evaluation with one or eight lanes per row (QSD_PATH_HALF_1, _8).  After a
+ * evaluation with one or eight lanes per row (QSD_PATH_HALF_1, _8), or a
+ * one-lane path in hash order (QSD_PATH_SCAN_HASH, _HALF_HASH).  After a
  * tuned product it is the cached measurement, else the forced choice or the
  * heuristic.  No counterpart in the paper (its kernel has one launch shape). */
 #define QSD_PATH_SCAN_1     0
@@ -302,6 +315,8 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
 #define QSD_PATH_EXCITATION 2
 #define QSD_PATH_HALF_1     3
 #define QSD_PATH_HALF_8     4
+#define QSD_PATH_SCAN_HASH  5  /* QSD_PATH_SCAN_1 with the rows in hash order */
+#define QSD_PATH_HALF_HASH  6  /* QSD_PATH_HALF_1 with the rows in hash order */
 int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
                      int64_t k, int32_t *path_out);
 

@@ -66,25 +66,26 @@ uint64_t splitmix_next(uint64_t &state) {
     return fmix64(state);
 }
 std::mutex g_nib_mu;
-std::vector<uint64_t> g_nib;  // [(W-1)*256]
-int g_nib_words = 1;
+std::vector<uint64_t> g_nib;  // [W*256]
+int g_nib_words = 0;
 }  // namespace
 
 const std::vector<uint64_t> &host_nibble_tables(int W) {
     std::lock_guard<std::mutex> lk(g_nib_mu);
     if (W > g_nib_words) {
-        // random GF(2) columns Q[q] for qubits 64..64W-1, fixed seed
+        // random GF(2) columns Q[q] for qubits 0..64W-1, fixed seed (the
+        // columns of a smaller W are a prefix: tables only ever grow)
         uint64_t st = 0x5153445F48415348ull;  // "QSD_HASH"
         std::vector<uint64_t> Q((size_t)64 * W);
         for (auto &v : Q) v = splitmix_next(st);
-        g_nib.assign((size_t)(W - 1) * 256, 0);
-        for (int w = 1; w < W; ++w)
+        g_nib.assign((size_t)W * 256, 0);
+        for (int w = 0; w < W; ++w)
             for (int j = 0; j < 16; ++j)
                 for (int v = 0; v < 16; ++v) {
                     uint64_t h = 0;
                     for (int b = 0; b < 4; ++b)
                         if ((v >> b) & 1) h ^= Q[(size_t)64 * w + 4 * j + b];
-                    g_nib[(size_t)(w - 1) * 256 + j * 16 + v] = h;
+                    g_nib[(size_t)w * 256 + j * 16 + v] = h;
                 }
         g_nib_words = W;
     }
@@ -93,9 +94,9 @@ const std::vector<uint64_t> &host_nibble_tables(int W) {
 
 uint64_t host_prehash(const uint64_t *x, int W) {
     const auto &t = host_nibble_tables(W);
-    uint64_t h = x[0];
-    for (int w = 1; w < W; ++w)
-        for (int j = 0; j < 16; ++j) h ^= t[(size_t)(w - 1) * 256 + j * 16 + ((x[w] >> (4 * j)) & 15)];
+    uint64_t h = 0;
+    for (int w = 0; w < W; ++w)
+        for (int j = 0; j < 16; ++j) h ^= t[(size_t)w * 256 + j * 16 + ((x[w] >> (4 * j)) & 15)];
     return h;
 }
 
@@ -196,6 +197,10 @@ ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag,
     p.tphi = op->tphi.as<double>();
     p.tflag = op->tflag.as<uint8_t>();
     p.diag = diag;
+    p.rhash = sub->rhash.as<uint64_t>();
+    p.hperm = sub->hperm.as<uint32_t>();
+    p.hkeys = sub->hkeys.as<uint64_t>();
+    p.hhash = sub->hhash.as<uint64_t>();
     p.x = x;
     p.y = y;
     p.ld = k;
@@ -221,11 +226,11 @@ ExcParams make_exc(qsd_op op) {
 // Product paths: 0 = per-row group scan with one lane per row, 1 = the same
 // with 8 lanes per row, 2 = excitation index (warp per row), 3 and 4 = the
 // half-evaluation scan (lower-triangle groups, mirrored by atomic adds) with
-// 1 or 8 lanes per row.
+// 1 or 8 lanes per row, 5 and 6 = paths 0 and 3 with the rows in hash order.
 void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int precision, int KB,
                  cudaStream_t stream) {
-    if (path == 3 || path == 4) {
-        launch_apply_sym(p, W, path == 4 ? 8 : 1, KB, stream);
+    if (path == 3 || path == 4 || path == 6) {
+        launch_apply_sym(p, W, path == 4 ? 8 : 1, KB, stream, path == 6);
         return;
     }
     if (path == 2) {
@@ -235,10 +240,14 @@ void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int 
         return;
     }
     const int R = path == 1 ? 8 : 1;
-    if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, W, R, KB, stream);
-    else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, W, R, KB, stream);
-    else launch_apply<QSD_FP32_DOT2>(p, W, R, KB, stream);
+    const bool ho = path == 5;
+    if (precision == QSD_FP64) launch_apply<QSD_FP64>(p, W, R, KB, stream, ho);
+    else if (precision == QSD_FP32_MIXED) launch_apply<QSD_FP32_MIXED>(p, W, R, KB, stream, ho);
+    else launch_apply<QSD_FP32_DOT2>(p, W, R, KB, stream, ho);
 }
+
+// The half-evaluation counterpart of a scan path.
+int half_of(int path) { return path == 5 ? 6 : path + 3; }
 
 int heuristic_path(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     if (use_excitation(ctx, op, sub)) return 2;
@@ -263,18 +272,25 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     // the half evaluation needs H = H^T (real Hermitian), FP64 storage and W <= 4
     const bool sym_ok = op->info.is_hermitian && op->info.is_real && precision == QSD_FP64 &&
                         op->W <= kMaxWordsStatic;
-    const int lanes_path = (ctx->tune_lanes ? ctx->tune_lanes : choose_lanes(ctx, sub->D, op->G)) == 8 ? 1 : 0;
+    // hash order: lane-per-row scans of subspaces that have one (W <= 4)
+    const bool ho_ok = op->W <= kMaxWordsStatic && sub->hperm.p != nullptr;
+    int lanes_path = (ctx->tune_lanes ? ctx->tune_lanes : choose_lanes(ctx, sub->D, op->G)) == 8 ? 1 : 0;
+    if (lanes_path == 0 && ho_ok && ctx->row_order == 2) lanes_path = 5;
     if (ctx->tune_mode == 1 || (ctx->tune_mode == 3 && !sym_ok)) return lanes_path;
-    if (ctx->tune_mode == 3) return lanes_path + 3;
+    if (ctx->tune_mode == 3) return half_of(lanes_path);
     if (ctx->tune_mode == 2 && op->exc_ok) return 2;
-    if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym)) return lanes_path;
+    const bool ho_open = ho_ok && ctx->row_order == 0 && lanes_path == 0;
+    if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym) && !ho_open) return lanes_path;
     const auto key = std::make_tuple((const void *)op, (const void *)sub, precision, KB);
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tune_cache.find(key);
         if (it != ctx->tune_cache.end()) return it->second;
     }
-    const int guess = heuristic_path(ctx, op, sub);
+    const int guess = [&] {
+        const int g = heuristic_path(ctx, op, sub);
+        return (g == 0 && ho_ok && ctx->row_order == 2) ? 5 : g;
+    }();
     if (!may_tune || !ctx->autotune || capturing(stream) || sub->D < 2048) return guess;
     // Candidates: the excitation index only where a row reaches fewer flip
     // masks than there are groups, the group scans only where the index does
@@ -290,10 +306,19 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
             cands.push_back(guess == 1 ? 1 : 0);
             cands.push_back(guess == 1 ? 0 : 1);
         }
+        if (ho_ok && ctx->row_order != 1) {
+            // the lane-per-row scan in hash order: beside index order (auto)
+            // or in its place (forced)
+            bool had0 = false;
+            for (int &c : cands)
+                if (c == 0 && ctx->row_order == 2) c = 5;
+                else if (c == 0) had0 = true;
+            if (had0) cands.push_back(5);
+        }
         if (sym_ok && ctx->allow_sym) {
             const size_t m = cands.size();
             for (size_t i = 0; i < m; ++i)
-                if (cands[i] < 2) cands.push_back(cands[i] + 3);
+                if (cands[i] < 2 || cands[i] == 5) cands.push_back(half_of(cands[i]));
         }
     }
     if (guess != 2 && cand >= 0.0 && cand < (double)op->G) cands.push_back(2);
@@ -735,6 +760,14 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
     case QSD_TUNE_HALF_EVALUATION:
         if (value != 0 && value != 1) return QSD_ERR_INVALID_ARG;
         ctx->allow_sym = (int)value;
+        {
+            std::lock_guard<std::mutex> lk2(ctx->tune_mu);
+            ctx->tune_cache.clear();
+        }
+        return QSD_OK;
+    case QSD_TUNE_ROW_ORDER:
+        if (value < 0 || value > 2) return QSD_ERR_INVALID_ARG;
+        ctx->row_order = (int)value;
         {
             std::lock_guard<std::mutex> lk2(ctx->tune_mu);
             ctx->tune_cache.clear();

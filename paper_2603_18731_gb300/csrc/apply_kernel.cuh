@@ -74,6 +74,10 @@ struct ApplyParams {
     const double *tphi;      // [T]
     const uint8_t *tflag;    // [T]
     const double *diag;      // [D]
+    const uint64_t *rhash;   // [D] hash h of each row
+    const uint32_t *hperm;   // [D] hash order: row at each position
+    const uint64_t *hkeys;   // [W][D] hash order: keys at the positions
+    const uint64_t *hhash;   // [D] hash order: h at the positions
     const void *x;
     void *y;
     int64_t ld;              // row stride of x and y (= k)
@@ -168,6 +172,11 @@ __device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e
 
 // One output row; the R lanes of a row call this together.
 //
+// HO (hash order, R = 1): `row` is a position in the subspace's bucket order;
+// the lane handles row hperm[row] with the key copy hkeys at that position
+// (coalesced), so that for each group the warp's 32 lookups fall in a few
+// consecutive buckets; diagonal, own x and y are then per-row gathers.
+//
 // SYM (Hermitian real operators, FP64 only): the row evaluates only the
 // groups whose most significant flipped qubit is set in it -- its
 // lower-triangle elements (Supplementary, "Lower / upper triangle
@@ -175,17 +184,20 @@ __device__ __forceinline__ void dot2_merge(float &s, float &e, float s2, float e
 // h x[r] to row c.  Both go to y by FP64 atomic adds into a zeroed y, so
 // every element is evaluated and looked up once instead of twice, at the
 // price of a summation order that varies from run to run.
-template <int W, int R, int KB, int PREC, bool SYM = false>
+template <int W, int R, int KB, int PREC, bool SYM = false, bool HO = false>
 __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t row) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     constexpr int U = ApplyShape<W, KB>::U;
+    static_assert(!HO || R == 1, "hash order: one lane per row");
     const int sub = threadIdx.x % R;
     const bool active = row < p.D;
-    const int64_t r = active ? row : p.D - 1;
+    const int64_t pos = active ? row : p.D - 1;
+    const int64_t r = HO ? (int64_t)__ldg(p.hperm + pos) : pos;
+    const uint64_t *__restrict__ kp = HO ? p.hkeys : p.keys;
     uint64_t key[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + r);
-    const uint64_t hr = prehash<W>(key, p.nib);
+    for (int w = 0; w < W; ++w) key[w] = __ldg(kp + (size_t)w * p.D + pos);
+    const uint64_t hr = __ldg((HO ? p.hhash : p.rhash) + pos);
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
     static_assert(!SYM || PREC == QSD_FP64, "half evaluation is FP64 only");
     // accumulators: FP64 (modes 0, 1) or FP32 (s, e) pairs (DOT2)
@@ -205,7 +217,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
         double a[U];
         float ah[U], al[U];
         uint2 tb[U];
-        uint64_t bidx[U];
+        uint32_t bidx[U];
         uint32_t tag[U];
         uint32_t aidx[U];  // table groups: amplitude index; kNoTable: a[u] holds the element
         bool need[U];
@@ -272,8 +284,7 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             }            need[u] = active && nz;
             if (need[u]) {
                 bidx[u] = hash_bucket(hr ^ hF, p.hv.shift, tag[u]);
-                // bucket counts stay below 2^32: a 32-bit index into 8-byte buckets
-                tb[u] = __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + (uint32_t)bidx[u]);
+                tb[u] = __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + bidx[u]);
             }
         }
         // phase 2: resolve the lookups and accumulate
@@ -331,9 +342,9 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
         }
     }
     if (active && sub == 0) {
-        const double d = __ldg(p.diag + row);
-        const TIO *xr = x + row * p.ld + p.col0;
-        TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0;
+        const double d = __ldg(p.diag + r);
+        const TIO *xr = x + r * p.ld + p.col0;
+        TIO *yr = static_cast<TIO *>(p.y) + r * p.ld + p.col0;
         if (PREC == QSD_FP32_DOT2) {
             const float dh = (float)d, dl = (float)(d - (double)dh);
 #pragma unroll
@@ -351,10 +362,11 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
     }
 }
 
-// One launch covers all rows: R lanes per row, rows past D inactive.
-template <int W, int R, int KB, int PREC, bool SYM = false>
+// One launch covers all rows: R lanes per row, rows past D inactive; HO:
+// rows in hash order.
+template <int W, int R, int KB, int PREC, bool SYM = false, bool HO = false>
 __global__ void __launch_bounds__(256, (ApplyShape<W, KB>::MINB)) k_apply(const ApplyParams p) {
-    apply_row<W, R, KB, PREC, SYM>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
+    apply_row<W, R, KB, PREC, SYM, HO>(p, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / R);
 }
 
 // Run-time W (W > kMaxWordsStatic): a lane per row, keys in local memory,
@@ -414,9 +426,10 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
     for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)xr[j], acc[j]);
 }
 
-// Launch one (W, R, KB) variant of precision mode PREC.
+// Launch one (W, R, KB) variant of precision mode PREC; hash_order (W <= 4,
+// R = 1) takes the rows in the subspace's bucket order.
 template <int PREC>
-void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
+void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s, bool hash_order = false);
 // Product parameters of one (operator, subspace) pair with x, y of row
 // stride k (column 0 first).
 ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y);
@@ -427,6 +440,6 @@ void launch_apply_batch(const ApplyParams *params, const int64_t *tile0, int n, 
                         int precision, cudaStream_t s);
 // Half-evaluation product (FP64, Hermitian real operators, W <= 4); zeroes
 // the launch's columns of y first.
-void launch_apply_sym(const ApplyParams &p, int W, int R, int KB, cudaStream_t s);
+void launch_apply_sym(const ApplyParams &p, int W, int R, int KB, cudaStream_t s, bool hash_order = false);
 
 }  // namespace qsd

@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     __shared__ uint8_t lists[8][4][64 * W];
     __shared__ int cnt[8][4];
+    __shared__ uint64_t bh[64 * W];  // h of each single qubit (the hash is linear)
+    for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) bh[q] = bit_hash(q, p.nib);
+    __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= p.D) return;  // warp-uniform
@@ -106,27 +109,43 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
             f[i] = choose(cnt[wib][i], k[i]);
             N *= f[i];
         }
-        for (int64_t t = lane; t < N; t += 32) {
-            int64_t rest = t;
+        // candidate t of the shape: mixed-radix digits (one per list) by
+        // division, in 32-bit arithmetic whenever the count allows
+        auto candidate = [&](auto t) {
+            using I = decltype(t);
+            I rest = t;
             uint64_t F[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) F[w] = 0;
+            uint64_t hF = 0;  // h(F) by linearity: the xor of its bits' hashes
 #pragma unroll
             for (int i = 3; i >= 0; --i) {
-                const int id = (int)(rest % f[i]);
-                rest /= f[i];
+                const I fi = (I)f[i];
+                const I qt = rest / fi;
+                const int id = (int)(rest - qt * fi);
+                rest = qt;
                 int q0 = -1, q1 = -1;
                 unrank(id, k[i], lists[wib][i], q0, q1);
-                if (q0 >= 0) set_bit<W>(F, q0);
-                if (q1 >= 0) set_bit<W>(F, q1);
+                if (q0 >= 0) {
+                    set_bit<W>(F, q0);
+                    hF ^= bh[q0];
+                }
+                if (q1 >= 0) {
+                    set_bit<W>(F, q1);
+                    hF ^= bh[q1];
+                }
             }
-            const uint64_t hF = prehash<W>(F, p.nib);
             const int64_t ge = probe<W>(F, hF, e.ght, p.err);
-            if (ge < 0) continue;
+            if (ge < 0) return;
             const int64_t g = __ldg(e.exc_gid + ge);
             const double amp = scan_amp<W>(p, g, key);
-            if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
+            if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) return;
             contribute(amp, F, hF);
+        };
+        if (N <= (int64_t)0xffffffffLL) {
+            for (uint32_t t = lane; t < (uint32_t)N; t += 32) candidate(t);
+        } else {
+            for (int64_t t = lane; t < N; t += 32) candidate(t);
         }
     }
     for (int64_t i = lane; i < e.n_rest; i += 32) {

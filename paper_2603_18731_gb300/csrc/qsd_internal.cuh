@@ -108,6 +108,7 @@ struct qsd_ctx_s {
     int tune_mode = 0;    // product path: 0 auto, 1 group scan, 2 excitation index, 3 half evaluation
     int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
     int allow_sym = 0;    // the autotuner may pick the half-evaluation product
+    int row_order = 0;    // lane-per-row scans: 0 auto, 1 index order, 2 hash order
     int autotune = 1;     // measure the product paths on first use and cache the fastest
     std::mutex tune_mu;
     std::map<std::tuple<const void *, const void *, int, int>, int> tune_cache;
@@ -119,7 +120,7 @@ struct qsd_ctx_s {
     qsd::Scratch scratch[4];
     // (operator, subspace) -> cached diagonal; dropped when either is freed
     std::map<std::pair<const void *, const void *>, qsd::Binding *> bindings;
-    // device copy of the nibble tables of the prehash (see hash_prehash)
+    // device copy of the nibble tables of the linear key hash
     qsd::DevBuf nib;
     int nib_words = 0;
     qsd::CsrState csr;
@@ -133,10 +134,15 @@ struct qsd_sub_s {
     int W = 1;
     int64_t D = 0;
     int64_t n_buckets = 0;  // power of two >= 2; capacity = 8 * n_buckets slots
-    int bucket_shift = 31;  // 32 - log2(n_buckets)
+    int bucket_shift = 63;  // 64 - log2(n_buckets)
     qsd::DevBuf keys;   // uint64 [W][D]
-    qsd::DevBuf tags;   // uint16 [8 * n_buckets], 0 = empty
+    qsd::DevBuf tags;   // uint8 [8 * n_buckets], 0 = empty
     qsd::DevBuf sidx;   // uint32 [8 * n_buckets]
+    // hash order (W <= 4): the rows in bucket order and their keys
+    qsd::DevBuf rhash;  // uint64 [D] hash h of each row (W <= 4)
+    qsd::DevBuf hperm;  // uint32 [D] row at each position
+    qsd::DevBuf hkeys;  // uint64 [W][D] keys[w][hperm[i]] at i
+    qsd::DevBuf hhash;  // uint64 [D] rhash[hperm[i]] at i
     std::vector<uint64_t> key0;  // host copy of the first (smallest) string
 };
 
@@ -199,14 +205,21 @@ struct Binding {
 };
 
 // ------------------------------------------------------------ device hash
-// Keys are hashed in two steps.  (1) A GF(2)-linear prehash h(x) = x_0 xor
-// L_1(x_1) xor ... where L_w is a random linear map of word w given by 16
-// nibble tables of 16 entries (one 128-byte line each).  Linearity gives
-// h(r xor F) = h(r) xor h(F): a row's prehash is computed once and each
-// group costs one xor.  (2) One multiplicative step (multiply-shift hashing,
-// Dietzfelbinger et al. 1997, with the golden-ratio multiplier of Fibonacci
-// hashing) on a 32-bit fold of h gives the bucket (top bits of the product)
-// and a second product gives an 8-bit tag (never 0).
+// Keys are hashed by one random GF(2)-linear map h: every word w of a key is
+// split into 16 nibbles and each nibble indexes a table of 16 random 64-bit
+// values (one 128-byte line), h(x) = xor of the W * 16 entries.  A random
+// linear map is a universal hash family (pairwise collision probability
+// 2^-m on m output bits; Carter and Wegman 1979), and its linearity gives
+// h(r xor F) = h(r) xor h(F): a row's hash is computed once and each group
+// costs one xor.  The bucket is the top log2(n_buckets) bits of h and the
+// tag its low 8 bits (0 mapped to 1).
+//
+// Because the bucket is itself linear, bucket(r xor F) = bucket(r) xor
+// bucket(F): rows taken in bucket order (the table's own slot order) send
+// the lookups of one group to buckets that stay together -- xor with a
+// constant maps an aligned run of buckets onto another aligned run -- so a
+// warp of consecutive rows probes a few cache lines instead of 32
+// (the hash-order traversal of the product).
 //
 // Table layout: buckets of 8 slots.  tags: uint8 [8 * n_buckets], 0 = empty,
 // one 8-byte load per bucket; sidx: uint32 [8 * n_buckets], the row index of
@@ -222,24 +235,22 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-// bucket in [0, 2^(32 - shift)); tag in [1, 65535].  32-bit arithmetic
-// only: the prehash is folded to 32 bits (lo xor hi * odd constant), the
-// bucket is the top bits of one multiply (multiply-shift) and the tag the top
-// 16 bits of a second, xorshifted multiply.
-__host__ __device__ __forceinline__ uint64_t hash_bucket(uint64_t h, int shift, uint32_t &tag) {
-    const uint32_t x = (uint32_t)h ^ ((uint32_t)(h >> 32) * 0x9E3779B1u);
-    const uint32_t t = ((x ^ (x >> 15)) * 0xC2B2AE3Du) >> 24;
+// bucket = top (64 - shift) bits of h, in [0, 2^(64 - shift)), with
+// 32 <= shift <= 63 (at most 2^32 buckets): a 32-bit shift of h's high word;
+// tag in [1, 255].
+__host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t h, int shift, uint32_t &tag) {
+    const uint32_t t = (uint32_t)h & 0xffu;
     tag = t ? t : 1u;
-    return (uint64_t)((x * 0x85EBCA77u) >> shift);
+    return (uint32_t)(h >> 32) >> (shift - 32);
 }
 
-// nib: tables for words 1..W-1, [(w-1)][16 nibble positions][16 values]
+// nib: [w][16 nibble positions][16 values] for words 0..W-1
 template <int W>
 __device__ __forceinline__ uint64_t prehash(const uint64_t (&x)[W], const uint64_t *__restrict__ nib) {
-    uint64_t h = x[0];
+    uint64_t h = 0;
 #pragma unroll
-    for (int w = 1; w < W; ++w) {
-        const uint64_t *t = nib + (size_t)(w - 1) * 256;
+    for (int w = 0; w < W; ++w) {
+        const uint64_t *t = nib + (size_t)w * 256;
 #pragma unroll
         for (int j = 0; j < 16; ++j) h ^= __ldg(t + j * 16 + ((x[w] >> (4 * j)) & 15));
     }
@@ -247,18 +258,23 @@ __device__ __forceinline__ uint64_t prehash(const uint64_t (&x)[W], const uint64
 }
 
 __device__ __forceinline__ uint64_t prehash_dyn(const uint64_t *x, int W, const uint64_t *__restrict__ nib) {
-    uint64_t h = x[0];
-    for (int w = 1; w < W; ++w) {
-        const uint64_t *t = nib + (size_t)(w - 1) * 256;
+    uint64_t h = 0;
+    for (int w = 0; w < W; ++w) {
+        const uint64_t *t = nib + (size_t)w * 256;
 #pragma unroll
         for (int j = 0; j < 16; ++j) h ^= __ldg(t + j * 16 + ((x[w] >> (4 * j)) & 15));
     }
     return h;
 }
 
-// Host prehash of a W-word key (same tables as the device copy).
+// h of the single bit q (the nibble entry with only that bit set).
+__device__ __forceinline__ uint64_t bit_hash(int q, const uint64_t *__restrict__ nib) {
+    return __ldg(nib + (size_t)(q >> 6) * 256 + ((q >> 2) & 15) * 16 + (1 << (q & 3)));
+}
+
+// Host hash of a W-word key (same tables as the device copy).
 uint64_t host_prehash(const uint64_t *x, int W);
-// Nibble tables for words 1..W-1 (host copy), [(W-1)*256].
+// Nibble tables for words 0..W-1 (host copy), [W*256].
 const std::vector<uint64_t> &host_nibble_tables(int W);
 void ensure_nibble_tables(qsd_ctx ctx, int W);
 
@@ -389,11 +405,13 @@ void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev);
 struct HashTable {
     DevBuf tags, sidx;
     int64_t n_buckets = 0;
-    int shift = 31;
+    int shift = 63;
 };
 // Hash table over n keys given as SoA words keys[w*n + i] (table layout of
-// the subspace index).
-HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n);
+// the subspace index); hash_out (optional, [n], W <= 4): each key's hash h.
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n, uint64_t *hash_out = nullptr);
+// The subspace's rows in bucket order (hperm, hkeys; W <= 4).
+void build_hash_order(qsd_ctx ctx, qsd_sub sub);
 void build_excitation_index(qsd_ctx ctx, qsd_op op);
 // Candidate flip masks per row of the excitation path for the subspace's
 // first string, or -1 when the operator has no excitation index.

@@ -62,14 +62,17 @@ __device__ __forceinline__ bool claim_slot(uint8_t *tags, uint32_t *sidx, uint64
 
 template <int W>
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ nib,
-                              uint8_t *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint32_t *err) {
+                              uint8_t *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint64_t *hash_out,
+                              uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     uint64_t x[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
     uint32_t tag;
-    uint64_t b = hash_bucket(prehash<W>(x, nib), shift, tag);
+    const uint64_t h = prehash<W>(x, nib);
+    if (hash_out) hash_out[i] = h;
+    uint64_t b = hash_bucket(h, shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
         if (claim_slot(tags, sidx, b, tag, (uint32_t)i)) return;
         b = (b + 1) & bucket_mask;
@@ -113,6 +116,35 @@ __global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, co
     out[i] = hv.D > 0 ? probe_dyn(c, W, prehash_dyn(c, W, nib), hv, err) : -1;
 }
 
+// Occupied slots per bucket (slots fill in order: the count is the index of
+// the first empty slot).
+__global__ void k_bucket_counts(const uint8_t *__restrict__ tags, int64_t nb, uint32_t *cnt) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint2 t = reinterpret_cast<const uint2 *>(tags)[b];
+    cnt[b] = (uint32_t)((__popc(__vcmpne4(t.x, 0u)) + __popc(__vcmpne4(t.y, 0u))) >> 3);
+}
+
+// Rows in slot order (bucket order) and their keys at those positions.
+template <int W>
+__global__ void k_hash_order(const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ start, int64_t nb,
+                             const uint8_t *__restrict__ tags, const uint64_t *__restrict__ keys,
+                             const uint64_t *__restrict__ rhash, int64_t D, uint32_t *perm, uint64_t *hkeys,
+                             uint64_t *hhash) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint2 t = reinterpret_cast<const uint2 *>(tags)[b];
+    const int n = (__popc(__vcmpne4(t.x, 0u)) + __popc(__vcmpne4(t.y, 0u))) >> 3;
+    uint32_t pos = start[b];
+    for (int i = 0; i < n; ++i, ++pos) {
+        const uint32_t row = sidx[b * kBucketSlots + i];
+        perm[pos] = row;
+        hhash[pos] = rhash[row];
+#pragma unroll
+        for (int w = 0; w < W; ++w) hkeys[(size_t)w * D + pos] = keys[(size_t)w * D + row];
+    }
+}
+
 uint64_t next_pow2(uint64_t v) {
     uint64_t p = 1;
     while (p < v) p <<= 1;
@@ -153,11 +185,13 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     sub->keys.alloc((size_t)std::max<int64_t>(D, 1) * W * 8);
     if (D > 0) unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, sub->keys.as<uint64_t>(), D);
     soa.release();
-    HashTable t = build_hash(ctx, sub->keys.as<uint64_t>(), W, D);
+    if (W <= kMaxWordsStatic) sub->rhash.alloc((size_t)std::max<int64_t>(D, 1) * 8);
+    HashTable t = build_hash(ctx, sub->keys.as<uint64_t>(), W, D, sub->rhash.as<uint64_t>());
     sub->n_buckets = t.n_buckets;
     sub->bucket_shift = t.shift;
     sub->tags = std::move(t.tags);
     sub->sidx = std::move(t.sidx);
+    if (D > 0 && W <= kMaxWordsStatic) build_hash_order(ctx, sub);
     sub->key0.assign(W, 0);
     if (D > 0)
         for (int w = 0; w < W; ++w)
@@ -166,7 +200,38 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     QSD_CUDA(cudaStreamSynchronize(s));
 }
 
-HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D) {
+// Positions of the rows in bucket order: a scan of the per-bucket counts,
+// then each bucket writes its rows (and their keys) at its offset.
+void build_hash_order(qsd_ctx ctx, qsd_sub sub) {
+    cudaStream_t s = ctx->stream;
+    const int64_t nb = sub->n_buckets, D = sub->D;
+    const int W = sub->W;
+    DevBuf start((size_t)nb * 4);
+    k_bucket_counts<<<blocks_for(nb, 256), 256, 0, s>>>(sub->tags.as<uint8_t>(), nb, start.as<uint32_t>());
+    QSD_LAUNCH_CHECK();
+    exclusive_scan_u32(ctx, start.as<uint32_t>(), start.as<uint32_t>(), nb, false);
+    sub->hperm.alloc((size_t)D * 4);
+    sub->hkeys.alloc((size_t)D * W * 8);
+    sub->hhash.alloc((size_t)D * 8);
+    const uint64_t *rh = sub->rhash.as<uint64_t>();
+    uint64_t *hh = sub->hhash.as<uint64_t>();
+    const uint32_t *si = sub->sidx.as<uint32_t>();
+    const uint8_t *tg = sub->tags.as<uint8_t>();
+    const uint64_t *keys = sub->keys.as<uint64_t>();
+    uint32_t *perm = sub->hperm.as<uint32_t>();
+    uint64_t *hk = sub->hkeys.as<uint64_t>();
+    const int g = blocks_for(nb, 256);
+    switch (W) {
+    case 1: k_hash_order<1><<<g, 256, 0, s>>>(si, start.as<uint32_t>(), nb, tg, keys, rh, D, perm, hk, hh); break;
+    case 2: k_hash_order<2><<<g, 256, 0, s>>>(si, start.as<uint32_t>(), nb, tg, keys, rh, D, perm, hk, hh); break;
+    case 3: k_hash_order<3><<<g, 256, 0, s>>>(si, start.as<uint32_t>(), nb, tg, keys, rh, D, perm, hk, hh); break;
+    default: k_hash_order<4><<<g, 256, 0, s>>>(si, start.as<uint32_t>(), nb, tg, keys, rh, D, perm, hk, hh); break;
+    }
+    QSD_LAUNCH_CHECK();
+    QSD_CUDA(cudaStreamSynchronize(s));  // start is freed on return
+}
+
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D, uint64_t *hash_out) {
     cudaStream_t s = ctx->stream;
     HashTable t;
     // load factor <= 1/4 over buckets of 8 slots: a bucket overflows into the
@@ -175,7 +240,7 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D) {
     int lg = 0;
     while ((1ll << lg) < t.n_buckets) ++lg;
     if (lg > 32) fail(QSD_ERR_CAPACITY, "hash table larger than 2^32 buckets");
-    t.shift = 32 - lg;
+    t.shift = 64 - lg;
     const size_t cap = (size_t)t.n_buckets * kBucketSlots;
     t.tags.alloc(cap);
     t.sidx.alloc(cap * 4);
@@ -189,10 +254,10 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D) {
         const int nb = blocks_for(D, 256);
         const int shift = t.shift;
         switch (W) {
-        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
-        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, ctx->d_err); break;
+        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
+        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
+        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
+        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
         default: k_hash_insert_dyn<<<nb, 256, 0, s>>>(keys, W, D, nib, tg, si, mask, shift, ctx->d_err);
         }
         QSD_LAUNCH_CHECK();

@@ -247,18 +247,21 @@ def test_autotuned_product_matches_oracle(ctx, kind, k):
     tuned = ctx.product_path(h, sub, k=k)
     y2 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))  # cached choice
     ctx.synchronize()
-    assert guess in (0, 1, 2) and tuned in (0, 1, 2)
+    assert guess in (0, 1, 2) and tuned in (0, 1, 2, 5)
     for y in (y0, y1, y2):
         assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
     assert torch.equal(y1, y2)
-    ctx.set_tuning(1, 1 if tuned < 2 else 2)
-    if tuned < 2:
+    ctx.set_tuning(1, 2 if tuned == 2 else 1)
+    if tuned != 2:
         ctx.set_tuning(2, 8 if tuned == 1 else 1)
+        ctx.set_tuning(5, 2 if tuned == 5 else 1)
+    assert ctx.product_path(h, sub, k=k) == tuned
     y3 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
     ctx.synchronize()
     assert torch.equal(y2, y3)  # the cached path is the forced one, bit for bit
     ctx.set_tuning(1, 0)
     ctx.set_tuning(2, 0)
+    ctx.set_tuning(5, 0)
 
 
 @pytest.mark.parametrize("n,T,wmax,count,k,lanes", [(12, 60, 4, 3000, 1, 1), (40, 80, 5, 4000, 4, 8),
@@ -301,7 +304,7 @@ def test_half_evaluation_models_and_tuner(ctx):
         ctx.set_tuning(4, 1)  # the tuner may pick the half evaluation
         y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
         ctx.synchronize()
-        assert ctx.product_path(h, sub) in (0, 1, 3, 4)
+        assert ctx.product_path(h, sub) in (0, 1, 3, 4, 5, 6)
         assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
         ctx.set_tuning(1, 3)
         y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
@@ -433,3 +436,115 @@ def test_lanczos_hubbard_dimer_closed_form(ctx):
     sub = ctx.build_subspace(4, wl.product_subspace([1, 2], [1, 2], 2))
     e, _ = ctx.lanczos_ground_state(h, sub, max_steps=10, tol=1e-12)
     assert abs(e - (U - math.sqrt(U * U + 16 * t * t)) / 2) < 1e-11
+
+
+# ------------------------------------------------------------ hash order
+def _hash_order_cases():
+    h1, eri = wl.chem_integrals(6, seed=9)
+    strings = [v for v in range(1 << 6) if bin(v).count("1") == 3]
+    return [
+        ("xxz", wl.xxz_square(4, 4, 1.0, 0.5), wl.xxz_walk_subspace(4, 4, 3000, seed=5)),
+        ("ising200", wl.ising_heavy_hex(200, seed=6), wl.flip_subspace(200, 6000, max_flips=3, seed=6)),
+        ("tfim", wl.tfim_chain(12), wl.full_space(12)),
+        ("rand70", wl.random_extended(70, 60, max_weight=5, seed=7), wl.random_subspace(70, 3000, seed=7)),
+        ("rand140", wl.random_extended(140, 50, max_weight=6, seed=8), wl.random_subspace(140, 2500, seed=8)),
+        ("chem", wl.molecular_qubit_operator(h1, eri), wl.product_subspace(strings, strings, 6)),
+    ]
+
+
+@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("k", [1, 4, 16, 21])
+def test_hash_order_is_bitwise_index_order(ctx, case, k):
+    """Rows taken in bucket order give, row for row, the same bits as rows
+    taken by index (same groups in the same order), in every precision; and
+    the FP64 result matches the oracle."""
+    import torch
+    import paper_2603_18731_gb300 as q
+    name, op, words = _hash_order_cases()[case]
+    keys = oracle.sort_unique(words)
+    if name.startswith("rand"):
+        words = np.concatenate([words] + [keys[:100] ^ f for f in oracle.groups(op)[:30]])
+        keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(op.n_qubits, words)
+    rng = np.random.default_rng(k + case)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    ctx.set_tuning(1, 1)
+    ctx.set_tuning(2, 1)
+    try:
+        for prec, dt in ((q.QSD_FP64, torch.float64), (q.QSD_FP32_MIXED, torch.float32),
+                         (q.QSD_FP32_DOT2, torch.float32)):
+            xd = to_cuda(ctx, x, dt)
+            out = {}
+            for order in (1, 2):
+                ctx.set_tuning(5, order)
+                assert ctx.product_path(h, sub, precision=prec, k=k) == (5 if order == 2 else 0)
+                out[order] = ctx.apply_H(h, sub, xd, precision=prec)
+            ctx.synchronize()
+            assert torch.equal(out[1], out[2]), (name, prec)
+            if prec == q.QSD_FP64:
+                assert rel_err(out[2].cpu().numpy(), oracle.apply(op, keys, x).real) <= FP64_TOL
+    finally:
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(2, 0)
+        ctx.set_tuning(5, 0)
+
+
+@pytest.mark.parametrize("case", [0, 1, 3, 4])
+@pytest.mark.parametrize("k", [1, 16])
+def test_hash_order_half_evaluation(ctx, case, k):
+    import torch
+    import paper_2603_18731_gb300 as q
+    name, op, words = _hash_order_cases()[case]
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(op.n_qubits, words)
+    rng = np.random.default_rng(k)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    ctx.set_tuning(1, 3)
+    ctx.set_tuning(2, 1)
+    ctx.set_tuning(5, 2)
+    try:
+        assert ctx.product_path(h, sub, k=k) == 6
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        assert rel_err(y.cpu().numpy(), oracle.apply(op, keys, x).real) <= FP64_TOL
+    finally:
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(2, 0)
+        ctx.set_tuning(5, 0)
+
+
+def test_hash_order_tuner_and_forced_fallbacks(ctx):
+    import torch
+    import paper_2603_18731_gb300 as q
+    op = wl.ising_heavy_hex(60, seed=4)
+    words = wl.flip_subspace(60, 20000, max_flips=3, seed=4)
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(60, words)
+    x = np.random.default_rng(3).normal(size=sub.dim)
+    ref = oracle.apply(op, keys, x).real
+    try:
+        ctx.set_tuning(5, 0)
+        y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+        ctx.synchronize()
+        assert ctx.product_path(h, sub) in (0, 1, 5)
+        assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
+        # forced hash order keeps 8 lanes per row in index order
+        ctx.set_tuning(1, 1)
+        ctx.set_tuning(2, 8)
+        ctx.set_tuning(5, 2)
+        assert ctx.product_path(h, sub) == 1
+        # more than 256 qubits: no hash order, the run-time-W scan
+        big = wl.random_extended(300, 20, max_weight=3, seed=2)
+        hb = ctx.load_operator(big)
+        sb = ctx.build_subspace(300, wl.random_subspace(300, 500, seed=2))
+        ctx.set_tuning(2, 1)
+        assert ctx.product_path(hb, sb) == 0
+        with pytest.raises(q.QsdError):
+            ctx.set_tuning(5, 3)
+    finally:
+        ctx.set_tuning(1, 0)
+        ctx.set_tuning(2, 0)
+        ctx.set_tuning(5, 0)
