@@ -92,6 +92,8 @@ typedef struct {
     int64_t n_ladder_groups;  /* groups that use the ladder-integer table */
     int64_t n_excitation_groups; /* ladder groups in the excitation index (0: none) */
     int32_t n_excitation_shapes; /* distinct occupied/empty shapes of their terms */
+    int32_t excitation_rank_index; /* 1: the index finds a flip mask's group by its
+                                      rank (one load); 0: through a hash table */
     int64_t max_group_terms;
     int32_t is_real;          /* every matrix element is real */
     int32_t is_hermitian;     /* term set closed under adjoint (rel. 1e-14) */

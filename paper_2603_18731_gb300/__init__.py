@@ -39,7 +39,8 @@ class OpInfo(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_words", C.c_int32), ("n_terms_in", C.c_int64),
                 ("n_terms", C.c_int64), ("n_diag_terms", C.c_int64), ("n_groups", C.c_int64),
                 ("n_ladder_groups", C.c_int64), ("n_excitation_groups", C.c_int64),
-                ("n_excitation_shapes", C.c_int32), ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
+                ("n_excitation_shapes", C.c_int32), ("excitation_rank_index", C.c_int32),
+                ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
                 ("is_hermitian", C.c_int32), ("identity_coef", C.c_double)]
 
 

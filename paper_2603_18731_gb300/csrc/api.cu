@@ -214,6 +214,11 @@ ExcParams make_exc(qsd_op op) {
     e.ght = HashView{op->gtags.as<uint8_t>(), op->gsidx.as<uint32_t>(), op->excF.as<uint64_t>(), op->G_exc,
                      (uint64_t)op->g_nbuckets - 1, op->g_shift};
     e.exc_gid = op->exc_gid.as<int32_t>();
+    e.dense = op->dense_ok ? op->dense.as<int32_t>() : nullptr;
+    for (int i = 0; i < op->n_shapes; ++i) {
+        e.dbase[i] = op->dbase[i];
+        e.dstride[i] = op->dstride[i];
+    }
     e.rest_gid = op->rest_gid.as<int32_t>();
     e.n_rest = op->G_rest;
     e.split = op->exc_split;

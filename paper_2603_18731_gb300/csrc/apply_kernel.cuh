@@ -299,8 +299,17 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             c[0] = key[0] ^ __ldg(p.gF + g);
 #pragma unroll
             for (int w = 1; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
-            int64_t idx = verify_matches<W>(p.hv, bidx[u], match, c);
-            if (idx < 0 && full) idx = probe_from<W>(p.hv, bidx[u], tag[u], c, p.err);
+            // k = 1 and multi-word keys: x of the candidate row is loaded with
+            // its key words (one-word keys at their 32-register budget spill
+            // more than the shorter chain saves: measured)
+            constexpr bool XSPEC = KB == 1 && W > 1;
+            TIO xv = TIO(0);
+            int64_t idx = XSPEC ? verify_matches_x<W, TIO>(p.hv, bidx[u], match, c, x + p.col0, p.ld, xv)
+                                : verify_matches<W>(p.hv, bidx[u], match, c);
+            if (idx < 0 && full) {
+                idx = probe_from<W>(p.hv, bidx[u], tag[u], c, p.err);
+                if (XSPEC && idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
+            }
             if (idx < 0) continue;
             if (KB > 1 && aidx[u] != kNoTable) {
                 if (PREC == QSD_FP32_DOT2) {
@@ -314,10 +323,10 @@ __device__ __forceinline__ void apply_row(const ApplyParams &p, const int64_t ro
             const TIO *xc = x + idx * p.ld + p.col0;
             if (PREC == QSD_FP32_DOT2) {
 #pragma unroll
-                for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], ah[u], al[u], (float)__ldg(xc + j));
+                for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], ah[u], al[u], (float)(XSPEC ? xv : __ldg(xc + j)));
             } else {
 #pragma unroll
-                for (int j = 0; j < KB; ++j) acc[j] = fma(a[u], (double)__ldg(xc + j), acc[j]);
+                for (int j = 0; j < KB; ++j) acc[j] = fma(a[u], (double)(XSPEC ? xv : __ldg(xc + j)), acc[j]);
                 if (SYM) {
                     double *yc = static_cast<double *>(p.y) + idx * p.ld + p.col0;
 #pragma unroll

@@ -8,6 +8,7 @@
 // that form -- its single and double "excitations" per shape of the operator --
 // and finds their groups in a hash table keyed by the flip mask.
 #include <algorithm>
+#include <map>
 #include <set>
 
 #include "excite.cuh"
@@ -52,6 +53,66 @@ __global__ void k_gather_exc(int W, int64_t G, const int32_t *__restrict__ ids, 
 }
 
 int64_t choose_h(int64_t m, int k) { return k == 0 ? 1 : (k == 1 ? m : m * (m - 1) / 2); }
+
+uint64_t binom_h(uint64_t n, int k) {
+    if ((uint64_t)k > n) return 0;
+    uint64_t c = 1;
+    for (int i = 0; i < k; ++i) c = c * (n - (uint64_t)i) / (uint64_t)(i + 1);
+    return c;
+}
+
+// Dense rank index: a group's flip mask F has b0 bits in sector 0 and b1 in
+// sector 1 (at most 4 each, from at most two raised and two lowered qubits
+// per sector); its entry is base(b0, b1) + rank0 * C(n1, b1) + rank1 with
+// rank_s = sum_j C(pos_j, j + 1) over the ascending positions of F's bits
+// within sector s (the combinatorial number system: a bijection between the
+// b-subsets of n positions and [0, C(n, b))).  Built only when all
+// signatures together stay within 2^24 entries; a row's candidate then finds
+// its group with one load.
+void build_dense_index(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc) {
+    op->dense_ok = false;
+    const int W = op->W, split = op->exc_split;
+    const int n0 = split, n1 = op->n_qubits - split;
+    std::map<std::pair<int, int>, uint64_t> base;
+    uint64_t total = 0;
+    for (int i = 0; i < op->n_shapes; ++i) {
+        const uint32_t sh = op->shapes[i];
+        const int b0 = (int)(sh & 15) + (int)((sh >> 4) & 15), b1 = (int)((sh >> 8) & 15) + (int)((sh >> 12) & 15);
+        if (base.count({b0, b1})) continue;
+        base[{b0, b1}] = total;
+        total += binom_h((uint64_t)n0, b0) * binom_h((uint64_t)n1, b1);
+        if (total > (1ull << 24)) return;
+    }
+    const int64_t n = op->G_exc;
+    std::vector<uint64_t> F((size_t)W * n);
+    QSD_CUDA(cudaMemcpyAsync(F.data(), op->excF.p, F.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> table(std::max<uint64_t>(total, 1), -1);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t rank[2] = {0, 0};
+        int b[2] = {0, 0};
+        for (int q = 0; q < op->n_qubits; ++q) {
+            if (!((F[(size_t)(q >> 6) * n + i] >> (q & 63)) & 1)) continue;
+            const int sct = q < split ? 0 : 1;
+            const int pos = q - (sct ? split : 0);
+            ++b[sct];
+            rank[sct] += binom_h((uint64_t)pos, b[sct]);
+        }
+        auto it = base.find({b[0], b[1]});
+        if (it == base.end()) return;  // not reachable from any shape: keep the hash table
+        table[it->second + rank[0] * binom_h((uint64_t)n1, b[1]) + rank[1]] = exc[(size_t)i];
+    }
+    for (int i = 0; i < op->n_shapes; ++i) {
+        const uint32_t sh = op->shapes[i];
+        const int b0 = (int)(sh & 15) + (int)((sh >> 4) & 15), b1 = (int)((sh >> 8) & 15) + (int)((sh >> 12) & 15);
+        op->dbase[i] = (uint32_t)base[{b0, b1}];
+        op->dstride[i] = (uint32_t)binom_h((uint64_t)n1, b1);
+    }
+    op->dense.alloc(table.size() * 4);
+    QSD_CUDA(cudaMemcpyAsync(op->dense.p, table.data(), table.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    QSD_CUDA(cudaStreamSynchronize(ctx->stream));
+    op->dense_ok = true;
+}
 
 }  // namespace
 
@@ -104,6 +165,7 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op) {
     op->g_nbuckets = t.n_buckets;
     op->g_shift = t.shift;
     QSD_CUDA(cudaStreamSynchronize(s));
+    build_dense_index(ctx, op, exc);
     op->exc_ok = true;
 }
 

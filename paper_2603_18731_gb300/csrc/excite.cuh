@@ -15,6 +15,8 @@ constexpr int kMaxShapes = 16;
 struct ExcParams {
     HashView ght;             // flip mask -> excitation-group index
     const int32_t *exc_gid;   // [G_exc] group index of each excitation group
+    const int32_t *dense;     // rank index (nullptr: use ght): entry -> group or -1
+    uint32_t dbase[kMaxShapes], dstride[kMaxShapes];  // per shape: signature base, C(n1, b1)
     const int32_t *rest_gid;  // [G_rest] groups evaluated by the per-row scan
     int64_t n_rest;
     int split;

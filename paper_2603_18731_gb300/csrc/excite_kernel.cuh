@@ -33,6 +33,25 @@ __device__ __forceinline__ void unrank(int i, int k, const uint8_t *list, int &q
     }
 }
 
+// Rank of a set of at most four positions (two picks of each of two lists,
+// -1 = none) in the combinatorial number system: sum over its elements x of
+// C(x, j) with j the element's 1-based place in ascending order (as unsigned,
+// -1 is never below an element).
+template <int W>
+__device__ __forceinline__ uint32_t sector_rank(int a0, int a1, int b0, int b1, const uint32_t (*binom)[64 * W]) {
+    const int v[4] = {a0, a1, b0, b1};
+    uint32_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (v[i] < 0) continue;
+        int j = 1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) j += (m != i && (unsigned)v[m] < (unsigned)v[i]) ? 1 : 0;
+        r += binom[j][v[i]];
+    }
+    return r;
+}
+
 template <int W>
 __device__ __forceinline__ void set_bit(uint64_t (&F)[W], int q) {
 #pragma unroll
@@ -46,7 +65,16 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
     __shared__ uint8_t lists[8][4][64 * W];
     __shared__ int cnt[8][4];
     __shared__ uint64_t bh[64 * W];  // h of each single qubit (the hash is linear)
+    __shared__ uint32_t binom[5][64 * W];  // C(x, j) for the rank index
     for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) bh[q] = bit_hash(q, p.nib);
+    if (e.dense) {
+        for (int i = threadIdx.x; i < 5 * 64 * W; i += blockDim.x) {
+            const int j = i / (64 * W), x = i % (64 * W);
+            uint64_t c = 1;
+            for (int t = 0; t < j; ++t) c = c * (uint64_t)(x - t) / (uint64_t)(t + 1);
+            binom[j][x] = x >= j ? (uint32_t)c : 0u;
+        }
+    }
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -118,6 +146,7 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
 #pragma unroll
             for (int w = 0; w < W; ++w) F[w] = 0;
             uint64_t hF = 0;  // h(F) by linearity: the xor of its bits' hashes
+            int qs[4][2];     // the picks of each list (-1: none), positions within the sector
 #pragma unroll
             for (int i = 3; i >= 0; --i) {
                 const I fi = (I)f[i];
@@ -126,6 +155,9 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
                 rest = qt;
                 int q0 = -1, q1 = -1;
                 unrank(id, k[i], lists[wib][i], q0, q1);
+                const int off = i >= 2 ? e.split : 0;
+                qs[i][0] = q0 >= 0 ? q0 - off : -1;
+                qs[i][1] = q1 >= 0 ? q1 - off : -1;
                 if (q0 >= 0) {
                     set_bit<W>(F, q0);
                     hF ^= bh[q0];
@@ -135,9 +167,17 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
                     hF ^= bh[q1];
                 }
             }
-            const int64_t ge = probe<W>(F, hF, e.ght, p.err);
-            if (ge < 0) return;
-            const int64_t g = __ldg(e.exc_gid + ge);
+            int64_t g;
+            if (e.dense) {
+                const uint32_t r0 = sector_rank<W>(qs[0][0], qs[0][1], qs[1][0], qs[1][1], binom);
+                const uint32_t r1 = sector_rank<W>(qs[2][0], qs[2][1], qs[3][0], qs[3][1], binom);
+                g = __ldg(e.dense + e.dbase[si] + r0 * e.dstride[si] + r1);
+                if (g < 0) return;
+            } else {
+                const int64_t ge = probe<W>(F, hF, e.ght, p.err);
+                if (ge < 0) return;
+                g = __ldg(e.exc_gid + ge);
+            }
             const double amp = scan_amp<W>(p, g, key);
             if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) return;
             contribute(amp, F, hF);

@@ -174,8 +174,15 @@ struct qsd_op_s {
     qsd::DevBuf exc_gid;   // int32 [G_exc]
     qsd::DevBuf rest_gid;  // int32 [G_rest]
     qsd::DevBuf gtags, gsidx;
+    // dense rank index of the excitation groups (when it fits): per sector
+    // bit-count signature (b0, b1), entry base + rank0 * C(n1, b1) + rank1
+    // holds the group of that flip mask or -1 (ranks in the combinatorial
+    // number system of the bits' positions within their sector)
+    bool dense_ok = false;
+    qsd::DevBuf dense;     // int32 [dense entries]
+    uint32_t dbase[16] = {0}, dstride[16] = {0};  // per shape
     int64_t g_nbuckets = 0;
-    int g_shift = 31;
+    int g_shift = 63;
     qsd::DevBuf tP, tV, tZ;  // uint64 [W][T]
     qsd::DevBuf tphi;    // double [T] real phase * coefficient
     qsd::DevBuf tphi_im; // double [T]
@@ -287,15 +294,17 @@ __device__ __forceinline__ uint2 load_tags(const uint8_t *__restrict__ tags, uin
 // Delight, section 6-1; exact as an existence test).
 __device__ __forceinline__ uint32_t zero_byte(uint32_t v) { return (v - 0x01010101u) & ~v & 0x80808080u; }
 
-// Bit i set when tag i of the bucket equals `tag` (exact per slot).
+// Bit 7 of each byte of v, packed into bits 0..3: with x = v >> 7 (bits at
+// 0, 8, 16, 24), x * 0x01020408 moves bit 8i to 24 + i and every cross term
+// to a distinct position below 24 (3, 10, 11, 17, 18, 19), so no carry
+// reaches bits 24..27.
+__device__ __forceinline__ uint32_t pack_byte_msbs(uint32_t v) { return (((v >> 7) * 0x01020408u) >> 24) & 0xfu; }
+
+// Bit i set when tag i of the bucket equals `tag` (exact per slot: a byte-wise
+// compare, then one bit per byte).
 __device__ __forceinline__ uint32_t tag_match(const uint2 t, uint32_t tag) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        m |= ((((t.x >> (8 * i)) & 0xffu) == tag) ? 1u : 0u) << i;
-        m |= ((((t.y >> (8 * i)) & 0xffu) == tag) ? 1u : 0u) << (i + 4);
-    }
-    return m;
+    const uint32_t tt = tag * 0x01010101u;
+    return pack_byte_msbs(__vcmpeq4(t.x, tt) & 0x80808080u) | (pack_byte_msbs(__vcmpeq4(t.y, tt) & 0x80808080u) << 4);
 }
 
 // Some tag of the bucket equals `tag`.
@@ -328,6 +337,30 @@ __device__ __forceinline__ int64_t verify_matches(const HashView &hv, uint64_t b
 #pragma unroll
         for (int w = 0; w < W; ++w) eq &= (__ldg(hv.keys + (size_t)w * hv.D + cand) == c[w]);
         if (eq) return (int64_t)cand;
+    }
+    return -1;
+}
+
+// verify_matches for a one-column product: x[cand] is loaded beside the
+// candidate's key words (both depend only on the candidate row), so a hit
+// costs one dependent load after the slot's row index instead of two; xv
+// receives x of the verified row.
+template <int W, typename TX>
+__device__ __forceinline__ int64_t verify_matches_x(const HashView &hv, uint64_t b, uint32_t match,
+                                                    const uint64_t (&c)[W], const TX *__restrict__ x0, int64_t ld,
+                                                    TX &xv) {
+    while (match) {
+        const int i = __ffs(match) - 1;
+        match &= match - 1;
+        const uint64_t cand = __ldg(hv.sidx + b * kBucketSlots + i);
+        const TX xs = __ldg(x0 + cand * ld);
+        bool eq = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) eq &= (__ldg(hv.keys + (size_t)w * hv.D + cand) == c[w]);
+        if (eq) {
+            xv = xs;
+            return (int64_t)cand;
+        }
     }
     return -1;
 }

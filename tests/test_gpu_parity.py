@@ -200,6 +200,51 @@ def test_excitation_path_matches_scan_and_oracle(ctx, n_orb, na, k):
     assert rel_err(outs[1], outs[2]) <= FP64_TOL
 
 
+def test_excitation_rank_index_and_hash_fallback(ctx):
+    """Molecular operators find a candidate flip mask's group by its rank (one
+    load); an operator whose rank table would be too large (cross-sector
+    doubles on 2 x 120 qubits: C(120, 2)^2 > 2^24 entries) keeps the hash
+    table.  Both match the oracle."""
+    import torch
+    h1, eri = wl.chem_integrals(6, seed=6)
+    assert ctx.load_operator(wl.molecular_qubit_operator(h1, eri)).info()["excitation_rank_index"] == 1
+    n = 240
+    rng = np.random.default_rng(12)
+    terms = []
+    for _ in range(30):
+        a, b = (int(v) for v in rng.choice(120, 2, replace=False))
+        c, d = (120 + int(v) for v in rng.choice(120, 2, replace=False))
+        coef = float(rng.normal())
+        terms.append((coef, [(a, "+"), (b, "-"), (c, "+"), (d, "-")]))
+        terms.append((coef, [(a, "-"), (b, "+"), (c, "-"), (d, "+")]))
+    for _ in range(20):
+        off = 120 * int(rng.integers(0, 2))
+        a, b = (off + int(v) for v in rng.choice(120, 2, replace=False))
+        coef = float(rng.normal())
+        terms.append((coef, [(a, "+"), (b, "-")]))
+        terms.append((coef, [(a, "-"), (b, "+")]))
+    terms.append((0.7, [(3, "Z"), (130, "Z")]))
+    op = wl.QubitOperator.from_terms(n, terms)
+    words = wl.random_subspace(n, 2000, seed=13)
+    keys0 = oracle.sort_unique(words)
+    words = np.concatenate([words] + [keys0[:200] ^ f for f in oracle.groups(op)])
+    keys = oracle.sort_unique(words)
+    h = ctx.load_operator(op)
+    info = h.info()
+    assert info["n_excitation_groups"] > 0 and info["excitation_rank_index"] == 0
+    sub = ctx.build_subspace(n, words)
+    x = np.random.default_rng(14).normal(size=(sub.dim, 4))
+    ref = oracle.apply(op, keys, x).real
+    try:
+        for path in (1, 2):
+            ctx.set_tuning(1, path)
+            y = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))
+            ctx.synchronize()
+            assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL, path
+    finally:
+        ctx.set_tuning(1, 0)
+
+
 def test_excitation_path_with_rest_groups(ctx):
     import torch
     n = 10
