@@ -70,7 +70,7 @@ std::vector<uint64_t> g_nib;  // [W*256]
 int g_nib_words = 0;
 }  // namespace
 
-const std::vector<uint64_t> &host_nibble_tables(int W) {
+std::vector<uint64_t> host_nibble_tables(int W) {
     std::lock_guard<std::mutex> lk(g_nib_mu);
     if (W > g_nib_words) {
         // random GF(2) columns Q[q] for qubits 0..64W-1, fixed seed (the
@@ -89,21 +89,14 @@ const std::vector<uint64_t> &host_nibble_tables(int W) {
                 }
         g_nib_words = W;
     }
-    return g_nib;
-}
-
-uint64_t host_prehash(const uint64_t *x, int W) {
-    const auto &t = host_nibble_tables(W);
-    uint64_t h = 0;
-    for (int w = 0; w < W; ++w)
-        for (int j = 0; j < 16; ++j) h ^= t[(size_t)w * 256 + j * 16 + ((x[w] >> (4 * j)) & 15)];
-    return h;
+    // a copy taken under the lock: another thread may grow the tables
+    return std::vector<uint64_t>(g_nib.begin(), g_nib.begin() + (size_t)W * 256);
 }
 
 void ensure_nibble_tables(qsd_ctx ctx, int W) {
     const int want = std::max(W, 8);
     if (ctx->nib_words >= want) return;
-    const auto &t = host_nibble_tables(want);
+    const std::vector<uint64_t> t = host_nibble_tables(want);
     QSD_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->nib.alloc(t.size() * 8);
     QSD_CUDA(cudaMemcpy(ctx->nib.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice));

@@ -279,10 +279,8 @@ __device__ __forceinline__ uint64_t bit_hash(int q, const uint64_t *__restrict__
     return __ldg(nib + (size_t)(q >> 6) * 256 + ((q >> 2) & 15) * 16 + (1 << (q & 3)));
 }
 
-// Host hash of a W-word key (same tables as the device copy).
-uint64_t host_prehash(const uint64_t *x, int W);
 // Nibble tables for words 0..W-1 (host copy), [W*256].
-const std::vector<uint64_t> &host_nibble_tables(int W);
+std::vector<uint64_t> host_nibble_tables(int W);
 void ensure_nibble_tables(qsd_ctx ctx, int W);
 
 // The 8 one-byte tags of bucket b (slot i in byte i of the 8-byte word).
