@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_apply_complex(const CplxParams p, int c
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
-    const uint64_t hr = prehash<W>(key, p.nib);
+    const uint64_t hr = key_hash<W>(key, p.nib);
     double2 acc[KB];
 #pragma unroll
     for (int j = 0; j < KB; ++j) acc[j] = make_double2(0.0, 0.0);

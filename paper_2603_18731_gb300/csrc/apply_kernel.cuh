@@ -47,7 +47,7 @@ template <int W, int KB> struct ApplyShape {
 
 // 32-byte group record, one per off-diagonal group
 struct __align__(16) GroupRec {
-    uint64_t hF;    // prehash of the flip mask F
+    uint64_t hF;    // hash h of the flip mask F
     uint64_t pos;   // table groups: support qubits, 12 bits each, ascending
     uint32_t off;   // table groups: offset of the 2^nb amplitudes
     uint32_t info;  // bits 0..2: nb; kGroupScan: scan group; bits 16..27: MSOB
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256) k_apply_dyn(const ApplyParams p, int W) {
     if (row >= p.D) return;
     uint64_t key[kMaxWordsDyn], c[kMaxWordsDyn];
     for (int w = 0; w < W; ++w) key[w] = p.keys[(size_t)w * p.D + row];
-    const uint64_t hr = prehash_dyn(key, W, p.nib);
+    const uint64_t hr = key_hash_dyn(key, W, p.nib);
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
     double acc[KB];
 #pragma unroll

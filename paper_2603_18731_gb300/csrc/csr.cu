@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_csr_rows(const CsrParams c) {
 #pragma unroll
     for (int w = 0; w < NW; ++w)
         if (w < nw) key[w] = __ldg(c.keys + (size_t)w * c.D + row);
-    const uint64_t hr = prehash_dyn(key, nw, c.nib);
+    const uint64_t hr = key_hash_dyn(key, nw, c.nib);
     IDX *ind = static_cast<IDX *>(c.indices);
     uint32_t n = 0;
     const uint32_t lim = FILL ? c.cnt[row] : 0u;

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_apply_exc(const ApplyParams p, const Ex
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
-    const uint64_t hr = prehash<W>(key, p.nib);
+    const uint64_t hr = key_hash<W>(key, p.nib);
     // occupied / empty lists per sector
     for (int sct = 0; sct < 2; ++sct) {
         const int lo = sct ? e.split : 0, hi = sct ? e.n_qubits : e.split;

@@ -100,7 +100,7 @@ __global__ void k_group_tables(int W, int64_t G, const int32_t *__restrict__ gra
         gF[(size_t)w * G + g] = F[w];
         L += __popcll(F[w]);
     }
-    ghash[g] = prehash_dyn(F, W, nib);
+    ghash[g] = key_hash_dyn(F, W, nib);
     atomicMax(max_terms, (unsigned long long)(e - b));
     // flipped-qubit positions, ascending (first four)
     uint64_t pos = 0;
@@ -392,7 +392,7 @@ __global__ void k_target_table(const uint64_t *__restrict__ keys, int64_t D, con
     uint64_t c[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = x[w] ^ gF[(size_t)w * G + g];
-    uint64_t hr = prehash<W>(x, nib);
+    uint64_t hr = key_hash<W>(x, nib);
     out[idx] = probe<W>(c, hr ^ ghash[g], hv, err);
 }
 
@@ -414,7 +414,7 @@ __global__ void k_target_table_dyn(const uint64_t *__restrict__ keys, int W, int
     }
     if (!any) { out[idx] = -2; return; }
     for (int w = 0; w < W; ++w) c[w] = x[w] ^ gF[(size_t)w * G + g];
-    out[idx] = probe_dyn(c, W, prehash_dyn(x, W, nib) ^ ghash[g], hv, err);
+    out[idx] = probe_dyn(c, W, key_hash_dyn(x, W, nib) ^ ghash[g], hv, err);
 }
 
 struct HostWord {

@@ -156,7 +156,7 @@ struct qsd_op_s {
     // off-diagonal groups (G) and terms (T), group order
     int64_t G = 0, T = 0;
     qsd::DevBuf gF;      // uint64 [W][G]
-    qsd::DevBuf ghash;   // uint64 [G]  prehash of F
+    qsd::DevBuf ghash;   // uint64 [G]  hash h of F
     qsd::DevBuf grange;  // int32  [G+1] term offsets
     qsd::DevBuf gL;      // uint8  [G]  ladder bits with a table (0: scan the group)
     qsd::DevBuf gpos;    // uint64 [G]  4 x 16-bit flipped-qubit positions, ascending
@@ -253,7 +253,7 @@ __host__ __device__ __forceinline__ uint32_t hash_bucket(uint64_t h, int shift, 
 
 // nib: [w][16 nibble positions][16 values] for words 0..W-1
 template <int W>
-__device__ __forceinline__ uint64_t prehash(const uint64_t (&x)[W], const uint64_t *__restrict__ nib) {
+__device__ __forceinline__ uint64_t key_hash(const uint64_t (&x)[W], const uint64_t *__restrict__ nib) {
     uint64_t h = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -264,7 +264,7 @@ __device__ __forceinline__ uint64_t prehash(const uint64_t (&x)[W], const uint64
     return h;
 }
 
-__device__ __forceinline__ uint64_t prehash_dyn(const uint64_t *x, int W, const uint64_t *__restrict__ nib) {
+__device__ __forceinline__ uint64_t key_hash_dyn(const uint64_t *x, int W, const uint64_t *__restrict__ nib) {
     uint64_t h = 0;
     for (int w = 0; w < W; ++w) {
         const uint64_t *t = nib + (size_t)w * 256;
@@ -377,7 +377,7 @@ __device__ int64_t probe_from(const HashView &hv, uint64_t b, uint32_t tag, cons
     return -1;
 }
 
-// Lookup of column key c (W words, prehash hc); returns the row index or -1.
+// Lookup of column key c (W words, key_hash hc); returns the row index or -1.
 // At most n_buckets buckets are visited (a full table yields -1, sets *err).
 template <int W>
 __device__ __forceinline__ int64_t probe(const uint64_t (&c)[W], uint64_t hc, const HashView &hv, uint32_t *err) {

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_ramps_expand(const RampsParams p) {
     if (!pass) return;
 #pragma unroll
     for (int w = 0; w < W; ++w) col[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
-    const uint64_t hk = prehash<W>(col, p.nib);
+    const uint64_t hk = key_hash<W>(col, p.nib);
     if (probe<W>(col, hk, p.out, p.err) >= 0) return;  // already in the output
     if (p.allowed.tags && probe<W>(col, hk, p.allowed, p.err) < 0) return;
     double hkk = p.identity;

@@ -70,7 +70,7 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, cons
 #pragma unroll
     for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
     uint32_t tag;
-    const uint64_t h = prehash<W>(x, nib);
+    const uint64_t h = key_hash<W>(x, nib);
     if (hash_out) hash_out[i] = h;
     uint64_t b = hash_bucket(h, shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
@@ -88,7 +88,7 @@ __global__ void k_hash_insert_dyn(const uint64_t *__restrict__ keys, int W, int6
     uint64_t x[kMaxWordsDyn];
     for (int w = 0; w < W; ++w) x[w] = keys[(size_t)w * D + i];
     uint32_t tag;
-    uint64_t b = hash_bucket(prehash_dyn(x, W, nib), shift, tag);
+    uint64_t b = hash_bucket(key_hash_dyn(x, W, nib), shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
         if (claim_slot(tags, sidx, b, tag, (uint32_t)i)) return;
         b = (b + 1) & bucket_mask;
@@ -104,7 +104,7 @@ __global__ void k_index(const uint64_t *__restrict__ q, int64_t n, const HashVie
     uint64_t c[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
-    out[i] = hv.D > 0 ? probe<W>(c, prehash<W>(c, nib), hv, err) : -1;
+    out[i] = hv.D > 0 ? probe<W>(c, key_hash<W>(c, nib), hv, err) : -1;
 }
 
 __global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, const HashView hv,
@@ -113,7 +113,7 @@ __global__ void k_index_dyn(const uint64_t *__restrict__ q, int W, int64_t n, co
     if (i >= n) return;
     uint64_t c[kMaxWordsDyn];
     for (int w = 0; w < W; ++w) c[w] = q[(size_t)i * W + w];
-    out[i] = hv.D > 0 ? probe_dyn(c, W, prehash_dyn(c, W, nib), hv, err) : -1;
+    out[i] = hv.D > 0 ? probe_dyn(c, W, key_hash_dyn(c, W, nib), hv, err) : -1;
 }
 
 // Occupied slots per bucket (slots fill in order: the count is the index of
