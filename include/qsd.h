@@ -392,17 +392,19 @@ int qsd_term_table(qsd_ctx ctx, qsd_op op, qsd_sub sub, int64_t row0,
 int qsd_rayleigh_quotient(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *u, double *out);
 
 /* The same Rayleigh quotient as qsd_rayleigh_quotient, for callers that
- * cannot allocate device memory: code that runs while a stream is captured
- * into a CUDA graph, serving or real-time loops that reserve all memory up
- * front, embedders whose own allocator owns the device.  It calls no
- * cudaMalloc, cudaFree or allocating library routine; its scratch is one
- * fixed __device__ array of the library (about 16.8 MB, held by every GPU
- * that loads the library until the process exits), so it serves subspaces
- * of at most 2^20 rows and returns QSD_ERR_CAPACITY above that.  The first
- * call on a device resolves the array's device address (do it before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller.  The paper has no counterpart;
- * it is a deployment variant of the refinement step. */
+ * cannot allocate device memory: host programs whose own pool or allocator
+ * owns the whole device (an allocation here would fail or fragment memory
+ * they manage), and serving or real-time loops that reserve all memory up
+ * front because cudaMalloc and cudaFree can synchronise the device and stall
+ * other streams mid-flight.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine; its scratch is one fixed __device__ array of the library
+ * (about 16.8 MB, held by every GPU that loads the library until the process
+ * exits), so it serves subspaces of at most 2^20 rows and returns
+ * QSD_ERR_CAPACITY above that.  The first call on a device resolves the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU race and must be serialised by the caller.  The paper has
+ * no counterpart; it is a deployment variant of the refinement step. */
 int qsd_rayleigh_quotient_noalloc(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *u, double *out);
 
 /* ------------------------------------------------------------- eigensolver */

@@ -145,9 +145,13 @@ def apply(op, keys: np.ndarray, x: np.ndarray) -> np.ndarray:
 
 
 def apply_rows(op, keys: np.ndarray, x: np.ndarray, rows) -> np.ndarray:
-    """(H_S x)[rows] for a real ``x`` ([D] or [D, k]); complex result."""
+    """(H_S x)[rows] for a real ``x`` ([D] or [D, k]); complex result (the
+    coefficients may be complex).  A complex ``x`` raises TypeError: the C
+    routine reads real x only.  ``rows`` may repeat and come in any order."""
     keys = np.ascontiguousarray(keys, np.uint64)
     D, W = keys.shape
+    if np.iscomplexobj(x):
+        raise TypeError("apply_rows takes a real x")
     x = np.asarray(x, np.float64)
     x2 = np.ascontiguousarray(x.reshape(D, 1) if x.ndim == 1 else x)
     k = x2.shape[1]

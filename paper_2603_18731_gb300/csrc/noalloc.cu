@@ -1,9 +1,11 @@
 // qsd_rayleigh_quotient_noalloc: the Rayleigh quotient without any device
-// allocation, for callers that cannot call cudaMalloc -- code running while a
-// stream is being captured into a CUDA graph (allocation is not capturable),
-// real-time or serving loops that reserve all their memory up front and must
-// not hit the allocator (or its implicit synchronisation) mid-flight, and
-// embedders whose own memory manager owns the whole device.
+// allocation, for callers that cannot call cudaMalloc:
+//   * host programs that hand the whole device to their own memory pool or
+//     allocator at start-up, so that an allocation by this library would fail
+//     or fragment memory the host program owns;
+//   * serving or real-time loops that reserve all their memory up front and
+//     must not reach the allocator mid-flight, because cudaMalloc and cudaFree
+//     can synchronise the device and stall the work of every other stream.
 //
 // The scratch it needs (H u, the diagonal of H_S and per-block partial sums)
 // lives in one file-scope __device__ array of fixed size, so every GPU that

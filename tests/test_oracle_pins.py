@@ -87,6 +87,53 @@ def test_oracle_apply_matches_kronecker(n, T, D, k, seed):
     assert np.allclose(oracle.dense(op, keys), H, atol=1e-13)
 
 
+@pytest.mark.parametrize("n,T,D,k,seed", [(6, 20, 50, 1, 20), (9, 35, 300, 4, 21), (12, 30, 900, 2, 22)])
+def test_oracle_apply_rows_matches_kronecker_and_apply(n, T, D, k, seed):
+    """The sampled-row product (the CPU baseline and the full-size parity
+    checker) against dense Kronecker rows and the whole-vector product: rows
+    in random order with repeats, k columns, complex non-Hermitian
+    coefficients, real x."""
+    op = wl.random_extended(n, T, max_weight=n, seed=seed, hermitian=False, real=False)
+    keys = _sorted_keys(wl.random_subspace(n, D, seed + 3, duplicates=7))
+    Dk = keys.shape[0]
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(Dk, k))
+    rows = rng.integers(0, Dk, size=min(Dk, 60))
+    rows[-1] = rows[0]  # a repeated row
+    H = brute.restricted(op, keys)
+    got = oracle.apply_rows(op, keys, x, rows)
+    assert got.shape == (rows.shape[0], k)
+    assert _rel(got, (H @ x)[rows]) < 1e-13
+    assert _rel(got, oracle.apply(op, keys, x)[rows]) < 1e-15
+    # one-dimensional x gives one-dimensional rows
+    y1 = oracle.apply_rows(op, keys, x[:, 0], rows)
+    assert y1.shape == rows.shape and _rel(y1, (H @ x[:, 0])[rows]) < 1e-13
+
+
+def test_oracle_apply_rows_column_not_row_index():
+    """A column's x is read at the column's index: with x = e_c only the rows
+    that reach column c see a nonzero, equal to H[row, c]."""
+    n = 8
+    op = wl.random_extended(n, 24, max_weight=4, seed=31, hermitian=True, real=True)
+    keys = _sorted_keys(wl.random_subspace(n, 200, 32))
+    Dk = keys.shape[0]
+    H = brute.restricted(op, keys)
+    rows = np.arange(Dk)
+    for c in (0, Dk // 3, Dk - 1):
+        x = np.zeros(Dk)
+        x[c] = 1.0
+        assert np.array_equal(oracle.apply_rows(op, keys, x, rows), H[:, c])
+
+
+def test_oracle_apply_rows_rejects_complex_x_and_bad_rows():
+    op = wl.tfim_chain(6, g=1.0)
+    keys = _sorted_keys(wl.full_space(6))
+    with pytest.raises(TypeError):
+        oracle.apply_rows(op, keys, np.ones(64) * 1j, [0, 1])
+    with pytest.raises(oracle.OracleError):
+        oracle.apply_rows(op, keys, np.ones(64), [64])
+
+
 def test_oracle_identity_term_and_empty_subspace():
     op = wl.QubitOperator.from_terms(3, [(2.5, []), (1.0, [(0, "X")])])
     keys = _sorted_keys(wl.full_space(3))

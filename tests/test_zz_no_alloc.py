@@ -1,10 +1,13 @@
 """The allocation-free Rayleigh quotient, for callers that cannot call
-cudaMalloc (stream capture, pre-reserved serving loops, foreign allocators).
+cudaMalloc: host programs whose own memory pool owns the whole device, and
+serving loops that reserve memory up front because cudaMalloc and cudaFree can
+synchronise the device mid-flight.
 
 Called through the C ABI and checked against qsd_rayleigh_quotient, which
 allocates its scratch, on two calls in a row (the shared fixed scratch keeps
-the previous call's contents, which must not leak into the next result), and
-its size limit.  Kept in a file that pytest collects last.
+the previous call's contents, which must not leak into the next result); the
+device's free memory is unchanged across a warm call; and its size limit.
+Kept in a file that pytest collects last.
 """
 import ctypes
 
@@ -44,6 +47,29 @@ def test_noalloc_matches_allocating_entry_point_twice():
             assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]), (call, got, ref)
             assert abs(got[1] - ref[1]) <= 1e-10 * abs(ref[1]), (call, got, ref)
             assert abs(got[2] - ref[2]) <= TOL * abs(ref[2]), (call, got, ref)
+
+
+def test_noalloc_leaves_device_free_memory_unchanged():
+    import torch
+    import paper_2603_18731_gb300 as q
+    with q.create(0) as ctx:
+        op = wl.ising_heavy_hex(60, seed=9)
+        words = wl.flip_subspace(60, 20_000, max_flips=8, seed=9)
+        h = ctx.load_operator(op)
+        sub = ctx.build_subspace(60, words)
+        with torch.cuda.stream(ctx.stream):
+            u = torch.as_tensor(np.random.default_rng(3).normal(size=sub.dim), device=ctx.device)
+        # the first call loads the kernels and resolves the scratch address
+        rc, first = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
+        assert rc == 0
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        rc, again = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert rc == 0
+        assert free1 == free0, (free0, free1)
+        assert np.array_equal(first, again)
 
 
 def test_noalloc_rejects_subspace_above_limit():
