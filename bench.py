@@ -42,7 +42,8 @@ L2_FLUSH_BYTES = 512 << 20
 PATH_NAMES = {0: "group scan, lane per row", 1: "group scan, 8 lanes per row", 2: "excitation index",
               3: "half evaluation, lane per row", 4: "half evaluation, 8 lanes per row",
               5: "group scan, lane per row, rows in hash order",
-              6: "half evaluation, lane per row, rows in hash order"}
+              6: "half evaluation, lane per row, rows in hash order",
+              7: "sector-factored enumeration, warp per row"}
 
 
 # ------------------------------------------------------------------ workloads

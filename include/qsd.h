@@ -147,6 +147,20 @@ int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,
 /* Dimension, qubit count and hash capacity (slots) of a subspace. */
 int qsd_subspace_info(qsd_sub sub, int64_t *dim, int32_t *n_qubits, int64_t *capacity);
 
+/* Sector-factored index of a subspace (Results: chemistry subspaces are the
+ * products of alpha and beta strings).  The build splits every string at
+ * qubit split = n / 2 (n <= 128) into a low half a and a high half b; when
+ * S is exactly A x B for its distinct halves A and B (D = |A| |B|), it keeps
+ * A and B sorted and, per string of each, its neighbours in the same list by
+ * excitation type (up to two set bits cleared and two clear bits set), so
+ * that row = ib |A| + ia and the factored product needs no lookup.  Outputs
+ * (any may be NULL): *is_product 1 or 0, *split, *n_a = |A|, *n_b = |B|,
+ * *neighbours = entries of both neighbour lists (0 when not a product).
+ * A product subspace is not indexed when a string has more than 4096
+ * neighbours of one type or the lists exceed 64 (|A| + |B|) + 2^20 entries. */
+int qsd_subspace_factored(qsd_sub sub, int32_t *is_product, int32_t *split, int64_t *n_a, int64_t *n_b,
+                          int64_t *neighbours);
+
 /* Copy the sorted bit-strings, row-major [D][W], to `out` (device memory when
  * out_on_device != 0, else host memory; host copies synchronise). */
 int qsd_subspace_keys(qsd_ctx ctx, qsd_sub sub, uint64_t *out, int out_on_device);
@@ -273,7 +287,9 @@ int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32
                                       index (ladder groups enumerated from each row's
                                       occupation; ignored when the operator has none);
                                       3 half evaluation (below; a plain scan where it
-                                      does not apply) */
+                                      does not apply); 4 sector-factored enumeration
+                                      where it applies (QSD_PATH_FACTORED), else as 0.
+                                      Auto takes the factored path whenever it applies. */
 #define QSD_TUNE_LANES_PER_ROW  2  /* per-row scan: 0 auto, 1 or 8 lanes per row */
 #define QSD_TUNE_AUTOTUNE       3  /* 1 (default): the first product of each (operator,
                                       subspace, precision, block width) on a context times
@@ -319,6 +335,15 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
 #define QSD_PATH_HALF_8     4
 #define QSD_PATH_SCAN_HASH  5  /* QSD_PATH_SCAN_1 with the rows in hash order */
 #define QSD_PATH_HALF_HASH  6  /* QSD_PATH_HALF_1 with the rows in hash order */
+#define QSD_PATH_FACTORED   7  /* product subspace S = A x B of its halves at qubit n/2
+                                  (see qsd_subspace_factored) and an operator whose
+                                  ladder groups have a rank index (qsd_op_info
+                                  excitation_rank_index, n <= 128): each row enumerates
+                                  only the columns in S -- products of its halves'
+                                  neighbours in A and B by excitation type -- and
+                                  computes their index as ib' |A| + ia' (no lookup);
+                                  bulk group rejection, named as future work in the
+                                  paper's Discussion */
 int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
                      int64_t k, int32_t *path_out);
 

@@ -98,6 +98,8 @@ SIGNATURES = [
     ("qsd_free_op", C.c_int, [_P]),
     ("qsd_build_subspace", C.c_int, [_P, _I32, _I64, _P, C.c_int, C.POINTER(_P), C.POINTER(_I64)]),
     ("qsd_subspace_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
+    ("qsd_subspace_factored", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
+                                        C.POINTER(_I64)]),
     ("qsd_subspace_keys", C.c_int, [_P, _P, _P, C.c_int]),
     ("qsd_subspace_index", C.c_int, [_P, _P, _I64, _P, _P]),
     ("qsd_free_sub", C.c_int, [_P]),
@@ -197,6 +199,15 @@ class Subspace:
         d, n, cap = C.c_int64(), C.c_int32(), C.c_int64()
         self.ctx._check(lib().qsd_subspace_info(self.handle, C.byref(d), C.byref(n), C.byref(cap)))
         return cap.value
+
+    def factored(self) -> dict:
+        """The sector-factored index: is_product, split, n_a, n_b, neighbours."""
+        ip, sp = C.c_int32(), C.c_int32()
+        na, nb, nn = C.c_int64(), C.c_int64(), C.c_int64()
+        self.ctx._check(lib().qsd_subspace_factored(self.handle, C.byref(ip), C.byref(sp), C.byref(na),
+                                                    C.byref(nb), C.byref(nn)))
+        return {"is_product": bool(ip.value), "split": sp.value, "n_a": na.value, "n_b": nb.value,
+                "neighbours": nn.value}
 
     def free(self):
         if self.handle:

@@ -5,7 +5,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "excite.cuh"
+#include "factor_kernel.cuh"
 #include "qsd_internal.cuh"
 
 namespace qsd {
@@ -166,6 +166,14 @@ static bool use_excitation(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     return cand >= 0.0 && 4.0 * cand < (double)op->G;
 }
 
+// The sector-factored path applies when the subspace is the product of its
+// halves at the operator's sector split and the operator's ladder groups have
+// a dense rank index (W <= 2).
+static bool use_factored(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    if (ctx->tune_mode == 1 || ctx->tune_mode == 2 || ctx->tune_mode == 3) return false;
+    return sub->fac.ok && op->exc_ok && op->dense_ok && op->W <= 2 && op->exc_split == sub->fac.split;
+}
+
 namespace {
 
 ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y) {
@@ -221,12 +229,34 @@ ExcParams make_exc(qsd_op op) {
     return e;
 }
 
+FacParams make_fac(qsd_sub sub) {
+    const Factored &f = sub->fac;
+    FacParams r{};
+    r.A = f.A.as<uint64_t>();
+    r.B = f.B.as<uint64_t>();
+    r.ptrA = f.ptrA.as<uint32_t>();
+    r.ptrB = f.ptrB.as<uint32_t>();
+    r.nbrA = f.nbrA.as<uint32_t>();
+    r.nbrB = f.nbrB.as<uint32_t>();
+    r.nA = (uint32_t)f.nA;
+    r.nB = (uint32_t)f.nB;
+    r.split = f.split;
+    return r;
+}
+
 // Product paths: 0 = per-row group scan with one lane per row, 1 = the same
 // with 8 lanes per row, 2 = excitation index (warp per row), 3 and 4 = the
 // half-evaluation scan (lower-triangle groups, mirrored by atomic adds) with
-// 1 or 8 lanes per row, 5 and 6 = paths 0 and 3 with the rows in hash order.
-void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int precision, int KB,
-                 cudaStream_t stream) {
+// 1 or 8 lanes per row, 5 and 6 = paths 0 and 3 with the rows in hash order,
+// 7 = sector-factored enumeration (warp per row, product subspaces).
+void launch_path(int path, const ApplyParams &p, const ExcParams &e, const FacParams &f, int W, int precision,
+                 int KB, cudaStream_t stream) {
+    if (path == 7) {
+        if (precision == QSD_FP64) launch_apply_fac<QSD_FP64>(p, e, f, W, KB, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_fac<QSD_FP32_MIXED>(p, e, f, W, KB, stream);
+        else launch_apply_fac<QSD_FP32_DOT2>(p, e, f, W, KB, stream);
+        return;
+    }
     if (path == 3 || path == 4 || path == 6) {
         launch_apply_sym(p, W, path == 4 ? 8 : 1, KB, stream, path == 6);
         return;
@@ -248,6 +278,7 @@ void launch_path(int path, const ApplyParams &p, const ExcParams &e, int W, int 
 int half_of(int path) { return path == 5 ? 6 : path + 3; }
 
 int heuristic_path(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    if (use_factored(ctx, op, sub)) return 7;
     if (use_excitation(ctx, op, sub)) return 2;
     return choose_lanes(ctx, sub->D, op->G) == 8 ? 1 : 0;
 }
@@ -277,6 +308,9 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     if (ctx->tune_mode == 1 || (ctx->tune_mode == 3 && !sym_ok)) return lanes_path;
     if (ctx->tune_mode == 3) return half_of(lanes_path);
     if (ctx->tune_mode == 2 && op->exc_ok) return 2;
+    // a product subspace with an indexed operator: the factored enumeration
+    // reaches only columns in S, so no other path is timed against it
+    if (use_factored(ctx, op, sub)) return 7;
     const bool ho_open = ho_ok && ctx->row_order == 0 && lanes_path == 0;
     if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym) && !ho_open) return lanes_path;
     const auto key = std::make_tuple((const void *)op, (const void *)sub, precision, KB);
@@ -328,6 +362,7 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     ApplyParams p = make_params(ctx, op, sub, diag, (int)ld, x, y);
     p.col0 = col0;
     const ExcParams e = op->exc_ok ? make_exc(op) : ExcParams{};
+    const FacParams f{};
     cudaEvent_t a, b;
     QSD_CUDA(cudaEventCreate(&a));
     QSD_CUDA(cudaEventCreate(&b));
@@ -337,7 +372,7 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
         float ms = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             QSD_CUDA(cudaEventRecord(a, stream));
-            launch_path(c, p, e, op->W, precision, KB, stream);
+            launch_path(c, p, e, f, op->W, precision, KB, stream);
             QSD_CUDA(cudaEventRecord(b, stream));
             QSD_CUDA(cudaEventSynchronize(b));
             float t = 0.f;
@@ -361,17 +396,19 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
              cudaStream_t stream, bool may_tune) {
     ApplyParams p = make_params(ctx, op, sub, diag, k, x, y);
     ExcParams e{};
+    FacParams f{};
     bool have_e = false;
     int64_t c = 0;
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
         p.col0 = c;
         const int path = product_path(ctx, op, sub, diag, precision, KB, x, y, k, c, stream, may_tune);
-        if (path == 2 && !have_e) {
+        if ((path == 2 || path == 7) && !have_e) {
             e = make_exc(op);
+            f = make_fac(sub);
             have_e = true;
         }
-        launch_path(path, p, e, op->W, precision, KB, stream);
+        launch_path(path, p, e, f, op->W, precision, KB, stream);
         c += KB;
     }
 }
@@ -537,6 +574,18 @@ int qsd_subspace_info(qsd_sub sub, int64_t *dim, int32_t *n_qubits, int64_t *cap
     if (dim) *dim = sub->D;
     if (n_qubits) *n_qubits = sub->n_qubits;
     if (capacity) *capacity = sub->n_buckets * kBucketSlots;
+    return QSD_OK;
+}
+
+int qsd_subspace_factored(qsd_sub sub, int32_t *is_product, int32_t *split, int64_t *n_a, int64_t *n_b,
+                          int64_t *neighbours) {
+    if (!sub) return QSD_ERR_INVALID_ARG;
+    const Factored &f = sub->fac;
+    if (is_product) *is_product = f.ok ? 1 : 0;
+    if (split) *split = f.ok ? f.split : 0;
+    if (n_a) *n_a = f.nA;
+    if (n_b) *n_b = f.nB;
+    if (neighbours) *neighbours = f.nnzA + f.nnzB;
     return QSD_OK;
 }
 
@@ -748,7 +797,7 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     switch (knob) {
     case QSD_TUNE_APPLY_PATH:
-        if (value < 0 || value > 3) return QSD_ERR_INVALID_ARG;
+        if (value < 0 || value > 4) return QSD_ERR_INVALID_ARG;
         ctx->tune_mode = (int)value;
         return QSD_OK;
     case QSD_TUNE_LANES_PER_ROW:

@@ -105,7 +105,8 @@ struct CsrState {
 
 struct qsd_ctx_s {
     int device = 0;
-    int tune_mode = 0;    // product path: 0 auto, 1 group scan, 2 excitation index, 3 half evaluation
+    int tune_mode = 0;    // product path: 0 auto, 1 group scan, 2 excitation index, 3 half evaluation,
+                          // 4 sector-factored where it applies (else auto)
     int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
     int allow_sym = 0;    // the autotuner may pick the half-evaluation product
     int row_order = 0;    // lane-per-row scans: 0 auto, 1 index order, 2 hash order
@@ -128,6 +129,26 @@ struct qsd_ctx_s {
     uint32_t *h_err = nullptr;   // pinned mirror
 };
 
+namespace qsd {
+// Sector-factored index of a subspace S whose strings split at qubit `split`
+// into a low half a (qubits [0, split)) and a high half b (qubits
+// [split, n)).  Built when S is exactly the product A x B of its distinct
+// halves (|S| = |A| |B|); S is then sorted by (b, a) and row = ib * |A| + ia
+// for a = A[ia], b = B[ib].  Per half list, each string's neighbours in the
+// same list by excitation type: the other strings reached by turning dOcc of
+// its set bits off and dEmp of its clear bits on (0 <= dOcc, dEmp <= 2, not
+// both 0), type t = 3 dOcc + dEmp - 1, ascending by index.
+struct Factored {
+    bool ok = false;
+    int split = 0;
+    int64_t nA = 0, nB = 0;
+    DevBuf A, B;        // uint64 [nA], [nB]: distinct halves, ascending
+    DevBuf ptrA, ptrB;  // uint32 [8 n + 1]: start of (string i, type t) at 8 i + t
+    DevBuf nbrA, nbrB;  // uint32: neighbour indices
+    int64_t nnzA = 0, nnzB = 0;
+};
+}  // namespace qsd
+
 struct qsd_sub_s {
     qsd_ctx ctx = nullptr;
     int32_t n_qubits = 0;
@@ -144,6 +165,7 @@ struct qsd_sub_s {
     qsd::DevBuf hkeys;  // uint64 [W][D] keys[w][hperm[i]] at i
     qsd::DevBuf hhash;  // uint64 [D] rhash[hperm[i]] at i
     std::vector<uint64_t> key0;  // host copy of the first (smallest) string
+    qsd::Factored fac;           // product subspaces (n <= 128), split n / 2
 };
 
 struct qsd_op_s {
@@ -444,6 +466,9 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n, uint64
 // The subspace's rows in bucket order (hperm, hkeys; W <= 4).
 void build_hash_order(qsd_ctx ctx, qsd_sub sub);
 void build_excitation_index(qsd_ctx ctx, qsd_op op);
+// Sector-factored index of the subspace at split n / 2 (n <= 128), kept only
+// when the subspace is the product of its distinct halves.
+void build_factored(qsd_ctx ctx, qsd_sub sub);
 // Candidate flip masks per row of the excitation path for the subspace's
 // first string, or -1 when the operator has no excitation index.
 double excitation_candidates(qsd_op op, qsd_sub sub);

@@ -192,6 +192,7 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     sub->tags = std::move(t.tags);
     sub->sidx = std::move(t.sidx);
     if (D > 0 && W <= kMaxWordsStatic) build_hash_order(ctx, sub);
+    build_factored(ctx, sub);
     sub->key0.assign(W, 0);
     if (D > 0)
         for (int w = 0; w < W; ++w)

@@ -323,6 +323,33 @@ def test_vectorised_jordan_wigner_matches_second_quantisation(n_orb, seed):
     np.testing.assert_allclose(brute.full_matrix(qop), fermion.dense(fop), atol=1e-13)
 
 
+def test_vectorised_jordan_wigner_two_words_matches_second_quantisation():
+    """72 modes (two-word keys): the vectorised transform of a sparse
+    molecular operator, restricted to a product subspace, equals the matrix
+    that second quantisation gives on the same occupation strings."""
+    n_orb = 36
+    h1, eri = wl.chem_integrals(n_orb, seed=5)
+    eri = np.where(np.abs(eri) >= 0.045, eri, 0.0)
+    h1 = np.where(np.abs(h1) >= 0.1, h1, 0.0)
+    qop = wl.molecular_qubit_operator(h1, eri)
+    fop = wl.molecular_fermionic(h1, eri)
+    alpha = wl.excitation_strings(n_orb, 3, 8, 2, 4)
+    beta = wl.excitation_strings(n_orb, 3, 7, 2, 1004)
+    keys = _sorted_keys(wl.product_subspace(alpha, beta, n_orb))
+    assert keys.shape[1] == 2
+    states = [int(k[0]) | (int(k[1]) << 64) for k in keys]
+    pos = {v: i for i, v in enumerate(states)}
+    ref = np.zeros((len(states), len(states)))
+    for coef, ops in fop.terms:
+        for b, sb in enumerate(states):
+            r = fermion.apply_term(ops, sb)
+            if r is not None and r[1] in pos:
+                ref[pos[r[1]], b] += coef * r[0]
+    got = oracle.dense(qop, keys)
+    assert np.count_nonzero(np.abs(ref) > 1e-12) > len(states)
+    np.testing.assert_allclose(got, ref, atol=1e-13)
+
+
 def test_hubbard_dimer_closed_form():
     t, U = 1.0, 3.0
     h = np.array([[0.0, -t], [-t, 0.0]])

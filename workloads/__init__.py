@@ -507,9 +507,9 @@ def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray
     L operators (leftmost first); ``coef``: [T].  Same algebra as
     ``jordan_wigner`` (per qubit, the ordered product of the factors each
     operator places there: its ladder letter on its own mode, Z below it), with
-    numpy over the T products.  Equal words are combined.  n_modes <= 64.
+    numpy over the T products.  Equal words are combined.  n_modes <= 128.
     """
-    assert n_modes <= 64
+    assert n_modes <= 128
     code, sign = _monoid_table()
     T, L = modes.shape
     modes = modes.astype(np.int64)
@@ -535,20 +535,28 @@ def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray
     alive = ~np.any(prod == 6, axis=1) & (scale != 0)
     modes, prod, scale = modes[alive], prod[alive], scale[alive]
     T = modes.shape[0]
+    NW = (n_modes + 63) // 64
     one = np.uint64(1)
-    bits = (one << modes.astype(np.uint64))
-    touched = np.zeros(T, np.uint64)
-    zstr = np.zeros(T, np.uint64)
+    word = modes // 64
+    bits = (one << (modes % 64).astype(np.uint64))  # [T, L] bit within its word
+    touched = np.zeros((T, NW), np.uint64)
+    zstr = np.zeros((T, NW), np.uint64)
     for a in range(L):
-        touched |= bits[:, a]
-        zstr ^= bits[:, a] - one  # Z on every mode below operator a
+        for w in range(NW):
+            on = word[:, a] == w
+            touched[:, w] |= np.where(on, bits[:, a], np.uint64(0))
+            # Z on every mode below operator a: whole lower words, and the
+            # bits below it in its own word
+            below = np.where(word[:, a] > w, ~np.uint64(0), np.where(on, bits[:, a] - one, np.uint64(0)))
+            zstr[:, w] ^= below
     zstr &= ~touched
-    masks = {c: np.zeros(T, np.uint64) for c in range(1, 6)}
+    masks = {c: np.zeros((T, NW), np.uint64) for c in range(1, 6)}
     for b in range(L):
         for c in range(1, 6):
-            masks[c] |= np.where(prod[:, b] == c, bits[:, b], np.uint64(0))
+            for w in range(NW):
+                masks[c][:, w] |= np.where((prod[:, b] == c) & (word[:, b] == w), bits[:, b], np.uint64(0))
     masks[1] |= zstr
-    key = np.stack([masks[c] for c in range(1, 6)], axis=1)
+    key = np.concatenate([masks[c] for c in range(1, 6)], axis=1)
     uniq, inv = np.unique(key, axis=0, return_inverse=True)
     csum = np.zeros(uniq.shape[0])
     np.add.at(csum, inv.ravel(), scale)
@@ -560,7 +568,7 @@ def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray
     mat = np.full((uniq.shape[0], n), 255, np.uint8)
     for c in range(1, 6):
         for q in range(n):
-            sel = (uniq[:, c - 1] >> np.uint64(q)) & one
+            sel = (uniq[:, (c - 1) * NW + q // 64] >> np.uint64(q % 64)) & one
             mat[sel.astype(bool), q] = lettermap[c]
     nz = mat != 255
     counts = nz.sum(axis=1)
@@ -609,10 +617,8 @@ def molecular_fermionic(h1: np.ndarray, eri: np.ndarray, const: float = 0.0):
             for q in range(n_orb):
                 if h1[p, q] != 0:
                     terms.append((h1[p, q], [(p + s * n_orb, True), (q + s * n_orb, False)]))
-    for p, q, r, s_ in itertools.product(range(n_orb), repeat=4):
+    for p, q, r, s_ in zip(*(idx.tolist() for idx in np.nonzero(eri))):  # lexicographic (p, q, r, s)
         v = eri[p, q, r, s_]
-        if v == 0:
-            continue
         for s in (0, 1):
             for t in (0, 1):
                 terms.append((0.5 * v, [(p + s * n_orb, True), (r + t * n_orb, True),
