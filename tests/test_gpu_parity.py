@@ -292,12 +292,16 @@ def test_autotuned_product_matches_oracle(ctx, kind, k):
     tuned = ctx.product_path(h, sub, k=k)
     y2 = ctx.apply_H(h, sub, to_cuda(ctx, x, torch.float64))  # cached choice
     ctx.synchronize()
-    assert guess in (0, 1, 2) and tuned in (0, 1, 2, 5)
+    if kind == "chem":
+        # a product subspace: the factored enumeration, chosen without timing
+        assert sub.factored()["is_product"] and guess == tuned == 7
+    else:
+        assert guess in (0, 1, 2) and tuned in (0, 1, 2, 5)
     for y in (y0, y1, y2):
         assert rel_err(y.cpu().numpy(), ref) <= FP64_TOL
     assert torch.equal(y1, y2)
-    ctx.set_tuning(1, 2 if tuned == 2 else 1)
-    if tuned != 2:
+    ctx.set_tuning(1, {2: 2, 7: 4}.get(tuned, 1))
+    if tuned not in (2, 7):
         ctx.set_tuning(2, 8 if tuned == 1 else 1)
         ctx.set_tuning(5, 2 if tuned == 5 else 1)
     assert ctx.product_path(h, sub, k=k) == tuned

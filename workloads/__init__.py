@@ -557,9 +557,16 @@ def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray
                 masks[c][:, w] |= np.where((prod[:, b] == c) & (word[:, b] == w), bits[:, b], np.uint64(0))
     masks[1] |= zstr
     key = np.concatenate([masks[c] for c in range(1, 6)], axis=1)
-    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    # equal words: sort by every key column (the first column most
+    # significant), then sum the coefficients of each run
+    order = np.lexsort(key.T[::-1])
+    ks = key[order]
+    start = np.ones(T, bool)
+    start[1:] = np.any(ks[1:] != ks[:-1], axis=1)
+    run = np.cumsum(start) - 1
+    uniq = ks[start]
     csum = np.zeros(uniq.shape[0])
-    np.add.at(csum, inv.ravel(), scale)
+    np.add.at(csum, run, scale[order])
     keep = csum != 0
     uniq, csum = uniq[keep], csum[keep]
     # words: letters on qubits in ascending order
@@ -567,9 +574,12 @@ def jordan_wigner_products(modes: np.ndarray, dags: np.ndarray, coef: np.ndarray
     lettermap = {1: Z, 2: P0, 3: P1, 4: RAISE, 5: LOWER}
     mat = np.full((uniq.shape[0], n), 255, np.uint8)
     for c in range(1, 6):
-        for q in range(n):
-            sel = (uniq[:, (c - 1) * NW + q // 64] >> np.uint64(q % 64)) & one
-            mat[sel.astype(bool), q] = lettermap[c]
+        for w in range(NW):
+            col = np.ascontiguousarray(uniq[:, (c - 1) * NW + w]).astype("<u8")
+            bitsel = np.unpackbits(col.view(np.uint8).reshape(-1, 8), axis=1, bitorder="little").astype(bool)
+            width = min(64, n - 64 * w)
+            blk = mat[:, 64 * w:64 * w + width]
+            blk[bitsel[:, :width]] = lettermap[c]
     nz = mat != 255
     counts = nz.sum(axis=1)
     term_ptr = np.zeros(uniq.shape[0] + 1, np.int64)
