@@ -50,7 +50,8 @@ PATH_NAMES = {0: "group scan, lane per row", 1: "group scan, 8 lanes per row", 2
               3: "half evaluation, lane per row", 4: "half evaluation, 8 lanes per row",
               5: "group scan, lane per row, rows in hash order",
               6: "half evaluation, lane per row, rows in hash order",
-              7: "sector-factored enumeration, warp per row"}
+              7: "sector-factored enumeration, warp per row",
+              8: "filter/verify scan, lane per row, rows in hash order"}
 
 
 # ------------------------------------------------------------------ workloads
@@ -179,6 +180,9 @@ def whole_job_rate(units_per_rank: float, seconds: float, world: int) -> float:
     return world * units_per_rank / seconds
 
 
+# product path -> qsd_set_tuning (knob, value) pairs
+PATH_KNOBS = {"auto": [], "scan": [(1, 1), (2, 1), (5, 1)], "scan-hash": [(1, 1), (2, 1), (5, 2)],
+              "scan8": [(1, 1), (2, 8)], "excitation": [(1, 2)], "factored": [(1, 4)], "filter-verify": [(1, 5)]}
 HEAD = {"chem": (0, 16), "xxz": (0, 1), "ising": (0, 1), "tfim": (0, 1)}  # (precision, k)
 SPIN_EXTRAS = ("ising", "xxz")
 
@@ -269,16 +273,36 @@ def count_lookups(ctx, h, sub, G):
     return lookups, hits, ("sampled %d rows" % nrow) if sampled else "every row"
 
 
+FP64_FMA_PER_SM_CYCLE = 2  # GB300: FP64 FMA issue rate per SM per cycle (1/64 of FP32)
+
+
 def roofline_of(ms, path, tag, D, W, k, prec, lookups, hits, info, peak, peak_kind, sm_mhz, n_sms):
+    """Roofline of one product launch.  The sector-factored path with FP64
+    accumulation (QSD_FP64, QSD_FP32_MIXED) is bound by the FP64 FMA pipe:
+    every found column costs k FP64 FMAs and the GB300 retires 2 per SM per
+    cycle, so that bound is reported ('alu', FP64 TFLOP/s at the sampled SM
+    clock) with the HBM figures beside it; every other launch by memory
+    ('hbm').  A committed ncu summary of the same path adds its measured DRAM
+    traffic and the warp-instruction issue roof."""
     s_x = 8 if prec == 0 else 4
     G = info["n_groups"]
     b_alg = algorithmic_bytes(path, D, W, k, s_x, lookups, hits, info["n_terms"], G)
     achieved = b_alg / (ms * 1e-3) / 1e9
     traffic, inst = read_profile(tag, path)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": f"{peak_kind} hbm_gbs (burst, kernel timed alone)", "traffic": traffic,
-            "algorithmic_bytes_per_launch": int(b_alg), "lookups_per_launch": 0 if path == 7 else lookups,
-            "hits_per_launch": hits, "kernel_ms": ms, "profile": f"profiles/{tag}.md" if traffic else None}
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": f"{peak_kind} hbm_gbs (burst, kernel timed alone)", "traffic": traffic,
+           "algorithmic_bytes_per_launch": int(b_alg), "lookups_per_launch": 0 if path == 7 else lookups,
+           "hits_per_launch": hits, "kernel_ms": ms, "profile": f"profiles/{tag}.md" if traffic else None}
+    roof = hbm
+    if path == 7 and prec in (0, 1) and hits and sm_mhz:
+        flops = 2.0 * hits * k
+        peak_f = FP64_FMA_PER_SM_CYCLE * 2 * n_sms * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak_f, "unit": "TFLOP/s",
+                "frac": flops / (ms * 1e-3) / 1e12 / peak_f, "traffic": traffic,
+                "peak_source": f"FP64 FMA pipe: {FP64_FMA_PER_SM_CYCLE} FMA/SM/cycle x {n_sms} SMs x "
+                               f"median SM clock {sm_mhz:.0f} MHz (derived from unit counts; no measured FP64 peak)",
+                "flops_per_launch": flops, "flops_definition": "2 x found columns x k (FP64 FMAs of the accumulation)",
+                "kernel_ms": ms, "hbm": {k2: v for k2, v in hbm.items() if k2 not in ("traffic",)}}
     if inst is not None and sm_mhz:
         # warp-instruction issue: 4 schedulers per SM, one instruction each per cycle
         peak_issue = n_sms * 4 * sm_mhz * 1e6
@@ -411,6 +435,8 @@ def run_gpu(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     ctx = q.create(local)
+    for knob, value in PATH_KNOBS[args.path]:
+        ctx.set_tuning(knob, value)
     timer = Timer(ctx, dist)
     name = args.workload
     prec0, k0 = HEAD[name]
@@ -843,6 +869,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the Ising and XXZ workloads")
     ap.add_argument("--chem-strings", type=int, default=1500,
                     help="alpha and beta strings of the fermionic workload (reduced cases for profiling)")
+    ap.add_argument("--path", default="auto", choices=sorted(PATH_KNOBS),
+                    help="force a product path (profiling); auto lets the library choose")
     ap.add_argument("--skip-counts", action="store_true",
                     help="do not count lookups and hits (the roofline's byte count is then incomplete)")
     ap.add_argument("--no-solve", action="store_true")

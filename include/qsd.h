@@ -288,7 +288,9 @@ int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32
                                       occupation; ignored when the operator has none);
                                       3 half evaluation (below; a plain scan where it
                                       does not apply); 4 sector-factored enumeration
-                                      where it applies (QSD_PATH_FACTORED), else as 0.
+                                      where it applies (QSD_PATH_FACTORED), else as 0;
+                                      5 filter/verify scan where it applies
+                                      (QSD_PATH_FILTER_VERIFY), else as 0.
                                       Auto takes the factored path whenever it applies. */
 #define QSD_TUNE_LANES_PER_ROW  2  /* per-row scan: 0 auto, 1 or 8 lanes per row */
 #define QSD_TUNE_AUTOTUNE       3  /* 1 (default): the first product of each (operator,
@@ -344,6 +346,16 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value);
                                   computes their index as ib' |A| + ia' (no lookup);
                                   bulk group rejection, named as future work in the
                                   paper's Discussion */
+#define QSD_PATH_FILTER_VERIFY 8  /* single-column products of operators whose groups all
+                                  test and sign at most 5 qubits (spin models; at most
+                                  1024 groups and 2048 tabulated elements), rows in
+                                  hash order (n <= 256): a filter pass over the
+                                  groups, with group records and elements staged in
+                                  shared memory, loads each row's bucket and queues
+                                  only tag matches and overflowing buckets; a verify
+                                  pass resolves 32 queued lookups at a time, one per
+                                  lane, and returns the found elements to their rows
+                                  in group order: bitwise QSD_PATH_SCAN_HASH */
 int qsd_product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t precision,
                      int64_t k, int32_t *path_out);
 

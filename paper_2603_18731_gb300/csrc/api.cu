@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "apply_fv.cuh"
 #include "factor_kernel.cuh"
 #include "qsd_internal.cuh"
 
@@ -171,7 +172,17 @@ static bool use_excitation(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
 // a dense rank index (W <= 2).
 static bool use_factored(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     if (ctx->tune_mode == 1 || ctx->tune_mode == 2 || ctx->tune_mode == 3) return false;
-    return sub->fac.ok && op->exc_ok && op->dense_ok && op->W <= 2 && op->exc_split == sub->fac.split;
+    return sub->fac.ok && op->exc_ok && op->dense_ok && op->W <= 2 && op->exc_split == sub->fac.split &&
+           op->trec.p != nullptr;
+}
+
+// The filter/verify scan applies to single-column products of operators whose
+// groups are all table groups, over subspaces with a hash order (W <= 4),
+// within its shared-memory staging limits.
+static bool fv_ok(qsd_ctx ctx, qsd_op op, qsd_sub sub, int KB) {
+    return KB == 1 && op->W <= kMaxWordsStatic && sub->hperm.p != nullptr && op->G >= 1 &&
+           op->n_table_groups == op->G && op->G <= kFvMaxGroups && op->n_amp <= kFvMaxAmps &&
+           fv_smem_bytes(op->G, op->n_amp) <= 48 * 1024 && ctx->row_order != 1;
 }
 
 namespace {
@@ -186,6 +197,7 @@ ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag,
     p.grec = op->grec.as<GroupRec>();
     p.amp = op->amp.as<double>();
     p.ampf = op->ampf.as<float2>();
+    p.n_amp = op->n_amp;
     p.gF = op->gF.as<uint64_t>();
     p.grange = op->grange.as<int32_t>();
     p.gL = op->gL.as<uint8_t>();
@@ -229,15 +241,17 @@ ExcParams make_exc(qsd_op op) {
     return e;
 }
 
-FacParams make_fac(qsd_sub sub) {
+FacParams make_fac(qsd_op op, qsd_sub sub) {
     const Factored &f = sub->fac;
     FacParams r{};
+    r.trec = op->trec.p;
+    r.qscale = op->qscale;
     r.A = f.A.as<uint64_t>();
     r.B = f.B.as<uint64_t>();
     r.ptrA = f.ptrA.as<uint32_t>();
     r.ptrB = f.ptrB.as<uint32_t>();
-    r.nbrA = f.nbrA.as<uint32_t>();
-    r.nbrB = f.nbrB.as<uint32_t>();
+    r.nbrA = f.nbrA.as<uint2>();
+    r.nbrB = f.nbrB.as<uint2>();
     r.nA = (uint32_t)f.nA;
     r.nB = (uint32_t)f.nB;
     r.split = f.split;
@@ -248,9 +262,16 @@ FacParams make_fac(qsd_sub sub) {
 // with 8 lanes per row, 2 = excitation index (warp per row), 3 and 4 = the
 // half-evaluation scan (lower-triangle groups, mirrored by atomic adds) with
 // 1 or 8 lanes per row, 5 and 6 = paths 0 and 3 with the rows in hash order,
-// 7 = sector-factored enumeration (warp per row, product subspaces).
+// 7 = sector-factored enumeration (warp per row, product subspaces),
+// 8 = filter/verify scan (lane per row, hash order, table groups, k = 1).
 void launch_path(int path, const ApplyParams &p, const ExcParams &e, const FacParams &f, int W, int precision,
                  int KB, cudaStream_t stream) {
+    if (path == 8) {
+        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, (int)p.n_amp, W, p.num_sms, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, (int)p.n_amp, W, p.num_sms, stream);
+        else launch_apply_fv<QSD_FP32_DOT2>(p, (int)p.n_amp, W, p.num_sms, stream);
+        return;
+    }
     if (path == 7) {
         if (precision == QSD_FP64) launch_apply_fac<QSD_FP64>(p, e, f, W, KB, stream);
         else if (precision == QSD_FP32_MIXED) launch_apply_fac<QSD_FP32_MIXED>(p, e, f, W, KB, stream);
@@ -308,11 +329,13 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     if (ctx->tune_mode == 1 || (ctx->tune_mode == 3 && !sym_ok)) return lanes_path;
     if (ctx->tune_mode == 3) return half_of(lanes_path);
     if (ctx->tune_mode == 2 && op->exc_ok) return 2;
+    if (ctx->tune_mode == 5 && fv_ok(ctx, op, sub, KB)) return 8;
     // a product subspace with an indexed operator: the factored enumeration
     // reaches only columns in S, so no other path is timed against it
     if (use_factored(ctx, op, sub)) return 7;
     const bool ho_open = ho_ok && ctx->row_order == 0 && lanes_path == 0;
-    if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym) && !ho_open) return lanes_path;
+    if (ctx->tune_lanes != 0 && !op->exc_ok && !(sym_ok && ctx->allow_sym) && !ho_open && !fv_ok(ctx, op, sub, KB))
+        return lanes_path;
     const auto key = std::make_tuple((const void *)op, (const void *)sub, precision, KB);
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
@@ -354,6 +377,7 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
         }
     }
     if (guess != 2 && cand >= 0.0 && cand < (double)op->G) cands.push_back(2);
+    if (fv_ok(ctx, op, sub, KB)) cands.push_back(8);
     if (cands.size() < 2) {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         ctx->tune_cache[key] = guess;
@@ -405,7 +429,7 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
         const int path = product_path(ctx, op, sub, diag, precision, KB, x, y, k, c, stream, may_tune);
         if ((path == 2 || path == 7) && !have_e) {
             e = make_exc(op);
-            f = make_fac(sub);
+            f = make_fac(op, sub);
             have_e = true;
         }
         launch_path(path, p, e, f, op->W, precision, KB, stream);
@@ -797,7 +821,7 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     switch (knob) {
     case QSD_TUNE_APPLY_PATH:
-        if (value < 0 || value > 4) return QSD_ERR_INVALID_ARG;
+        if (value < 0 || value > 5) return QSD_ERR_INVALID_ARG;
         ctx->tune_mode = (int)value;
         return QSD_OK;
     case QSD_TUNE_LANES_PER_ROW:

@@ -1,0 +1,229 @@
+// Filter/verify product for operators whose groups are all table groups
+// (every term tests and signs only qubits of a support of <= 5, e.g. all
+// spin models), one lane per row, rows in the subspace's hash order, one
+// right-hand side (included by the apply_fv_inst.cu units).
+//
+// The per-row group loop of the gather product (Methods, "Matrix evaluation")
+// is split in two passes so that the rare work of a lookup runs at full warp
+// width:
+//   filter  the warp walks the groups together (group records and amplitude
+//           tables staged in shared memory once per block); each lane takes
+//           its row's pattern on the group's support, skips a zero element
+//           (the paper's rejection of null terms before the query), and loads
+//           the bucket of r xor F.  A bucket with no matching tag that does
+//           not overflow is a miss -- the common case -- and costs nothing
+//           more.  Otherwise (row, group, bucket, tag matches) goes to a
+//           per-warp ring of candidates in shared memory.
+//   verify  whenever 32 candidates are queued, each lane takes one: the
+//           owner's key (by shuffle) xor F, the row indices of the matching
+//           slots, the full-key check, x of the found column, and the probe's
+//           continuation into the next buckets when the bucket overflowed.
+//           The found (element, x) pairs go back to their owners in queue
+//           order by shuffles.
+// Candidates enter the ring in group order and leave it in that order, so
+// each row accumulates its elements in group order with the same operations
+// as the one-pass scan: the result is bitwise that of QSD_PATH_SCAN_HASH.
+// The grid is persistent (the resident blocks of every SM) so that the
+// staging is paid once per block; blocks take 256-row tiles in a grid-stride
+// loop.
+#pragma once
+
+#include "apply_kernel.cuh"
+
+namespace qsd {
+
+constexpr int kFvMaxGroups = 1024;  // group records staged per block (G < 2^18 for the meta word)
+constexpr int kFvMaxAmps = 2048;    // amplitudes staged per block (index < 2^24)
+constexpr int kFvRing = 64;         // candidates per warp (at most 31 + 32 queued)
+constexpr int kFvThreads = 256;
+constexpr int kFvWarps = kFvThreads / 32;
+constexpr int kFvU = 4;             // groups per filter batch (bucket loads in flight per lane)
+
+struct FvRec {
+    uint32_t hhi;     // high word of h(F)
+    uint32_t tagnb;   // bits 0-7: low byte of h(F); bits 8-10: support size nb
+    uint32_t aoff;    // first amplitude of the group
+    uint32_t nzmask;  // bit l: the amplitude of pattern l is nonzero
+    uint64_t pos;     // support qubits, 12 bits each, ascending
+};
+static_assert(sizeof(FvRec) == 24, "24-byte staged group record");
+
+// Shared memory: records, amplitudes (8 bytes each: FP64, or the FP32 (hi,
+// lo) pair of DOT2), then per warp a ring of kFvRing candidates as three
+// uint32 arrays: bucket; meta = owner lane (bits 0-4), bucket overflowed (bit
+// 5), tag matches (bits 6-13), group (bits 14-31); amplitude index (bits
+// 0-23) and tag (bits 24-31).
+inline size_t fv_smem_bytes(int64_t G, int64_t n_amp) {
+    return (size_t)G * sizeof(FvRec) + (size_t)n_amp * 8 + (size_t)kFvWarps * kFvRing * 12;
+}
+
+template <int W, int PREC>
+__global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, int n_amp, int64_t tiles) {
+    using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char fv_smem[];
+    const int G = (int)p.G;
+    FvRec *rec = reinterpret_cast<FvRec *>(fv_smem);
+    double *amp = reinterpret_cast<double *>(fv_smem + (size_t)G * sizeof(FvRec));
+    float2 *ampf = reinterpret_cast<float2 *>(amp);
+    uint32_t *ring = reinterpret_cast<uint32_t *>(fv_smem + (size_t)G * sizeof(FvRec) + (size_t)n_amp * 8);
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *q_b = ring + (size_t)wib * kFvRing * 3;
+    uint32_t *q_m = q_b + kFvRing;
+    uint32_t *q_a = q_m + kFvRing;
+
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(p.grec + g));
+        const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(p.grec + g) + 1);
+        FvRec R;
+        R.hhi = (uint32_t)(r0.x >> 32);
+        R.tagnb = ((uint32_t)r0.x & 0xffu) | ((r1.y & 7u) << 8);
+        R.aoff = r1.x;
+        R.nzmask = r1.z;
+        R.pos = r0.y;
+        rec[g] = R;
+    }
+    if (PREC == QSD_FP32_DOT2) {
+        for (int i = threadIdx.x; i < n_amp; i += blockDim.x) ampf[i] = __ldg(p.ampf + i);
+    } else {
+        for (int i = threadIdx.x; i < n_amp; i += blockDim.x) amp[i] = __ldg(p.amp + i);
+    }
+    __syncthreads();
+
+    const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
+    const uint32_t bshift = (uint32_t)p.hv.shift - 32u;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t pos = tile * kFvThreads + threadIdx.x;
+        const bool active = pos < p.D;
+        const int64_t pc = active ? pos : p.D - 1;
+        uint64_t key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = __ldg(p.hkeys + (size_t)w * p.D + pc);
+        const uint64_t hr = __ldg(p.hhash + pc);
+        const uint32_t hr_hi = (uint32_t)(hr >> 32), hr_lo = (uint32_t)hr & 0xffu;
+        double acc = 0.0;
+        float as = 0.f, ae = 0.f;
+        uint32_t head = 0, tail = 0;  // warp-uniform ring positions
+
+        // verify the n (1..32) oldest candidates, deliver them in queue order
+        auto verify = [&](int n) {
+            const uint32_t slot = (head + (uint32_t)lane) & (kFvRing - 1);
+            const bool mine = lane < n;
+            const uint32_t meta = mine ? q_m[slot] : 0u;
+            const uint32_t b = mine ? q_b[slot] : 0u;
+            const uint32_t at = mine ? q_a[slot] : 0u;
+            const int o = (int)(meta & 31u);
+            uint64_t c[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[w] = __shfl_sync(0xffffffffu, key[w], o);
+            bool found = false;
+            TIO xv = TIO(0);
+            double a = 0.0;
+            float ah = 0.f, al = 0.f;
+            if (mine) {
+                const int64_t g = (int64_t)(meta >> 14);
+#pragma unroll
+                for (int w = 0; w < W; ++w) c[w] ^= __ldg(p.gF + (size_t)w * p.G + g);
+                int64_t idx = verify_matches_x<W, TIO>(p.hv, b, (meta >> 6) & 0xffu, c, x + p.col0, p.ld, xv);
+                if (idx < 0 && (meta & 32u)) {
+                    idx = probe_from<W>(p.hv, b, at >> 24, c, p.err);
+                    if (idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
+                }
+                found = idx >= 0;
+                const uint32_t ai = at & 0xffffffu;
+                if (PREC == QSD_FP32_DOT2) {
+                    const float2 f = ampf[ai];
+                    ah = f.x;
+                    al = f.y;
+                } else {
+                    a = amp[ai];
+                }
+            }
+            const uint32_t tagged = (uint32_t)o | (found ? 32u : 0u);
+            for (int t = 0; t < n; ++t) {
+                const uint32_t ot = __shfl_sync(0xffffffffu, tagged, t);
+                const TIO xt = __shfl_sync(0xffffffffu, xv, t);
+                if (PREC == QSD_FP32_DOT2) {
+                    const float aht = __shfl_sync(0xffffffffu, ah, t);
+                    const float alt = __shfl_sync(0xffffffffu, al, t);
+                    if (ot == ((uint32_t)lane | 32u)) dot2_add(as, ae, aht, alt, (float)xt);
+                } else {
+                    const double at_ = __shfl_sync(0xffffffffu, a, t);
+                    if (ot == ((uint32_t)lane | 32u)) acc = fma(at_, (double)xt, acc);
+                }
+            }
+            head += (uint32_t)n;
+        };
+
+        for (int g0 = 0; g0 < G; g0 += kFvU) {
+            uint2 tb[kFvU];
+            uint32_t bk[kFvU], tg[kFvU], ai[kFvU];
+            bool need[kFvU];
+#pragma unroll
+            for (int u = 0; u < kFvU; ++u) {
+                const int g = g0 + u;
+                need[u] = false;
+                if (g < G) {  // warp-uniform
+                    const FvRec R = rec[g];
+                    const int nb = (int)((R.tagnb >> 8) & 7u);
+                    int l = 0;
+                    for (int i = 0; i < nb; ++i) l |= (int)bit_of<W>(key, (int)((R.pos >> (12 * i)) & 0xfff)) << i;
+                    need[u] = active && ((R.nzmask >> l) & 1u);
+                    ai[u] = R.aoff + (uint32_t)l;
+                    const uint32_t t = (hr_lo ^ R.tagnb) & 0xffu;
+                    tg[u] = t ? t : 1u;
+                    bk[u] = (hr_hi ^ R.hhi) >> bshift;
+                    if (need[u]) tb[u] = __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + bk[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kFvU; ++u) {
+                bool cand = false;
+                uint32_t match = 0, full = 0;
+                if (need[u]) {
+                    full = bucket_full(tb[u]) ? 1u : 0u;
+                    cand = full || tag_any(tb[u], tg[u]);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                if (bal == 0u) continue;  // warp-uniform: every lookup of the group missed
+                if (cand) {
+                    match = tag_match(tb[u], tg[u]);
+                    const uint32_t slot = (tail + (uint32_t)__popc(bal & lt)) & (kFvRing - 1);
+                    q_b[slot] = bk[u];
+                    q_m[slot] = (uint32_t)lane | (full << 5) | (match << 6) | ((uint32_t)(g0 + u) << 14);
+                    q_a[slot] = ai[u] | (tg[u] << 24);
+                }
+                tail += (uint32_t)__popc(bal);
+                __syncwarp();
+                if (tail - head >= 32u) {
+                    verify(32);
+                    __syncwarp();
+                }
+            }
+        }
+        __syncwarp();
+        if (tail != head) verify((int)(tail - head));
+        __syncwarp();
+        if (active) {
+            const int64_t r = (int64_t)__ldg(p.hperm + pc);
+            const double d = __ldg(p.diag + r);
+            const TIO xr = __ldg(x + r * p.ld + p.col0);
+            TIO *yr = static_cast<TIO *>(p.y) + r * p.ld + p.col0;
+            if (PREC == QSD_FP32_DOT2) {
+                const float dh = (float)d, dl = (float)(d - (double)dh);
+                dot2_add(as, ae, dh, dl, (float)xr);
+                *yr = (TIO)(as + ae);
+            } else {
+                *yr = (TIO)fma(d, (double)xr, acc);
+            }
+        }
+    }
+}
+
+// Launch the filter/verify product for precision mode PREC (W <= 4, k = 1,
+// hash order, every group a table group, G <= kFvMaxGroups, n_amp <=
+// kFvMaxAmps).
+template <int PREC>
+void launch_apply_fv(const ApplyParams &p, int n_amp, int W, int num_sms, cudaStream_t s);
+
+}  // namespace qsd

@@ -64,6 +64,7 @@ struct ApplyParams {
     const GroupRec *grec;    // [G]
     const double *amp;       // table amplitudes
     const float2 *ampf;      // the same split into FP32 (hi, lo)
+    int64_t n_amp;           // number of table amplitudes
     const uint64_t *gF;      // [W][G]
     const int32_t *grange;   // [G+1]
     const uint8_t *gL;       // [G]
@@ -147,6 +148,25 @@ __device__ __noinline__ double scan_amp(const ApplyParams &p, int64_t g, const u
         amp += ph;
     }
     return amp;
+}
+
+// The double of a float, exactly, by integer operations on the IEEE-754
+// encodings: sign kept, 8-bit exponent rebiased by 1023 - 127 = 896, the 23
+// mantissa bits moved up by 29 (a float's value fits a double exactly).
+// Zeros map to zeros; subnormal, infinite and NaN inputs (exponent field 0
+// with a nonzero mantissa, or 255) take the hardware conversion.  Cheaper
+// than the conversion instruction where FP64 work is the bottleneck.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    const uint32_t sign_hi = u & 0x80000000u;
+    if (ex - 1u < 254u) {  // normal: exponent 1..254
+        const uint32_t hi = sign_hi | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        const uint32_t lo = u << 29;
+        return __hiloint2double((int)hi, (int)lo);
+    }
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)sign_hi, 0);
+    return (double)f;
 }
 
 // Error-free accumulation of hi*x + lo*x into (s, e).

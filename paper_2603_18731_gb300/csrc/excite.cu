@@ -8,8 +8,10 @@
 // that form -- its single and double "excitations" per shape of the operator --
 // and finds their groups in a hash table keyed by the flip mask.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <set>
+#include <vector>
 
 #include "excite.cuh"
 
@@ -50,6 +52,38 @@ __global__ void k_gather_exc(int W, int64_t G, const int32_t *__restrict__ ids, 
     if (i >= n) return;
     const int32_t g = ids[i];
     for (int w = 0; w < W; ++w) out[(size_t)w * n + i] = gF[(size_t)w * G + g];
+}
+
+template <int W>
+__global__ void k_term_records(int64_t T, const uint64_t *__restrict__ tP, const uint64_t *__restrict__ tV,
+                               const uint64_t *__restrict__ tZ, const double *__restrict__ tphi, double scale,
+                               TermRec<W> *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    TermRec<W> r{};
+    for (int w = 0; w < W; ++w) {
+        r.P[w] = tP[(size_t)w * T + t];
+        r.V[w] = tV[(size_t)w * T + t];
+        r.Z[w] = tZ[(size_t)w * T + t];
+    }
+    r.q = __double2ll_rn(tphi[t] * scale);  // scale is a power of two: the product is exact
+    out[t] = r;
+}
+
+// Fixed-point exponent e of an operator's term phases: the largest e with
+// max over groups of sum |phi| * 2^e < 2^62 (at most 2^62 in magnitude for
+// any sum of a group's terms), capped at 1000.
+int fixed_point_exponent(const std::vector<double> &phi, const std::vector<int32_t> &grange) {
+    double m = 0.0;
+    for (size_t g = 0; g + 1 < grange.size(); ++g) {
+        double s = 0.0;
+        for (int32_t t = grange[g]; t < grange[g + 1]; ++t) s += std::fabs(phi[(size_t)t]);
+        m = std::max(m, s);
+    }
+    if (!(m > 0.0)) return 0;
+    int ex = 0;
+    std::frexp(m, &ex);  // m < 2^ex
+    return std::min(1000, 61 - ex);
 }
 
 int64_t choose_h(int64_t m, int k) { return k == 0 ? 1 : (k == 1 ? m : m * (m - 1) / 2); }
@@ -166,6 +200,26 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op) {
     op->g_shift = t.shift;
     QSD_CUDA(cudaStreamSynchronize(s));
     build_dense_index(ctx, op, exc);
+    if (W <= 2) {
+        const size_t rb = W == 1 ? sizeof(TermRec<1>) : sizeof(TermRec<2>);
+        std::vector<double> phi((size_t)T);
+        QSD_CUDA(cudaMemcpyAsync(phi.data(), op->tphi.p, (size_t)T * 8, cudaMemcpyDeviceToHost, s));
+        QSD_CUDA(cudaStreamSynchronize(s));
+        const int ex = fixed_point_exponent(phi, gr);
+        const double scale = std::ldexp(1.0, ex);
+        op->qscale = std::ldexp(1.0, -ex);
+        op->trec.alloc((size_t)T * rb);
+        if (W == 1)
+            k_term_records<1><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
+                                                                 op->trec.as<TermRec<1>>());
+        else
+            k_term_records<2><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
+                                                                 op->trec.as<TermRec<2>>());
+        QSD_LAUNCH_CHECK();
+        QSD_CUDA(cudaStreamSynchronize(s));
+    }
     op->exc_ok = true;
 }
 

@@ -25,6 +25,33 @@ struct ExcParams {
     uint32_t shapes[kMaxShapes];
 };
 
+// The masks of one term and its phase in 64-bit fixed point, side by side
+// (whole 16-byte loads), for the factored product (W <= 2): q = phi 2^e
+// rounded to an integer, with one exponent e per operator chosen so that any
+// group's sum of |q| stays below 2^62 (the operator's qscale = 2^-e).  A sum
+// of terms is then an exact integer sum, converted to FP64 once.
+template <int W> struct TermRec;
+template <> struct alignas(16) TermRec<1> {
+    uint64_t P[1], V[1], Z[1];
+    int64_t q;
+};
+template <> struct alignas(16) TermRec<2> {
+    uint64_t P[2], V[2], Z[2];
+    int64_t q;
+    uint64_t pad;
+};
+
+template <int W>
+__device__ __forceinline__ TermRec<W> load_term(const TermRec<W> *__restrict__ r) {
+    static_assert(sizeof(TermRec<W>) % 16 == 0, "whole 16-byte loads");
+    TermRec<W> out;
+    const uint4 *src = reinterpret_cast<const uint4 *>(r);
+    uint4 *dst = reinterpret_cast<uint4 *>(&out);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(TermRec<W>) / 16); ++i) dst[i] = __ldg(src + i);
+    return out;
+}
+
 // Launch the warp-per-row excitation product for precision mode PREC.
 template <int PREC>
 void launch_apply_exc(const ApplyParams &p, const ExcParams &e, int W, int KB, cudaStream_t s);

@@ -11,7 +11,10 @@
 // misses -- and computes their index as ib' |A| + ia' instead of probing the
 // hash table.  This file builds what that needs: the two sorted half lists
 // and, per string of each list, its neighbours in the same list by
-// excitation type (see Factored in qsd_internal.cuh).
+// excitation type (see Factored in qsd_internal.cuh), each with what the
+// product needs of its flip mask: the rank of the flipped positions (the
+// group's entry in the operator's rank index) and the row's pattern on them
+// (its ladder integer within the sector).
 #include <algorithm>
 #include <vector>
 
@@ -38,13 +41,35 @@ __global__ void k_halves(const uint64_t *__restrict__ keys, int64_t D, int split
     }
 }
 
+// Rank of the set of bits of F (positions below 64, at most four bits) in
+// the combinatorial number system, sum over the ascending positions p_k of
+// C(p_k, k), with the row's bits at those positions (bit k - 1 of the
+// pattern = bit p_k of `row`) and the number of bits.  Packed as rank (bits
+// 0-19; C(64, 4) < 2^20), pattern (bits 20-23) and count (bits 24-26).
+__device__ __forceinline__ uint32_t neighbour_meta(uint64_t F, uint64_t row) {
+    uint64_t rank = 0;
+    uint32_t pat = 0;
+    int k = 0;
+    while (F) {
+        const uint64_t p = (uint64_t)(__ffsll((long long)F) - 1);
+        ++k;
+        uint64_t c = p;  // C(p, k) by the multiplicative formula, exact in 64 bits
+        for (int i = 1; i < k; ++i) c = c * (p - (uint64_t)i) / (uint64_t)(i + 1);
+        rank += c;
+        pat |= (uint32_t)((row >> p) & 1ull) << (k - 1);
+        F &= F - 1;
+    }
+    return (uint32_t)rank | (pat << 20) | ((uint32_t)k << 24);
+}
+
 // One warp per string i of the list L[0..n): its neighbours j by type
 // t = 3 dOcc + dEmp - 1 with dOcc = popc(L[i] & ~L[j]) and
 // dEmp = popc(~L[i] & L[j]) both <= 2 (j = i has type -1).  Count mode
 // (ptr == nullptr): cnt[8 i + t] = number of neighbours of type t.  Fill
-// mode: writes them at ptr[8 i + t] in ascending j.
+// mode: writes (j, neighbour_meta(L[i] ^ L[j], L[i])) at ptr[8 i + t] in
+// ascending j.
 __global__ void k_neighbours(const uint64_t *__restrict__ L, uint32_t n, const uint32_t *__restrict__ ptr,
-                             uint32_t *out) {
+                             uint32_t *cnt, uint2 *out) {
     const uint32_t i = (uint32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;  // warp-uniform
@@ -54,22 +79,24 @@ __global__ void k_neighbours(const uint64_t *__restrict__ L, uint32_t n, const u
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
         const uint32_t j = j0 + (uint32_t)lane;
         int t = -1;
+        uint64_t b = 0;
         if (j < n) {
-            const uint64_t b = L[j];
+            b = L[j];
             const int dO = __popcll(a & ~b), dE = __popcll(~a & b);
             if (dO <= 2 && dE <= 2) t = 3 * dO + dE - 1;
         }
 #pragma unroll
         for (int tt = 0; tt < 8; ++tt) {
             const uint32_t m = __ballot_sync(0xffffffffu, t == tt);
-            if (ptr && t == tt) out[ptr[8 * (size_t)i + tt] + run[tt] + __popc(m & lt)] = j;
+            if (ptr && t == tt)
+                out[ptr[8 * (size_t)i + tt] + run[tt] + __popc(m & lt)] = make_uint2(j, neighbour_meta(a ^ b, a));
             run[tt] += __popc(m);
         }
     }
     if (!ptr) {
 #pragma unroll
         for (int tt = 0; tt < 8; ++tt)
-            if (lane == tt) out[8 * (size_t)i + tt] = run[tt];
+            if (lane == tt) cnt[8 * (size_t)i + tt] = run[tt];
     }
 }
 
@@ -85,7 +112,7 @@ bool build_neighbours(qsd_ctx ctx, const uint64_t *L, int64_t n, int64_t cap, De
     DevBuf cnt((size_t)m * 4);
     ptr.alloc((size_t)(m + 1) * 4);
     const unsigned blocks = (unsigned)blocks_for(n * 32, 256);
-    k_neighbours<<<blocks, 256, 0, s>>>(L, (uint32_t)n, nullptr, cnt.as<uint32_t>());
+    k_neighbours<<<blocks, 256, 0, s>>>(L, (uint32_t)n, nullptr, cnt.as<uint32_t>(), nullptr);
     QSD_LAUNCH_CHECK();
     // at most kMaxTypeNeighbours per (string, type): a row's candidate count
     // (products of two lists, summed over at most 16 shapes) stays in 32 bits
@@ -103,9 +130,9 @@ bool build_neighbours(qsd_ctx ctx, const uint64_t *L, int64_t n, int64_t cap, De
     }
     k_set_u32<<<1, 1, 0, s>>>(ptr.as<uint32_t>() + m, (uint32_t)total);
     QSD_LAUNCH_CHECK();
-    nbr.alloc((size_t)std::max<uint64_t>(total, 1) * 4);
+    nbr.alloc((size_t)std::max<uint64_t>(total, 1) * 8);
     if (total > 0) {
-        k_neighbours<<<blocks, 256, 0, s>>>(L, (uint32_t)n, ptr.as<uint32_t>(), nbr.as<uint32_t>());
+        k_neighbours<<<blocks, 256, 0, s>>>(L, (uint32_t)n, ptr.as<uint32_t>(), nullptr, nbr.as<uint2>());
         QSD_LAUNCH_CHECK();
     }
     QSD_CUDA(cudaStreamSynchronize(s));  // cnt is freed on return

@@ -5,16 +5,23 @@
 // shape of the operator's ladder terms -- (dOcc, dEmp) changes in sector 0
 // and in sector 1 (see excite.cuh) -- the columns the row can reach inside S
 // are the products of ia's neighbours of the sector-0 type and ib's
-// neighbours of the sector-1 type (a type (0, 0) keeps the half).  The lanes
-// split the concatenation of these products over all shapes; each candidate
-// column (a', b') gives the flip mask F = (a ^ a', b ^ b'), whose group the
-// dense rank index returns (one load; -1: no group has that mask), and the
-// group's matrix element at the row (ladder-integer term range, projector
-// tests, Jordan-Wigner signs: the same evaluation as every other path).  A
-// nonzero element is multiplied by x at column ib' |A| + ia': no lookup.
-// Groups outside the excitation index are scanned per row with a lookup.
-// Each lane accumulates its candidates in a fixed order and the warp reduces
-// with shuffles: the result is deterministic.
+// neighbours of the sector-1 type (a type (0, 0) keeps the half).  Each
+// neighbour entry carries the rank of its flipped positions and the row's
+// bits on them, so a candidate column (a', b') finds its group in the dense
+// rank index with one load (-1: no group has that flip mask) and its ladder
+// integer -- the row's pattern on F, low sector first -- without touching
+// the strings.  The group's terms with that ladder integer (int_ptrs, Fig.
+// 3b) pass their remaining projector tests and add phi (-1)^popc(r & Z): the
+// same element as every other path.  A nonzero element multiplies x at
+// column ib' |A| + ia': no lookup.  Groups outside the excitation index are
+// evaluated and looked up per row.
+//
+// Work split: the warp evaluates 32 candidates at a time, one per lane; then
+// the (element, column) pairs are broadcast by shuffles and the block's KB
+// columns of x are gathered by KB lanes per candidate (32 / KB candidates per
+// load instruction: one coalesced row of x each), each lane accumulating one
+// column.  Lanes holding the same column are reduced with shuffles at the
+// end.  Every order is fixed: the result is deterministic.
 #pragma once
 
 #include "excite.cuh"
@@ -24,25 +31,12 @@ namespace qsd {
 struct FacParams {
     const uint64_t *A, *B;        // distinct halves
     const uint32_t *ptrA, *ptrB;  // [8 n + 1] neighbour list starts by (string, type)
-    const uint32_t *nbrA, *nbrB;  // neighbour indices
+    const uint2 *nbrA, *nbrB;     // (neighbour index, rank | pattern << 20 | bits << 24)
+    const void *trec;             // TermRec<W> [T]
+    double qscale;                // value of one fixed-point unit of the term phases
     uint32_t nA, nB;
     int split;
 };
-
-// Rank of the set of bits of F (positions below 64) in the combinatorial
-// number system: sum over the ascending positions p_1 < p_2 < ... of
-// C(p_j, j).  F has at most four bits.
-__device__ __forceinline__ uint32_t bits_rank(uint64_t F, const uint32_t (*binom)[64]) {
-    uint32_t r = 0;
-    int j = 1;
-    while (F) {
-        const int p = __ffsll((long long)F) - 1;
-        r += binom[j][p];
-        F &= F - 1;
-        ++j;
-    }
-    return r;
-}
 
 // Neighbour type of (dOcc, dEmp) in the low (sector 0) or high (sector 1)
 // fields of a shape; -1 for (0, 0): the half is kept.
@@ -52,19 +46,39 @@ __device__ __forceinline__ int shape_type(uint32_t occ, uint32_t emp) {
 
 constexpr uint32_t kKeepHalf = 0xffffffffu;
 
+// Element of group g at the row from the terms [b, e) of its ladder range,
+// in fixed-point units: each term's projector test (the ladder bits already
+// match) and sign, summed exactly in 64-bit integers.  The FP64 pipe of the
+// GB300 runs at 1/64 of the FP32 rate and the lanes' term loops diverge, so
+// per-term FP64 adds took a third of it; the integer sum costs ALU slots
+// only, and its one conversion to FP64 per candidate is exact to within the
+// rounding of each phase to a multiple of 2^-e.
+template <int W>
+__device__ __forceinline__ int64_t ladder_terms(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
+                                                const uint64_t (&key)[W]) {
+    int64_t sum = 0;
+    for (int32_t t = b; t < e; ++t) {
+        const TermRec<W> r = load_term<W>(tr + t);
+        bool ok = true;
+        int par = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            ok &= (key[w] & r.P[w]) == r.V[w];
+            par ^= __popcll(key[w] & r.Z[w]);
+        }
+        const int64_t v = (par & 1) ? -r.q : r.q;
+        sum += ok ? v : 0;
+    }
+    return sum;
+}
+
 template <int W, int KB, int PREC>
 __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const ExcParams e, const FacParams f) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
-    __shared__ uint32_t binom[5][64];
+    static_assert(32 % KB == 0, "KB divides the warp");
+    constexpr int NC = 32 / KB;  // candidates per gather instruction
     __shared__ uint32_t pre[8][kMaxShapes + 1];  // per warp: first candidate of each shape
     __shared__ uint32_t sa[8][kMaxShapes], sb[8][kMaxShapes], lb[8][kMaxShapes];
-    for (int i = threadIdx.x; i < 5 * 64; i += blockDim.x) {
-        const int j = i / 64, x = i % 64;
-        uint64_t c = 1;
-        for (int t = 0; t < j; ++t) c = c * (uint64_t)(x - t) / (uint64_t)(t + 1);
-        binom[j][x] = x >= j ? (uint32_t)c : 0u;
-    }
-    __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= p.D) return;  // warp-uniform
@@ -72,7 +86,7 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
-    const uint64_t a = __ldg(f.A + ia), b = __ldg(f.B + ib);
+    const TermRec<W> *__restrict__ trec = static_cast<const TermRec<W> *>(f.trec);
     // lane s < n_shapes: the candidate lists of shape s and their product size
     uint32_t cnt = 0;
     if (lane < e.n_shapes) {
@@ -102,84 +116,108 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     if (lane < e.n_shapes) pre[wib][lane + 1] = incl;
     if (lane == 0) pre[wib][0] = 0;
     __syncwarp();
-    const uint32_t total = pre[wib][e.n_shapes];
+    const uint32_t n_exc = pre[wib][e.n_shapes];
+    const uint32_t total = n_exc + (uint32_t)e.n_rest;
+    const uint64_t hr = e.n_rest > 0 ? key_hash<W>(key, p.nib) : 0ull;
 
-    const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
-    double acc[KB];
-    float as[KB], ae[KB];
+    const TIO *__restrict__ x = static_cast<const TIO *>(p.x) + p.col0 + (lane % KB);
+    double acc = 0.0;
+    float as = 0.f, ae = 0.f;
+    int si = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        // 1. one candidate per lane: its element (0: none) and column
+        const uint32_t t = base + (uint32_t)lane;
+        double amp = 0.0;
+        uint32_t col = 0;
+        if (t < n_exc) {
+            while (pre[wib][si + 1] <= t) ++si;  // t ascends: the shape only moves forward
+            const uint32_t u = t - pre[wib][si];
+            const uint32_t l1 = lb[wib][si];
+            const uint32_t ua = u / l1, ub = u - ua * l1;
+            const uint32_t s0 = sa[wib][si], s1 = sb[wib][si];
+            const uint2 nA = s0 == kKeepHalf ? make_uint2(ia, 0u) : __ldg(f.nbrA + s0 + ua);
+            const uint2 nB = s1 == kKeepHalf ? make_uint2(ib, 0u) : __ldg(f.nbrB + s1 + ub);
+            const int32_t g = __ldg(e.dense + e.dbase[si] + (nA.y & 0xfffffu) * e.dstride[si] + (nB.y & 0xfffffu));
+            if (g >= 0) {
+                const uint32_t na = (nA.y >> 24) & 7u, nb = (nB.y >> 24) & 7u;
+                int32_t tb, te;
+                if (na + nb <= 4) {
+                    // ladder table (every indexed group is ladder-only on F)
+                    const uint32_t l = ((nA.y >> 20) & 15u) | (((nB.y >> 20) & 15u) << na);
+                    tb = __ldg(p.gptr + (size_t)g * 17 + l);
+                    te = __ldg(p.gptr + (size_t)g * 17 + l + 1);
+                } else {
+                    tb = __ldg(p.grange + g);
+                    te = __ldg(p.grange + g + 1);
+                }
+                const int64_t qs = ladder_terms<W>(trec, tb, te, key);
+                if (qs != 0) amp = __ll2double_rn(qs) * f.qscale;
+                col = nB.x * f.nA + nA.x;
+            }
+        } else if (t < total) {
+            const int64_t g = __ldg(e.rest_gid + (t - n_exc));
+            const double a = scan_amp<W>(p, g, key);
+            if (((uint64_t)__double_as_longlong(a) << 1) != 0ull) {
+                uint64_t c[W];
 #pragma unroll
-    for (int j = 0; j < KB; ++j) { acc[j] = 0.0; as[j] = 0.f; ae[j] = 0.f; }
-
-    auto add = [&](double amp, uint64_t col) {
-        const TIO *xc = x + col * p.ld + p.col0;
+                for (int w = 0; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
+                const int64_t idx = probe<W>(c, hr ^ __ldg(&p.grec[g].hF), p.hv, p.err);
+                if (idx >= 0) {
+                    amp = a;
+                    col = (uint32_t)idx;
+                }
+            }
+        }
+        // 2. gather: KB lanes per candidate, NC candidates per instruction
+        const bool nz = ((uint64_t)__double_as_longlong(amp) << 1) != 0ull;
+        const uint32_t any = __ballot_sync(0xffffffffu, nz);
+        if (!any) continue;
         if (PREC == QSD_FP32_DOT2) {
-            const float h = (float)amp, l = (float)(amp - (double)h);
+            // the element's FP32 (hi, lo) split once, in the candidate's lane
+            const float ah = (float)amp, al = (float)(amp - (double)ah);
 #pragma unroll
-            for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], h, l, (float)__ldg(xc + j));
+            for (int i = 0; i < KB; ++i) {
+                const int src = i * NC + lane / KB;
+                const float h = __shfl_sync(0xffffffffu, ah, src);
+                const float l = __shfl_sync(0xffffffffu, al, src);
+                const uint32_t c = __shfl_sync(0xffffffffu, col, src);
+                if (h != 0.f || l != 0.f) dot2_add(as, ae, h, l, (float)__ldg(x + (size_t)c * p.ld));
+            }
         } else {
 #pragma unroll
-            for (int j = 0; j < KB; ++j) acc[j] = fma(amp, (double)__ldg(xc + j), acc[j]);
-        }
-    };
-
-    int si = 0;
-    for (uint32_t t = lane; t < total; t += 32) {
-        while (pre[wib][si + 1] <= t) ++si;  // t ascends: the shape only moves forward
-        const uint32_t u = t - pre[wib][si];
-        const uint32_t l1 = lb[wib][si];
-        const uint32_t ua = u / l1, ub = u - ua * l1;
-        const uint32_t s0 = sa[wib][si], s1 = sb[wib][si];
-        const uint32_t ia2 = s0 == kKeepHalf ? ia : __ldg(f.nbrA + s0 + ua);
-        const uint32_t ib2 = s1 == kKeepHalf ? ib : __ldg(f.nbrB + s1 + ub);
-        const uint64_t Fa = a ^ __ldg(f.A + ia2), Fb = b ^ __ldg(f.B + ib2);
-        const uint32_t r0 = bits_rank(Fa, binom), r1 = bits_rank(Fb, binom);
-        const int32_t g = __ldg(e.dense + e.dbase[si] + r0 * e.dstride[si] + r1);
-        if (g < 0) continue;
-        const double amp = scan_amp<W>(p, g, key);
-        if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
-        add(amp, (uint64_t)ib2 * f.nA + ia2);
-    }
-    // groups outside the excitation index: evaluated and looked up per row
-    if (e.n_rest > 0) {
-        const uint64_t hr = key_hash<W>(key, p.nib);
-        for (int64_t i = lane; i < e.n_rest; i += 32) {
-            const int64_t g = __ldg(e.rest_gid + i);
-            const double amp = scan_amp<W>(p, g, key);
-            if (((uint64_t)__double_as_longlong(amp) << 1) == 0ull) continue;
-            uint64_t c[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) c[w] = key[w] ^ __ldg(p.gF + (size_t)w * p.G + g);
-            const int64_t idx = probe<W>(c, hr ^ __ldg(&p.grec[g].hF), p.hv, p.err);
-            if (idx >= 0) add(amp, (uint64_t)idx);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < KB; ++j) {
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            if (PREC == QSD_FP32_DOT2) {
-                const float s2 = __shfl_xor_sync(0xffffffffu, as[j], o);
-                const float e2 = __shfl_xor_sync(0xffffffffu, ae[j], o);
-                dot2_merge(as[j], ae[j], s2, e2);
-            } else {
-                acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+            for (int i = 0; i < KB; ++i) {
+                const int src = i * NC + lane / KB;
+                const double a = __shfl_sync(0xffffffffu, amp, src);
+                const uint32_t c = __shfl_sync(0xffffffffu, col, src);
+                if (((uint64_t)__double_as_longlong(a) << 1) != 0ull) {
+                    const TIO xv = __ldg(x + (size_t)c * p.ld);
+                    if (PREC == QSD_FP32_MIXED) acc = fma(a, f32_to_f64((float)xv), acc);
+                    else acc = fma(a, (double)xv, acc);
+                }
             }
         }
     }
-    if (lane == 0) {
+    // lanes with the same column (lane % KB) hold parts of its sum
+#pragma unroll
+    for (int o = KB; o < 32; o <<= 1) {
+        if (PREC == QSD_FP32_DOT2) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, as, o);
+            const float e2 = __shfl_xor_sync(0xffffffffu, ae, o);
+            dot2_merge(as, ae, s2, e2);
+        } else {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
+    }
+    if (lane < KB) {
         const double d = __ldg(p.diag + row);
-        const TIO *xr = x + row * p.ld + p.col0;
-        TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0;
+        const TIO xr = __ldg(x + row * p.ld);
+        TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0 + lane;
         if (PREC == QSD_FP32_DOT2) {
             const float dh = (float)d, dl = (float)(d - (double)dh);
-#pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
-                yr[j] = (TIO)(as[j] + ae[j]);
-            }
+            dot2_add(as, ae, dh, dl, (float)xr);
+            *yr = (TIO)(as + ae);
         } else {
-#pragma unroll
-            for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
+            *yr = (TIO)fma(d, (double)xr, acc);
         }
     }
 }

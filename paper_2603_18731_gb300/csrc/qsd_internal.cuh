@@ -106,7 +106,8 @@ struct CsrState {
 struct qsd_ctx_s {
     int device = 0;
     int tune_mode = 0;    // product path: 0 auto, 1 group scan, 2 excitation index, 3 half evaluation,
-                          // 4 sector-factored where it applies (else auto)
+                          // 4 sector-factored where it applies (else auto), 5 filter/verify scan
+                          // where it applies (else auto)
     int tune_lanes = 0;   // lanes per row of the group scan: 0 auto, 1 or 8
     int allow_sym = 0;    // the autotuner may pick the half-evaluation product
     int row_order = 0;    // lane-per-row scans: 0 auto, 1 index order, 2 hash order
@@ -137,14 +138,17 @@ namespace qsd {
 // for a = A[ia], b = B[ib].  Per half list, each string's neighbours in the
 // same list by excitation type: the other strings reached by turning dOcc of
 // its set bits off and dEmp of its clear bits on (0 <= dOcc, dEmp <= 2, not
-// both 0), type t = 3 dOcc + dEmp - 1, ascending by index.
+// both 0), type t = 3 dOcc + dEmp - 1, ascending by index.  An entry is
+// (index j, meta) with meta = rank of the flipped positions F = L[i] ^ L[j]
+// in the combinatorial number system (bits 0-19), L[i]'s bits on them in
+// ascending order (bits 20-23) and popc(F) (bits 24-26).
 struct Factored {
     bool ok = false;
     int split = 0;
     int64_t nA = 0, nB = 0;
     DevBuf A, B;        // uint64 [nA], [nB]: distinct halves, ascending
     DevBuf ptrA, ptrB;  // uint32 [8 n + 1]: start of (string i, type t) at 8 i + t
-    DevBuf nbrA, nbrB;  // uint32: neighbour indices
+    DevBuf nbrA, nbrB;  // uint2: (neighbour index, meta)
     int64_t nnzA = 0, nnzB = 0;
 };
 }  // namespace qsd
@@ -209,6 +213,8 @@ struct qsd_op_s {
     qsd::DevBuf tphi;    // double [T] real phase * coefficient
     qsd::DevBuf tphi_im; // double [T]
     qsd::DevBuf tflag;   // uint8  [T] bit0: P != 0, bit1: Z != 0
+    qsd::DevBuf trec;    // TermRec<W> [T]: P, V, Z, fixed-point phase (W <= 2, excitation index built)
+    double qscale = 1.0; // value of one fixed-point unit of trec
     qsd::DevBuf gmsob;   // uint16 [G] most significant flipped qubit (built by the first CSR call)
     // diagonal terms (Td)
     int64_t Td = 0;
