@@ -198,6 +198,7 @@ ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag,
     p.amp = op->amp.as<double>();
     p.ampf = op->ampf.as<float2>();
     p.n_amp = op->n_amp;
+    p.table_const = op->max_table_size == 1 ? 1 : 0;
     p.gF = op->gF.as<uint64_t>();
     p.grange = op->grange.as<int32_t>();
     p.gL = op->gL.as<uint8_t>();
@@ -267,9 +268,11 @@ FacParams make_fac(qsd_op op, qsd_sub sub) {
 void launch_path(int path, const ApplyParams &p, const ExcParams &e, const FacParams &f, int W, int precision,
                  int KB, cudaStream_t stream) {
     if (path == 8) {
-        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, (int)p.n_amp, W, p.num_sms, stream);
-        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, (int)p.n_amp, W, p.num_sms, stream);
-        else launch_apply_fv<QSD_FP32_DOT2>(p, (int)p.n_amp, W, p.num_sms, stream);
+        const int na = (int)p.n_amp;
+        const bool c = p.table_const != 0;
+        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, na, W, c, p.num_sms, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, na, W, c, p.num_sms, stream);
+        else launch_apply_fv<QSD_FP32_DOT2>(p, na, W, c, p.num_sms, stream);
         return;
     }
     if (path == 7) {

@@ -39,48 +39,116 @@ constexpr int kFvThreads = 256;
 constexpr int kFvWarps = kFvThreads / 32;
 constexpr int kFvU = 4;             // groups per filter batch (bucket loads in flight per lane)
 
-struct FvRec {
-    uint32_t hhi;     // high word of h(F)
-    uint32_t tagnb;   // bits 0-7: low byte of h(F); bits 8-10: support size nb
-    uint32_t aoff;    // first amplitude of the group
-    uint32_t nzmask;  // bit l: the amplitude of pattern l is nonzero
-    uint64_t pos;     // support qubits, 12 bits each, ascending
-};
-static_assert(sizeof(FvRec) == 24, "24-byte staged group record");
+__host__ __device__ inline int64_t fv_padded_groups(int64_t G) { return (G + kFvU - 1) / kFvU * kFvU; }
 
-// Shared memory: records, amplitudes (8 bytes each: FP64, or the FP32 (hi,
-// lo) pair of DOT2), then per warp a ring of kFvRing candidates as three
+// Shared memory: per (padded) group a 16-byte record {high word of h(F), low
+// byte of h(F), nonzero-pattern mask, first amplitude} and its 8-byte support
+// (qubits, 12 bits each); the amplitudes (8 bytes each: FP64, or the FP32
+// (hi, lo) pair of DOT2); then per warp a ring of kFvRing candidates as three
 // uint32 arrays: bucket; meta = owner lane (bits 0-4), bucket overflowed (bit
 // 5), tag matches (bits 6-13), group (bits 14-31); amplitude index (bits
-// 0-23) and tag (bits 24-31).
+// 0-23) and tag (bits 24-31).  Padding groups have an empty mask.
 inline size_t fv_smem_bytes(int64_t G, int64_t n_amp) {
-    return (size_t)G * sizeof(FvRec) + (size_t)n_amp * 8 + (size_t)kFvWarps * kFvRing * 12;
+    return (size_t)fv_padded_groups(G) * 24 + (size_t)n_amp * 8 + (size_t)kFvWarps * kFvRing * 12;
 }
 
-template <int W, int PREC>
+struct FvRing {
+    uint32_t *b, *m, *a;
+};
+
+// Verify the n (1..32) oldest queued candidates of the warp (one per lane)
+// and deliver the found (element, x) pairs to their owner lanes in queue
+// order; the same operations as the one-pass scan's accumulation.
+template <int W, int PREC, typename TIO>
+__device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q, uint32_t head, int n, int lane,
+                                          const uint64_t (&key)[W], const double *amp, const float2 *ampf,
+                                          const TIO *__restrict__ x, double &acc, float &as, float &ae) {
+    const uint32_t slot = (head + (uint32_t)lane) & (kFvRing - 1);
+    const bool mine = lane < n;
+    const uint32_t meta = mine ? q.m[slot] : 0u;
+    const uint32_t b = mine ? q.b[slot] : 0u;
+    const uint32_t at = mine ? q.a[slot] : 0u;
+    const int o = (int)(meta & 31u);
+    uint64_t c[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) c[w] = __shfl_sync(0xffffffffu, key[w], o);
+    bool found = false;
+    TIO xv = TIO(0);
+    double a = 0.0;
+    float ah = 0.f, al = 0.f;
+    if (mine) {
+        const int64_t g = (int64_t)(meta >> 14);
+#pragma unroll
+        for (int w = 0; w < W; ++w) c[w] ^= __ldg(p.gF + (size_t)w * p.G + g);
+        int64_t idx = verify_matches_x<W, TIO>(p.hv, b, (meta >> 6) & 0xffu, c, x + p.col0, p.ld, xv);
+        if (idx < 0 && (meta & 32u)) {
+            idx = probe_from<W>(p.hv, b, at >> 24, c, p.err);
+            if (idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
+        }
+        found = idx >= 0;
+        const uint32_t ai = at & 0xffffffu;
+        if (PREC == QSD_FP32_DOT2) {
+            const float2 f = ampf[ai];
+            ah = f.x;
+            al = f.y;
+        } else {
+            a = amp[ai];
+        }
+    }
+    const uint32_t tagged = (uint32_t)o | (found ? 32u : 0u);
+    const uint32_t me = (uint32_t)lane | 32u;
+    for (int t = 0; t < n; ++t) {
+        const uint32_t ot = __shfl_sync(0xffffffffu, tagged, t);
+        const TIO xt = __shfl_sync(0xffffffffu, xv, t);
+        if (PREC == QSD_FP32_DOT2) {
+            const float aht = __shfl_sync(0xffffffffu, ah, t);
+            const float alt = __shfl_sync(0xffffffffu, al, t);
+            if (ot == me) dot2_add(as, ae, aht, alt, (float)xt);
+        } else {
+            const double at_ = __shfl_sync(0xffffffffu, a, t);
+            if (ot == me) acc = fma(at_, (double)xt, acc);
+        }
+    }
+}
+
+// The row's bits on a group's support (nb <= 5 qubits, 12 bits each in pos).
+template <int W>
+__device__ __forceinline__ uint32_t fv_pattern(uint64_t pos, uint32_t nb, const uint64_t (&key)[W]) {
+    uint32_t l = 0;
+    for (uint32_t i = 0; i < nb; ++i) l |= bit_of<W>(key, (int)((pos >> (12 * i)) & 0xfff)) << i;
+    return l;
+}
+
+// CONST: every group's element is one constant (no support bits, e.g. X
+// flips), so the filter reads no row bits.
+template <int W, int PREC, bool CONST>
 __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, int n_amp, int64_t tiles) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
     const int G = (int)p.G;
-    FvRec *rec = reinterpret_cast<FvRec *>(fv_smem);
-    double *amp = reinterpret_cast<double *>(fv_smem + (size_t)G * sizeof(FvRec));
+    const int Gp = (int)fv_padded_groups(p.G);
+    uint4 *recA = reinterpret_cast<uint4 *>(fv_smem);
+    uint64_t *recB = reinterpret_cast<uint64_t *>(fv_smem + (size_t)Gp * 16);
+    double *amp = reinterpret_cast<double *>(fv_smem + (size_t)Gp * 24);
     float2 *ampf = reinterpret_cast<float2 *>(amp);
-    uint32_t *ring = reinterpret_cast<uint32_t *>(fv_smem + (size_t)G * sizeof(FvRec) + (size_t)n_amp * 8);
+    uint32_t *ring = reinterpret_cast<uint32_t *>(fv_smem + (size_t)Gp * 24 + (size_t)n_amp * 8);
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *q_b = ring + (size_t)wib * kFvRing * 3;
-    uint32_t *q_m = q_b + kFvRing;
-    uint32_t *q_a = q_m + kFvRing;
+    FvRing q;
+    q.b = ring + (size_t)wib * kFvRing * 3;
+    q.m = q.b + kFvRing;
+    q.a = q.m + kFvRing;
 
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(p.grec + g));
-        const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(p.grec + g) + 1);
-        FvRec R;
-        R.hhi = (uint32_t)(r0.x >> 32);
-        R.tagnb = ((uint32_t)r0.x & 0xffu) | ((r1.y & 7u) << 8);
-        R.aoff = r1.x;
-        R.nzmask = r1.z;
-        R.pos = r0.y;
-        rec[g] = R;
+    for (int g = threadIdx.x; g < Gp; g += blockDim.x) {
+        uint4 A = make_uint4(0u, 0u, 0u, 0u);
+        uint64_t B = 0;
+        if (g < G) {
+            const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(p.grec + g));
+            const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(p.grec + g) + 1);
+            A = make_uint4((uint32_t)(r0.x >> 32), ((uint32_t)r0.x & 0xffu) | ((r1.y & 7u) << 8), r1.z, r1.x);
+            B = r0.y;
+        }
+        recA[g] = A;
+        recB[g] = B;
     }
     if (PREC == QSD_FP32_DOT2) {
         for (int i = threadIdx.x; i < n_amp; i += blockDim.x) ampf[i] = __ldg(p.ampf + i);
@@ -90,6 +158,7 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
     __syncthreads();
 
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
+    const uint2 *__restrict__ tags = reinterpret_cast<const uint2 *>(p.hv.tags);
     const uint32_t bshift = (uint32_t)p.hv.shift - 32u;
     const uint32_t lt = (1u << lane) - 1u;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -101,108 +170,58 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         for (int w = 0; w < W; ++w) key[w] = __ldg(p.hkeys + (size_t)w * p.D + pc);
         const uint64_t hr = __ldg(p.hhash + pc);
         const uint32_t hr_hi = (uint32_t)(hr >> 32), hr_lo = (uint32_t)hr & 0xffu;
+        // an inactive lane (past the last row) needs no group: its mask bit
+        // is taken from an empty pattern range
+        const uint32_t live = active ? 0xffffffffu : 0u;
         double acc = 0.0;
         float as = 0.f, ae = 0.f;
         uint32_t head = 0, tail = 0;  // warp-uniform ring positions
 
-        // verify the n (1..32) oldest candidates, deliver them in queue order
-        auto verify = [&](int n) {
-            const uint32_t slot = (head + (uint32_t)lane) & (kFvRing - 1);
-            const bool mine = lane < n;
-            const uint32_t meta = mine ? q_m[slot] : 0u;
-            const uint32_t b = mine ? q_b[slot] : 0u;
-            const uint32_t at = mine ? q_a[slot] : 0u;
-            const int o = (int)(meta & 31u);
-            uint64_t c[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) c[w] = __shfl_sync(0xffffffffu, key[w], o);
-            bool found = false;
-            TIO xv = TIO(0);
-            double a = 0.0;
-            float ah = 0.f, al = 0.f;
-            if (mine) {
-                const int64_t g = (int64_t)(meta >> 14);
-#pragma unroll
-                for (int w = 0; w < W; ++w) c[w] ^= __ldg(p.gF + (size_t)w * p.G + g);
-                int64_t idx = verify_matches_x<W, TIO>(p.hv, b, (meta >> 6) & 0xffu, c, x + p.col0, p.ld, xv);
-                if (idx < 0 && (meta & 32u)) {
-                    idx = probe_from<W>(p.hv, b, at >> 24, c, p.err);
-                    if (idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
-                }
-                found = idx >= 0;
-                const uint32_t ai = at & 0xffffffu;
-                if (PREC == QSD_FP32_DOT2) {
-                    const float2 f = ampf[ai];
-                    ah = f.x;
-                    al = f.y;
-                } else {
-                    a = amp[ai];
-                }
-            }
-            const uint32_t tagged = (uint32_t)o | (found ? 32u : 0u);
-            for (int t = 0; t < n; ++t) {
-                const uint32_t ot = __shfl_sync(0xffffffffu, tagged, t);
-                const TIO xt = __shfl_sync(0xffffffffu, xv, t);
-                if (PREC == QSD_FP32_DOT2) {
-                    const float aht = __shfl_sync(0xffffffffu, ah, t);
-                    const float alt = __shfl_sync(0xffffffffu, al, t);
-                    if (ot == ((uint32_t)lane | 32u)) dot2_add(as, ae, aht, alt, (float)xt);
-                } else {
-                    const double at_ = __shfl_sync(0xffffffffu, a, t);
-                    if (ot == ((uint32_t)lane | 32u)) acc = fma(at_, (double)xt, acc);
-                }
-            }
-            head += (uint32_t)n;
-        };
-
-        for (int g0 = 0; g0 < G; g0 += kFvU) {
+        for (int g0 = 0; g0 < Gp; g0 += kFvU) {
+            // phase 1: every group's bucket load in flight (tags and tag
+            // bytes kept; bucket, pattern and amplitude index are recomputed
+            // for the rare candidates)
             uint2 tb[kFvU];
-            uint32_t bk[kFvU], tg[kFvU], ai[kFvU];
-            bool need[kFvU];
+            uint32_t tg[kFvU];
+            uint32_t needm = 0;
 #pragma unroll
             for (int u = 0; u < kFvU; ++u) {
-                const int g = g0 + u;
-                need[u] = false;
-                if (g < G) {  // warp-uniform
-                    const FvRec R = rec[g];
-                    const int nb = (int)((R.tagnb >> 8) & 7u);
-                    int l = 0;
-                    for (int i = 0; i < nb; ++i) l |= (int)bit_of<W>(key, (int)((R.pos >> (12 * i)) & 0xfff)) << i;
-                    need[u] = active && ((R.nzmask >> l) & 1u);
-                    ai[u] = R.aoff + (uint32_t)l;
-                    const uint32_t t = (hr_lo ^ R.tagnb) & 0xffu;
-                    tg[u] = t ? t : 1u;
-                    bk[u] = (hr_hi ^ R.hhi) >> bshift;
-                    if (need[u]) tb[u] = __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + bk[u]);
-                }
+                const uint4 R = recA[g0 + u];
+                uint32_t l = 0;
+                if (!CONST) l = fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
+                const uint32_t need = ((R.z & live) >> l) & 1u;
+                const uint32_t t = (hr_lo ^ R.y) & 0xffu;
+                tg[u] = t ? t : 1u;
+                if (need) tb[u] = __ldg(tags + ((hr_hi ^ R.x) >> bshift));
+                needm |= need << u;
             }
+            // phase 2: misses end here; candidates enter the ring in group order
 #pragma unroll
             for (int u = 0; u < kFvU; ++u) {
-                bool cand = false;
-                uint32_t match = 0, full = 0;
-                if (need[u]) {
-                    full = bucket_full(tb[u]) ? 1u : 0u;
-                    cand = full || tag_any(tb[u], tg[u]);
-                }
+                const bool cand = ((needm >> u) & 1u) && (bucket_full(tb[u]) || tag_any(tb[u], tg[u]));
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 if (bal == 0u) continue;  // warp-uniform: every lookup of the group missed
                 if (cand) {
-                    match = tag_match(tb[u], tg[u]);
+                    const uint4 R = recA[g0 + u];
+                    const uint32_t l = CONST ? 0u : fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
+                    const uint32_t full = bucket_full(tb[u]) ? 1u : 0u;
+                    const uint32_t match = tag_match(tb[u], tg[u]);
                     const uint32_t slot = (tail + (uint32_t)__popc(bal & lt)) & (kFvRing - 1);
-                    q_b[slot] = bk[u];
-                    q_m[slot] = (uint32_t)lane | (full << 5) | (match << 6) | ((uint32_t)(g0 + u) << 14);
-                    q_a[slot] = ai[u] | (tg[u] << 24);
+                    q.b[slot] = (hr_hi ^ R.x) >> bshift;
+                    q.m[slot] = (uint32_t)lane | (full << 5) | (match << 6) | ((uint32_t)(g0 + u) << 14);
+                    q.a[slot] = (R.w + l) | (tg[u] << 24);
                 }
                 tail += (uint32_t)__popc(bal);
                 __syncwarp();
                 if (tail - head >= 32u) {
-                    verify(32);
+                    fv_verify<W, PREC, TIO>(p, q, head, 32, lane, key, amp, ampf, x, acc, as, ae);
+                    head += 32u;
                     __syncwarp();
                 }
             }
         }
         __syncwarp();
-        if (tail != head) verify((int)(tail - head));
+        if (tail != head) fv_verify<W, PREC, TIO>(p, q, head, (int)(tail - head), lane, key, amp, ampf, x, acc, as, ae);
         __syncwarp();
         if (active) {
             const int64_t r = (int64_t)__ldg(p.hperm + pc);
@@ -222,8 +241,8 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
 
 // Launch the filter/verify product for precision mode PREC (W <= 4, k = 1,
 // hash order, every group a table group, G <= kFvMaxGroups, n_amp <=
-// kFvMaxAmps).
+// kFvMaxAmps); constant: every group's element is one constant.
 template <int PREC>
-void launch_apply_fv(const ApplyParams &p, int n_amp, int W, int num_sms, cudaStream_t s);
+void launch_apply_fv(const ApplyParams &p, int n_amp, int W, bool constant, int num_sms, cudaStream_t s);
 
 }  // namespace qsd

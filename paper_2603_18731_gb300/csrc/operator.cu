@@ -666,7 +666,11 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
             QSD_CUDA(cudaMemcpyAsync(hsz.data(), size.p, (size_t)G * 4, cudaMemcpyDeviceToHost, s));
             QSD_CUDA(cudaStreamSynchronize(s));
             op->n_table_groups = 0;
-            for (auto v : hsz) op->n_table_groups += v > 0;
+            op->max_table_size = 0;
+            for (auto v : hsz) {
+                op->n_table_groups += v > 0;
+                op->max_table_size = std::max<int64_t>(op->max_table_size, v);
+            }
         }
         op->host_groups.resize((size_t)G * W);
         std::vector<uint64_t> gsoa((size_t)G * W);
