@@ -198,7 +198,9 @@ ApplyParams make_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag,
     p.amp = op->amp.as<double>();
     p.ampf = op->ampf.as<float2>();
     p.n_amp = op->n_amp;
-    p.table_const = op->max_table_size == 1 ? 1 : 0;
+    p.table_nb = -1;
+    if (op->min_table_size == op->max_table_size && op->max_table_size == 1) p.table_nb = 0;
+    if (op->min_table_size == op->max_table_size && op->max_table_size == 4 && op->n_qubits <= 256) p.table_nb = 2;
     p.gF = op->gF.as<uint64_t>();
     p.grange = op->grange.as<int32_t>();
     p.gL = op->gL.as<uint8_t>();
@@ -269,10 +271,10 @@ void launch_path(int path, const ApplyParams &p, const ExcParams &e, const FacPa
                  int KB, cudaStream_t stream) {
     if (path == 8) {
         const int na = (int)p.n_amp;
-        const bool c = p.table_const != 0;
-        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, na, W, c, p.num_sms, stream);
-        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, na, W, c, p.num_sms, stream);
-        else launch_apply_fv<QSD_FP32_DOT2>(p, na, W, c, p.num_sms, stream);
+        const int nb = p.table_nb;
+        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, na, W, nb, p.num_sms, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, na, W, nb, p.num_sms, stream);
+        else launch_apply_fv<QSD_FP32_DOT2>(p, na, W, nb, p.num_sms, stream);
         return;
     }
     if (path == 7) {

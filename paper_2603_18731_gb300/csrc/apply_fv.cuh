@@ -119,9 +119,17 @@ __device__ __forceinline__ uint32_t fv_pattern(uint64_t pos, uint32_t nb, const 
     return l;
 }
 
-// CONST: every group's element is one constant (no support bits, e.g. X
-// flips), so the filter reads no row bits.
-template <int W, int PREC, bool CONST>
+// The row's bits on a two-qubit support whose qubits sit in bits 16-23 and
+// 24-31 of y.
+template <int W>
+__device__ __forceinline__ uint32_t fv_pattern2(uint32_t y, const uint64_t (&key)[W]) {
+    return bit_of<W>(key, (int)((y >> 16) & 0xffu)) | (bit_of<W>(key, (int)(y >> 24)) << 1);
+}
+
+// NB: the support size of every group when fixed (0: one constant element,
+// e.g. X flips, so the filter reads no row bits; 2: e.g. flip-flop bonds),
+// or -1 (read per group).
+template <int W, int PREC, int NB>
 __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, int n_amp, int64_t tiles) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
@@ -144,7 +152,12 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         if (g < G) {
             const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(p.grec + g));
             const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(p.grec + g) + 1);
-            A = make_uint4((uint32_t)(r0.x >> 32), ((uint32_t)r0.x & 0xffu) | ((r1.y & 7u) << 8), r1.z, r1.x);
+            // y: tag byte, support size (bits 8-10), first two support qubits
+            // (bits 16-23, 24-31; n <= 256)
+            A = make_uint4((uint32_t)(r0.x >> 32),
+                           ((uint32_t)r0.x & 0xffu) | ((r1.y & 7u) << 8) | (((uint32_t)r0.y & 0xffu) << 16) |
+                               ((((uint32_t)(r0.y >> 12)) & 0xffu) << 24),
+                           r1.z, r1.x);
             B = r0.y;
         }
         recA[g] = A;
@@ -188,7 +201,8 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
             for (int u = 0; u < kFvU; ++u) {
                 const uint4 R = recA[g0 + u];
                 uint32_t l = 0;
-                if (!CONST) l = fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
+                if (NB == 2) l = fv_pattern2<W>(R.y, key);
+                else if (NB < 0) l = fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
                 const uint32_t need = ((R.z & live) >> l) & 1u;
                 const uint32_t t = (hr_lo ^ R.y) & 0xffu;
                 tg[u] = t ? t : 1u;
@@ -203,7 +217,9 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
                 if (bal == 0u) continue;  // warp-uniform: every lookup of the group missed
                 if (cand) {
                     const uint4 R = recA[g0 + u];
-                    const uint32_t l = CONST ? 0u : fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
+                    const uint32_t l = NB == 0 ? 0u
+                                       : NB == 2 ? fv_pattern2<W>(R.y, key)
+                                                 : fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
                     const uint32_t full = bucket_full(tb[u]) ? 1u : 0u;
                     const uint32_t match = tag_match(tb[u], tg[u]);
                     const uint32_t slot = (tail + (uint32_t)__popc(bal & lt)) & (kFvRing - 1);
@@ -241,8 +257,9 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
 
 // Launch the filter/verify product for precision mode PREC (W <= 4, k = 1,
 // hash order, every group a table group, G <= kFvMaxGroups, n_amp <=
-// kFvMaxAmps); constant: every group's element is one constant.
+// kFvMaxAmps); nb: the support size of every group when fixed (0 or 2), else
+// -1.
 template <int PREC>
-void launch_apply_fv(const ApplyParams &p, int n_amp, int W, bool constant, int num_sms, cudaStream_t s);
+void launch_apply_fv(const ApplyParams &p, int n_amp, int W, int nb, int num_sms, cudaStream_t s);
 
 }  // namespace qsd

@@ -15,33 +15,34 @@ namespace qsd {
 namespace {
 constexpr int kPrec = QSD_PREC;
 
-template <int W, bool CONST>
+template <int W, int NB>
 void launch_wc(const ApplyParams &p, int n_amp, int num_sms, cudaStream_t s) {
     const size_t smem = fv_smem_bytes(p.G, n_amp);
     const int64_t tiles = (p.D + kFvThreads - 1) / kFvThreads;
     int per_sm = 0;
-    QSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_fv<W, kPrec, CONST>, kFvThreads, smem));
+    QSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_fv<W, kPrec, NB>, kFvThreads, smem));
     const int64_t blocks = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * num_sms);
-    k_apply_fv<W, kPrec, CONST><<<(unsigned)blocks, kFvThreads, smem, s>>>(p, n_amp, tiles);
+    k_apply_fv<W, kPrec, NB><<<(unsigned)blocks, kFvThreads, smem, s>>>(p, n_amp, tiles);
 }
 
 template <int W>
-void launch_w(const ApplyParams &p, int n_amp, bool constant, int num_sms, cudaStream_t s) {
-    if (constant) launch_wc<W, true>(p, n_amp, num_sms, s);
-    else launch_wc<W, false>(p, n_amp, num_sms, s);
+void launch_w(const ApplyParams &p, int n_amp, int nb, int num_sms, cudaStream_t s) {
+    if (nb == 0) launch_wc<W, 0>(p, n_amp, num_sms, s);
+    else if (nb == 2) launch_wc<W, 2>(p, n_amp, num_sms, s);
+    else launch_wc<W, -1>(p, n_amp, num_sms, s);
 }
 }  // namespace
 
 template <>
-void launch_apply_fv<kPrec>(const ApplyParams &p, int n_amp, int W, bool constant, int num_sms, cudaStream_t s) {
+void launch_apply_fv<kPrec>(const ApplyParams &p, int n_amp, int W, int nb, int num_sms, cudaStream_t s) {
     if (p.D <= 0) return;
     if (p.G < 1 || p.G > kFvMaxGroups || n_amp > kFvMaxAmps || !p.hperm || fv_smem_bytes(p.G, n_amp) > 48 * 1024)
         fail(QSD_ERR_INTERNAL, "filter/verify product: operator or subspace outside its limits");
     switch (W) {
-    case 1: launch_w<1>(p, n_amp, constant, num_sms, s); break;
-    case 2: launch_w<2>(p, n_amp, constant, num_sms, s); break;
-    case 3: launch_w<3>(p, n_amp, constant, num_sms, s); break;
-    case 4: launch_w<4>(p, n_amp, constant, num_sms, s); break;
+    case 1: launch_w<1>(p, n_amp, nb, num_sms, s); break;
+    case 2: launch_w<2>(p, n_amp, nb, num_sms, s); break;
+    case 3: launch_w<3>(p, n_amp, nb, num_sms, s); break;
+    case 4: launch_w<4>(p, n_amp, nb, num_sms, s); break;
     default: fail(QSD_ERR_INTERNAL, "filter/verify product: W > 4");
     }
     QSD_LAUNCH_CHECK();

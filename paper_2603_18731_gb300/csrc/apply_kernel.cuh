@@ -65,7 +65,7 @@ struct ApplyParams {
     const double *amp;       // table amplitudes
     const float2 *ampf;      // the same split into FP32 (hi, lo)
     int64_t n_amp;           // number of table amplitudes
-    int table_const;         // every table group's element is one constant (support size 0)
+    int table_nb;            // support size shared by every group (0: constant elements), or -1
     const uint64_t *gF;      // [W][G]
     const int32_t *grange;   // [G+1]
     const uint8_t *gL;       // [G]

@@ -667,9 +667,11 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
             QSD_CUDA(cudaStreamSynchronize(s));
             op->n_table_groups = 0;
             op->max_table_size = 0;
+            op->min_table_size = G > 0 ? (int64_t)1 << 62 : 0;
             for (auto v : hsz) {
                 op->n_table_groups += v > 0;
                 op->max_table_size = std::max<int64_t>(op->max_table_size, v);
+                op->min_table_size = std::min<int64_t>(op->min_table_size, v);
             }
         }
         op->host_groups.resize((size_t)G * W);

@@ -191,7 +191,8 @@ struct qsd_op_s {
     qsd::DevBuf amp;     // double [n_amp] matrix element per support pattern (table groups)
     qsd::DevBuf ampf;    // float2 [n_amp] the same split into FP32 (hi, lo)
     int64_t n_amp = 0, n_table_groups = 0;
-    int64_t max_table_size = 0;  // largest amplitude table (2^support size) of a table group
+    int64_t max_table_size = 0;  // largest amplitude table (2^support size) of a group (0: scan group)
+    int64_t min_table_size = 0;  // smallest
     // excitation index of the ladder groups (fermionic operators)
     bool exc_ok = false;
     int exc_split = 0, n_shapes = 0;

@@ -48,6 +48,11 @@ def case(kind):
         return wl.ising_heavy_hex(200, seed=4), wl.flip_subspace(200, 50_003, max_flips=20, seed=5)
     if kind == "xxz":
         return wl.xxz_square(6, 6, 0.5, 1.0), wl.xxz_walk_subspace(6, 6, count=40_000, max_len=12, seed=3)
+    if kind == "mixed":
+        # single-qubit flips (constant elements) and flip-flop bonds (two-qubit
+        # supports): the per-group support size is read at run time
+        op = wl.ising_heavy_hex(36, seed=3) + wl.xxz_square(6, 6, 0.5, 1.0)
+        return op, wl.xxz_walk_subspace(6, 6, count=20_000, max_len=12, seed=4)
     if kind == "tiny":
         return wl.ising_heavy_hex(30, seed=2), wl.flip_subspace(30, 20, max_flips=3, seed=2)
     raise ValueError(kind)
@@ -71,7 +76,7 @@ def forced(ctx, h, sub, x, prec, path):
         ctx.set_tuning(5, 0)
 
 
-@pytest.mark.parametrize("kind", ["ising60", "ising200", "xxz", "tiny"])
+@pytest.mark.parametrize("kind", ["ising60", "ising200", "xxz", "mixed", "tiny"])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_filter_verify_equals_scan_and_oracle(ctx, kind, prec):
     import torch
