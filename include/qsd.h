@@ -486,6 +486,14 @@ int qsd_lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub,
                              const qsd_lanczos_params *p, double *energy,
                              double *vec_out, qsd_lanczos_info *info);
 
+/* Failure injection for tests (the paper has no counterpart): the next n
+ * device allocations of the library, in any context or thread, fail with
+ * QSD_ERR_OOM as if the device were out of memory, without calling CUDA; 0
+ * cancels what is left.  The call that meets the failure returns
+ * QSD_ERR_OOM and leaves its context usable.  Errors: QSD_ERR_INVALID_ARG
+ * (n < 0). */
+int qsd_inject_alloc_failures(int64_t n);
+
 /* --------------------------------------------------------------- serving */
 /* Continuous-batching ground-state server (the served loop of the build
  * target; the paper runs one eigensolve at a time).  One scheduler thread

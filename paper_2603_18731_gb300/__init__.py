@@ -98,6 +98,7 @@ SIGNATURES = [
     ("qsd_free_op", C.c_int, [_P]),
     ("qsd_build_subspace", C.c_int, [_P, _I32, _I64, _P, C.c_int, C.POINTER(_P), C.POINTER(_I64)]),
     ("qsd_subspace_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
+    ("qsd_inject_alloc_failures", C.c_int, [_I64]),
     ("qsd_subspace_factored", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
                                         C.POINTER(_I64)]),
     ("qsd_subspace_keys", C.c_int, [_P, _P, _P, C.c_int]),

@@ -1,6 +1,7 @@
 // C ABI entry points (include/qsd.h): argument checks, handle management,
 // error translation, and the host side of the product dispatch.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -23,9 +24,22 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
                           std::to_string(line) + ")");
 }
 
+// Test hook: the next g_fail_allocs device allocations fail as if the
+// device were out of memory (no CUDA call is made for them).
+static std::atomic<int64_t> g_fail_allocs{0};
+
+static bool injected_failure() {
+    int64_t n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 void DevBuf::alloc(size_t n) {
     release();
     if (n == 0) return;
+    if (injected_failure())
+        throw Error(QSD_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed: injected failure");
     const cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -38,6 +52,8 @@ void DevBuf::alloc(size_t n) {
 void DevBuf::alloc_async(size_t n, cudaStream_t s) {
     release();
     if (n == 0) return;
+    if (injected_failure())
+        throw Error(QSD_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed: injected failure");
     const cudaError_t e = cudaMallocAsync(&p, n, s);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -521,6 +537,12 @@ int qsd_destroy(qsd_ctx ctx) {
 }
 
 const char *qsd_last_error(qsd_ctx ctx) { return ctx ? ctx->last_error.c_str() : g_thread_error.c_str(); }
+
+int qsd_inject_alloc_failures(int64_t n) {
+    if (n < 0) return QSD_ERR_INVALID_ARG;
+    g_fail_allocs.store(n);
+    return QSD_OK;
+}
 
 int qsd_load_operator(qsd_ctx ctx, int32_t n_qubits, int64_t n_terms, const int64_t *term_ptr,
                       const int32_t *op_qubit, const uint8_t *op_code, const double *coef_re,
