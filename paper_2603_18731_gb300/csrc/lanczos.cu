@@ -69,25 +69,50 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
 // arguments, so that a packed launch (below) can run the same arithmetic for
 // several jobs in one grid.
 
-// partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j
+// partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j.
+// The vectors are taken kGemvBatch at a time: each thread keeps one partial
+// sum per vector of the batch, and one block reduction (shuffles, then the
+// warps' sums in warp order) serves the whole batch -- a fixed order, so the
+// result is deterministic.  sh holds (blockDim.x / 32) * kGemvBatch doubles.
+constexpr int kGemvBatch = 8;
+constexpr int kGemvSh = (kLanczosThreads / 32) * kGemvBatch;
+
 template <typename TV, typename TU>
 __device__ void gemv_t_body(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u,
                             double *partial, int vb, int B, double *sh) {
     const int64_t chunk = (D + B - 1) / B;
     const int64_t r0 = (int64_t)vb * chunk, r1 = min(D, r0 + chunk);
-    for (int i = 0; i < nvec; ++i) {
-        const TV *vi = V + (size_t)i * D;
-        double s = 0.0;
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) s = fma((double)vi[r], (double)u[r], s);
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) partial[(size_t)i * B + vb] = s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i0 = 0; i0 < nvec; i0 += kGemvBatch) {
+        const int nb = min(kGemvBatch, nvec - i0);
+        double s[kGemvBatch];
+#pragma unroll
+        for (int k = 0; k < kGemvBatch; ++k) s[k] = 0.0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const double ur = (double)u[r];
+#pragma unroll
+            for (int k = 0; k < kGemvBatch; ++k)
+                if (k < nb) s[k] = fma((double)V[(size_t)(i0 + k) * D + r], ur, s[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kGemvBatch; ++k) {
+            s[k] = warp_sum(s[k]);
+            if (lane == 0) sh[warp * kGemvBatch + k] = s[k];
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w * kGemvBatch + threadIdx.x];
+            partial[(size_t)(i0 + threadIdx.x) * B + vb] = t;
+        }
+        __syncthreads();
     }
 }
 
 template <typename TV, typename TU>
 __global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
                          const TU *__restrict__ u, double *partial) {
-    __shared__ double sh[32];
+    __shared__ double sh[kGemvSh];
     gemv_t_body<TV, TU>(V, D, *jdev + 1, u, partial, blockIdx.x, gridDim.x, sh);
 }
 
@@ -240,7 +265,6 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
     if (m <= 0) return;
     double *a = sm, *b = sm + m, *s = sm + 2 * m;
     __shared__ double lo_hi[2];
-    __shared__ int cnt[kLanczosThreads];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         a[i] = alpha[i];
         b[i] = i ? beta[i] : 0.0;
@@ -258,22 +282,23 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
         lo_hi[1] = hi + pad;
     }
     __syncthreads();
-    // multisection: each thread tests one of blockDim.x interior points
+    // multisection: each thread tests one of blockDim.x interior points; the
+    // Sturm count is monotone in x, so the number of points with no
+    // eigenvalue below them is the index of the subinterval that holds the
+    // lowest one.  Stop at a few ulps, or when rounding stops the shrinking.
     for (int it = 0; it < 64; ++it) {
         const double lo = lo_hi[0], hi = lo_hi[1];
         const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(blockDim.x + 1);
-        cnt[threadIdx.x] = sturm(a, b, m, x);
+        const int k = __syncthreads_count(sturm(a, b, m, x) < 1);
+        const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(blockDim.x + 1);
+        const double nhi = k == (int)blockDim.x ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(blockDim.x + 1);
         __syncthreads();
         if (threadIdx.x == 0) {
-            int k = 0;
-            while (k < (int)blockDim.x && cnt[k] < 1) ++k;
-            const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(blockDim.x + 1);
-            const double nhi = k == (int)blockDim.x ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(blockDim.x + 1);
             lo_hi[0] = nlo;
             lo_hi[1] = nhi;
         }
         __syncthreads();
-        if (lo_hi[1] - lo_hi[0] <= 4e-16 * fmax(fabs(lo_hi[0]), fabs(lo_hi[1])) + 1e-300) break;
+        if (nhi - nlo <= 4e-16 * fmax(fabs(nlo), fabs(nhi)) + 1e-300 || (nlo == lo && nhi == hi)) break;
     }
     if (threadIdx.x != 0) return;
     const double theta = 0.5 * (lo_hi[0] + lo_hi[1]);
@@ -387,7 +412,7 @@ __device__ __forceinline__ int find_job(const int *__restrict__ first, int n, in
 // which = 0: u = hv (type TV); 1: u = w (double)
 template <typename TV, typename TU>
 __global__ void kp_gemv_t(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n, int which) {
-    __shared__ double sh[32];
+    __shared__ double sh[kGemvSh];
     const int i = find_job(first, n, blockIdx.x);
     const PackJob &J = jobs[i];
     const int j = *J.jdev;
