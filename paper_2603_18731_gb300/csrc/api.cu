@@ -264,7 +264,9 @@ FacParams make_fac(qsd_op op, qsd_sub sub) {
     const Factored &f = sub->fac;
     FacParams r{};
     r.trec = op->trec.p;
+    r.trec64 = op->trec64.p;
     r.qscale = op->qscale;
+    r.qexp = op->qexp;
     r.A = f.A.as<uint64_t>();
     r.B = f.B.as<uint64_t>();
     r.ptrA = f.ptrA.as<uint32_t>();

@@ -66,7 +66,9 @@ __global__ void k_term_records(int64_t T, const uint64_t *__restrict__ tP, const
         r.V[w] = tV[(size_t)w * T + t];
         r.Z[w] = tZ[(size_t)w * T + t];
     }
-    r.q = __double2ll_rn(tphi[t] * scale);  // scale is a power of two: the product is exact
+    // scale > 0: fixed point (a power of two: the product is exact); 0: the
+    // FP64 phase's bits
+    r.q = scale > 0.0 ? __double2ll_rn(tphi[t] * scale) : __double_as_longlong(tphi[t]);
     out[t] = r;
 }
 
@@ -208,15 +210,21 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op) {
         const int ex = fixed_point_exponent(phi, gr);
         const double scale = std::ldexp(1.0, ex);
         op->qscale = std::ldexp(1.0, -ex);
+        op->qexp = ex;
         op->trec.alloc((size_t)T * rb);
-        if (W == 1)
-            k_term_records<1><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
-                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
-                                                                 op->trec.as<TermRec<1>>());
-        else
-            k_term_records<2><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
-                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
-                                                                 op->trec.as<TermRec<2>>());
+        op->trec64.alloc((size_t)T * rb);
+        for (int pass = 0; pass < 2; ++pass) {
+            DevBuf &dst = pass ? op->trec64 : op->trec;
+            const double sc = pass ? 0.0 : scale;
+            if (W == 1)
+                k_term_records<1><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                     op->tZ.as<uint64_t>(), op->tphi.as<double>(), sc,
+                                                                     dst.as<TermRec<1>>());
+            else
+                k_term_records<2><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                     op->tZ.as<uint64_t>(), op->tphi.as<double>(), sc,
+                                                                     dst.as<TermRec<2>>());
+        }
         QSD_LAUNCH_CHECK();
         QSD_CUDA(cudaStreamSynchronize(s));
     }

@@ -25,11 +25,12 @@ struct ExcParams {
     uint32_t shapes[kMaxShapes];
 };
 
-// The masks of one term and its phase in 64-bit fixed point, side by side
-// (whole 16-byte loads), for the factored product (W <= 2): q = phi 2^e
-// rounded to an integer, with one exponent e per operator chosen so that any
-// group's sum of |q| stays below 2^62 (the operator's qscale = 2^-e).  A sum
-// of terms is then an exact integer sum, converted to FP64 once.
+// The masks of one term and its phase side by side (whole 16-byte loads), for
+// the factored product (W <= 2).  Two arrays: in one, q is the phase in
+// 64-bit fixed point, q = phi 2^e rounded to an integer, with one exponent e
+// per operator chosen so that any group's sum of |q| stays below 2^62 (a sum
+// of terms is then an exact integer sum, converted to FP64 once); in the
+// other, q holds the bits of the FP64 phase.
 template <int W> struct TermRec;
 template <> struct alignas(16) TermRec<1> {
     uint64_t P[1], V[1], Z[1];

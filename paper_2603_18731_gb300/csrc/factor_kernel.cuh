@@ -16,12 +16,15 @@
 // column ib' |A| + ia': no lookup.  Groups outside the excitation index are
 // evaluated and looked up per row.
 //
-// Work split: the warp evaluates 32 candidates at a time, one per lane; then
-// the (element, column) pairs are broadcast by shuffles and the block's KB
-// columns of x are gathered by KB lanes per candidate (32 / KB candidates per
-// load instruction: one coalesced row of x each), each lane accumulating one
-// column.  Lanes holding the same column are reduced with shuffles at the
-// end.  Every order is fixed: the result is deterministic.
+// Work split: the warp evaluates 32 candidates at a time, one per lane; the
+// found (element, column) pairs are compacted in shared memory in candidate
+// order, and the block's KB columns of x are gathered by KB lanes per
+// candidate (32 / KB candidates per load instruction: one coalesced row of x
+// each), each lane accumulating one column.  Lanes holding the same column
+// are reduced with shuffles at the end.  Every order is fixed: the result is
+// deterministic.  Element sums and their conversion run on the integer
+// pipes: the FP64 pipe (1/64 of the FP32 rate on GB300) is left to the
+// accumulation's FMAs, k per found column.
 #pragma once
 
 #include "excite.cuh"
@@ -32,8 +35,10 @@ struct FacParams {
     const uint64_t *A, *B;        // distinct halves
     const uint32_t *ptrA, *ptrB;  // [8 n + 1] neighbour list starts by (string, type)
     const uint2 *nbrA, *nbrB;     // (neighbour index, rank | pattern << 20 | bits << 24)
-    const void *trec;             // TermRec<W> [T]
-    double qscale;                // value of one fixed-point unit of the term phases
+    const void *trec;             // TermRec<W> [T], fixed-point phases
+    const void *trec64;           // TermRec<W> [T], the same with the FP64 phases' bits in q
+    double qscale;                // value of one fixed-point unit of the term phases, 2^-qexp
+    int qexp;
     uint32_t nA, nB;
     int split;
 };
@@ -46,16 +51,18 @@ __device__ __forceinline__ int shape_type(uint32_t occ, uint32_t emp) {
 
 constexpr uint32_t kKeepHalf = 0xffffffffu;
 
-// Element of group g at the row from the terms [b, e) of its ladder range,
-// in fixed-point units: each term's projector test (the ladder bits already
-// match) and sign, summed exactly in 64-bit integers.  The FP64 pipe of the
-// GB300 runs at 1/64 of the FP32 rate and the lanes' term loops diverge, so
-// per-term FP64 adds took a third of it; the integer sum costs ALU slots
-// only, and its one conversion to FP64 per candidate is exact to within the
-// rounding of each phase to a multiple of 2^-e.
+// Element of group g at the row from the terms [b, e) of its ladder range:
+// each term's projector test (the ladder bits already match) and sign.
+// Two forms.  Fixed point (block products with FP64 accumulation, which
+// saturate the FP64 pipe -- 1/64 of the FP32 rate on GB300 -- with their k
+// FMAs per found column): the terms' phases in 64-bit fixed point, summed
+// exactly in integers and converted once by integer operations, exact to
+// within the rounding of each phase to a multiple of 2^-e.  FP64 adds
+// (single-column and DOT2 products, whose FP64 pipe has room): fewer
+// instructions per term than the 64-bit integer sum.
 template <int W>
-__device__ __forceinline__ int64_t ladder_terms(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
-                                                const uint64_t (&key)[W]) {
+__device__ __forceinline__ int64_t ladder_terms_fixed(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
+                                                      const uint64_t (&key)[W]) {
     int64_t sum = 0;
     for (int32_t t = b; t < e; ++t) {
         const TermRec<W> r = load_term<W>(tr + t);
@@ -72,6 +79,51 @@ __device__ __forceinline__ int64_t ladder_terms(const TermRec<W> *__restrict__ t
     return sum;
 }
 
+template <int W>
+__device__ __forceinline__ double ladder_terms_fp64(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
+                                                    const uint64_t (&key)[W]) {
+    double amp = 0.0;
+    for (int32_t t = b; t < e; ++t) {
+        const TermRec<W> r = load_term<W>(tr + t);
+        bool ok = true;
+        int par = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            ok &= (key[w] & r.P[w]) == r.V[w];
+            par ^= __popcll(key[w] & r.Z[w]);
+        }
+        const double ph = __longlong_as_double(r.q);  // this array holds the FP64 phases
+        if (ok) amp += (par & 1) ? -ph : ph;
+    }
+    return amp;
+}
+
+// v * 2^-ex rounded to the nearest double (ties to even), by integer
+// operations on the IEEE-754 encoding: the 53 leading bits of |v| become the
+// significand (the bits below decide the rounding), the exponent is the
+// position of the leading bit minus ex.  Results below the normal range take
+// the hardware conversion.  Keeps the conversion off the FP64 pipe, which
+// the accumulation of the found columns saturates.
+__device__ __forceinline__ double scaled_i64_to_f64(int64_t v, int ex) {
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? (1ull << 63) : 0ull;
+    const uint64_t u = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+    const int lz = __clzll((long long)u);
+    const int e = 63 - lz - ex;  // |v| 2^-ex lies in [2^e, 2^(e+1))
+    if (e < -1022) return __ll2double_rn(v) * exp2((double)-ex);
+    const uint64_t m = u << lz;  // leading one at bit 63
+    uint64_t mant = (m >> 11) & ((1ull << 52) - 1);
+    const uint64_t rest = m & 0x7ffull;
+    const uint64_t up = (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    mant += up;
+    int eb = e + 1023;
+    if (mant >> 52) {  // the rounding carried into the next binade
+        mant = 0;
+        ++eb;
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)eb << 52) | mant));
+}
+
 template <int W, int KB, int PREC>
 __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const ExcParams e, const FacParams f) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
@@ -79,6 +131,9 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     constexpr int NC = 32 / KB;  // candidates per gather instruction
     __shared__ uint32_t pre[8][kMaxShapes + 1];  // per warp: first candidate of each shape
     __shared__ uint32_t sa[8][kMaxShapes], sb[8][kMaxShapes], lb[8][kMaxShapes];
+    // per warp: the found candidates of the current round, compacted
+    __shared__ double camp[8][32];
+    __shared__ uint32_t ccol[8][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= p.D) return;  // warp-uniform
@@ -86,7 +141,9 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
-    const TermRec<W> *__restrict__ trec = static_cast<const TermRec<W> *>(f.trec);
+    // fixed-point element sums where the FP64 pipe is the bottleneck
+    constexpr bool kFixed = PREC != QSD_FP32_DOT2 && KB > 1;
+    const TermRec<W> *__restrict__ trec = static_cast<const TermRec<W> *>(kFixed ? f.trec : f.trec64);
     // lane s < n_shapes: the candidate lists of shape s and their product size
     uint32_t cnt = 0;
     if (lane < e.n_shapes) {
@@ -150,8 +207,8 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
                     tb = __ldg(p.grange + g);
                     te = __ldg(p.grange + g + 1);
                 }
-                const int64_t qs = ladder_terms<W>(trec, tb, te, key);
-                if (qs != 0) amp = __ll2double_rn(qs) * f.qscale;
+                if (kFixed) amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
+                else amp = ladder_terms_fp64<W>(trec, tb, te, key);
                 col = nB.x * f.nA + nA.x;
             }
         } else if (t < total) {
@@ -168,12 +225,29 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
                 }
             }
         }
-        // 2. gather: KB lanes per candidate, NC candidates per instruction
+        // 2. gather
         const bool nz = ((uint64_t)__double_as_longlong(amp) << 1) != 0ull;
-        const uint32_t any = __ballot_sync(0xffffffffu, nz);
-        if (!any) continue;
+        if (KB == 1) {
+            // each lane its own candidate
+            if (nz) {
+                const TIO xv = __ldg(x + (size_t)col * p.ld);
+                if (PREC == QSD_FP32_DOT2) {
+                    const float ah = (float)amp, al = (float)(amp - (double)ah);
+                    dot2_add(as, ae, ah, al, (float)xv);
+                } else if (PREC == QSD_FP32_MIXED) {
+                    acc = fma(amp, f32_to_f64((float)xv), acc);
+                } else {
+                    acc = fma(amp, (double)xv, acc);
+                }
+            }
+            continue;
+        }
+        const uint32_t found = __ballot_sync(0xffffffffu, nz);
+        if (!found) continue;
         if (PREC == QSD_FP32_DOT2) {
-            // the element's FP32 (hi, lo) split once, in the candidate's lane
+            // KB lanes per candidate, NC candidates per load instruction: the
+            // element's FP32 (hi, lo) split once, in the candidate's lane, and
+            // broadcast by shuffles
             const float ah = (float)amp, al = (float)(amp - (double)ah);
 #pragma unroll
             for (int i = 0; i < KB; ++i) {
@@ -183,19 +257,27 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
                 const uint32_t c = __shfl_sync(0xffffffffu, col, src);
                 if (h != 0.f || l != 0.f) dot2_add(as, ae, h, l, (float)__ldg(x + (size_t)c * p.ld));
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < KB; ++i) {
-                const int src = i * NC + lane / KB;
-                const double a = __shfl_sync(0xffffffffu, amp, src);
-                const uint32_t c = __shfl_sync(0xffffffffu, col, src);
-                if (((uint64_t)__double_as_longlong(a) << 1) != 0ull) {
-                    const TIO xv = __ldg(x + (size_t)c * p.ld);
-                    if (PREC == QSD_FP32_MIXED) acc = fma(a, f32_to_f64((float)xv), acc);
-                    else acc = fma(a, (double)xv, acc);
-                }
+            continue;
+        }
+        // FP64 accumulation: the found candidates compacted in candidate
+        // order, KB lanes per candidate and NC candidates per load
+        // instruction, so that every FP64 FMA runs at full lanes but the last
+        if (nz) {
+            const int slot = __popc(found & ((1u << lane) - 1u));
+            camp[wib][slot] = amp;
+            ccol[wib][slot] = col;
+        }
+        __syncwarp();
+        const int nf = __popc(found);
+        for (int i0 = 0; i0 < nf; i0 += NC) {
+            const int src = i0 + lane / KB;
+            if (src < nf) {
+                const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
+                if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
+                else acc = fma(camp[wib][src], (double)xv, acc);
             }
         }
+        __syncwarp();
     }
     // lanes with the same column (lane % KB) hold parts of its sum
 #pragma unroll

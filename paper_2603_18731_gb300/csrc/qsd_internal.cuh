@@ -216,7 +216,9 @@ struct qsd_op_s {
     qsd::DevBuf tphi_im; // double [T]
     qsd::DevBuf tflag;   // uint8  [T] bit0: P != 0, bit1: Z != 0
     qsd::DevBuf trec;    // TermRec<W> [T]: P, V, Z, fixed-point phase (W <= 2, excitation index built)
-    double qscale = 1.0; // value of one fixed-point unit of trec
+    qsd::DevBuf trec64;  // TermRec<W> [T]: P, V, Z and the FP64 phase's bits
+    double qscale = 1.0; // value of one fixed-point unit of trec, 2^-qexp
+    int qexp = 0;
     qsd::DevBuf gmsob;   // uint16 [G] most significant flipped qubit (built by the first CSR call)
     // diagonal terms (Td)
     int64_t Td = 0;
