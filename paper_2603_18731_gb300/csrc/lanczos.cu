@@ -29,6 +29,16 @@
 
 namespace qsd {
 
+// Row blocks of the dot passes: about 1024 rows per block (four rows per
+// thread per vector) for large subspaces, at most four blocks per SM; small
+// subspaces keep at least min(D / 256, 2 per SM) blocks (measured on GB300:
+// XXZ 300,000 rows 304 blocks, Ising 1 M rows 608, TFIM 4096 rows 16).
+int dot_blocks(int64_t D, int num_sms) {
+    const int64_t by_rows = (D + 1023) / 1024;
+    const int64_t floor_blocks = std::min<int64_t>((D + 255) / 256, 2 * (int64_t)num_sms);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)num_sms, std::max(by_rows, floor_blocks)));
+}
+
 namespace {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -70,44 +80,33 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
 // several jobs in one grid.
 
 // partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j.
-// The vectors are taken kGemvBatch at a time: each thread keeps one partial
-// sum per vector of the batch, and one block reduction (shuffles, then the
-// warps' sums in warp order) serves the whole batch -- a fixed order, so the
-// result is deterministic.  sh holds (blockDim.x / 32) * kGemvBatch doubles.
-constexpr int kGemvBatch = 8;
-constexpr int kGemvSh = (kLanczosThreads / 32) * kGemvBatch;
-
+// Warp w of the block takes the vectors i = w, w + 8, ...: its lanes stride
+// the block's rows (coalesced; the block's slice of u stays in L1 across the
+// vectors), four loads in flight per lane, and one warp reduction per vector
+// -- no block barrier.  A fixed order: the result is deterministic.
 template <typename TV, typename TU>
 __device__ void gemv_t_body(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u,
                             double *partial, int vb, int B, double *sh) {
+    (void)sh;
     const int64_t chunk = (D + B - 1) / B;
     const int64_t r0 = (int64_t)vb * chunk, r1 = min(D, r0 + chunk);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i0 = 0; i0 < nvec; i0 += kGemvBatch) {
-        const int nb = min(kGemvBatch, nvec - i0);
-        double s[kGemvBatch];
-#pragma unroll
-        for (int k = 0; k < kGemvBatch; ++k) s[k] = 0.0;
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const double ur = (double)u[r];
-#pragma unroll
-            for (int k = 0; k < kGemvBatch; ++k)
-                if (k < nb) s[k] = fma((double)V[(size_t)(i0 + k) * D + r], ur, s[k]);
+    for (int i = warp; i < nvec; i += nw) {
+        const TV *__restrict__ vi = V + (size_t)i * D;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t r = r0 + lane;
+        for (; r + 96 < r1; r += 128) {
+            s0 = fma((double)vi[r], (double)u[r], s0);
+            s1 = fma((double)vi[r + 32], (double)u[r + 32], s1);
+            s2 = fma((double)vi[r + 64], (double)u[r + 64], s2);
+            s3 = fma((double)vi[r + 96], (double)u[r + 96], s3);
         }
-#pragma unroll
-        for (int k = 0; k < kGemvBatch; ++k) {
-            s[k] = warp_sum(s[k]);
-            if (lane == 0) sh[warp * kGemvBatch + k] = s[k];
-        }
-        __syncthreads();
-        if (threadIdx.x < nb) {
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += sh[w * kGemvBatch + threadIdx.x];
-            partial[(size_t)(i0 + threadIdx.x) * B + vb] = t;
-        }
-        __syncthreads();
+        for (; r < r1; r += 32) s0 = fma((double)vi[r], (double)u[r], s0);
+        const double t = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) partial[(size_t)i * B + vb] = t;
     }
 }
+constexpr int kGemvSh = 32;
 
 template <typename TV, typename TU>
 __global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
@@ -203,6 +202,52 @@ __global__ void k_next(const double *__restrict__ w, const double *__restrict__ 
 
 __global__ void k_incr(int *jdev) { *jdev += 1; }
 
+// ---- fused tail of one step (single-job path)
+// The second Gram-Schmidt subtraction also sums w^2 per 256-row block
+// (k_sub_sq), and every block of k_norm_next sums those partials itself (in
+// block order, so all agree) before writing v_{j+1} = w / beta_{j+1}: 8
+// launches per step instead of 11, with the subtraction's full grid.
+
+// w[r] -= sum_{i<=j} V[i][r] h[i]; part[b] = sum over the block's rows of w^2
+template <typename TV>
+__global__ void k_sub_sq(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
+                         const double *__restrict__ h, double *w, double *part) {
+    extern __shared__ double hs[];
+    __shared__ double sh[32];
+    const int nvec = *jdev + 1;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (r < D) {
+        double acc = w[r];
+        for (int i = 0; i < nvec; ++i) acc = fma(-(double)V[(size_t)i * D + r], hs[i], acc);
+        w[r] = acc;
+        sq = acc * acc;
+    }
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = sq;
+}
+
+template <typename TV>
+__global__ void k_norm_next(const double *__restrict__ w, const double *__restrict__ part, int B,
+                            const int *__restrict__ jdev, int64_t D, int m, TV *V, TV *vcur, double *beta) {
+    __shared__ double sh[32];
+    __shared__ double nrm;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) t += part[b];
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) nrm = sqrt(t);
+    __syncthreads();
+    const int j1 = *jdev + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) beta[j1] = nrm;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x) {
+        const TV v = (TV)(nrm > 0.0 ? w[r] / nrm : 0.0);
+        if (j1 <= m) V[(size_t)j1 * D + r] = v;
+        vcur[r] = v;
+    }
+}
+
 __global__ void k_scale(double *u, const double *__restrict__ nrm, int64_t D) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= D) return;
@@ -236,14 +281,32 @@ __global__ void k_residual(const double *__restrict__ hu, const double *__restri
 }
 
 // ------------------------------------------------------------- tridiagonal
-// Number of eigenvalues of T (diagonal a[0..m), off-diagonal b[1..m)) below x.
+// Number of eigenvalues of T (diagonal a[0..m), off-diagonal b[1..m)) below
+// x: the sign changes of the Sturm sequence p_0 = 1, p_k = det(T_k - x I) =
+// (a_k - x) p_{k-1} - b_k^2 p_{k-2} (a zero takes the sign opposite to its
+// predecessor).  No division: the GB300's FP64 pipe runs at 1/64 of the FP32
+// rate and a division costs several of its operations; the pair (p_{k-1},
+// p_k) is rescaled by 2^-600 whenever it grows past 2^600, and by 2^600 when
+// both fall below 2^-600 (exact scalings that keep every sign).
 __device__ int sturm(const double *a, const double *b, int m, double x) {
     int c = 0;
-    double q = 1.0;
-    for (int i = 0; i < m; ++i) {
-        q = a[i] - x - (i ? b[i] * b[i] / q : 0.0);
-        if (q == 0.0) q = -1e-300;
-        c += q < 0.0;
+    double p0 = 1.0, p1 = a[0] - x;
+    bool neg = p1 < 0.0 || (p1 == 0.0);  // p_1 of sign opposite to p_0 = 1
+    c += neg;
+    for (int i = 1; i < m; ++i) {
+        double p2 = fma(a[i] - x, p1, -(b[i] * b[i]) * p0);
+        if (fabs(p2) > 0x1p600 || fabs(p1) > 0x1p600) {
+            p2 *= 0x1p-600;
+            p1 *= 0x1p-600;
+        } else if (fabs(p2) < 0x1p-600 && fabs(p1) < 0x1p-600) {
+            p2 *= 0x1p600;
+            p1 *= 0x1p600;
+        }
+        const bool prev_neg = neg;
+        neg = p2 < 0.0 || (p2 == 0.0 && !prev_neg);
+        c += (neg != prev_neg);
+        p0 = p1;
+        p1 = p2;
     }
     return c;
 }
@@ -282,16 +345,21 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
         lo_hi[1] = hi + pad;
     }
     __syncthreads();
-    // multisection: each thread tests one of blockDim.x interior points; the
-    // Sturm count is monotone in x, so the number of points with no
+    // multisection: the first kTriPoints threads test one interior point
+    // each; the Sturm count is monotone in x, so the number of points with no
     // eigenvalue below them is the index of the subinterval that holds the
     // lowest one.  Stop at a few ulps, or when rounding stops the shrinking.
+    constexpr int kTriPoints = 64;
     for (int it = 0; it < 64; ++it) {
         const double lo = lo_hi[0], hi = lo_hi[1];
-        const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(blockDim.x + 1);
-        const int k = __syncthreads_count(sturm(a, b, m, x) < 1);
-        const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(blockDim.x + 1);
-        const double nhi = k == (int)blockDim.x ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(blockDim.x + 1);
+        bool below = false;
+        if (threadIdx.x < kTriPoints) {
+            const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(kTriPoints + 1);
+            below = sturm(a, b, m, x) < 1;
+        }
+        const int k = __syncthreads_count(below);
+        const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(kTriPoints + 1);
+        const double nhi = k == kTriPoints ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(kTriPoints + 1);
         __syncthreads();
         if (threadIdx.x == 0) {
             lo_hi[0] = nlo;
@@ -628,7 +696,7 @@ void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int prod
     m = (int)std::min<int64_t>(std::min(steps, kLanczosMaxSteps), D);
     check_every = std::max(1, std::min(check, m));
     s = st;
-    B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
+    B = dot_blocks(D, ctx->num_sms);
     nbD = blocks_for(D, 256);
     const size_t sv = fp32 ? 4 : 8;
     auto A = [&](DevBuf &b, size_t n) {
@@ -640,7 +708,7 @@ void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int prod
     A(hv, (size_t)D * sv);
     A(w, (size_t)D * 8);
     A(h, (size_t)(m + 2) * 8);
-    A(part, (size_t)(m + 2) * B * 8);
+    A(part, ((size_t)(m + 2) * B + nbD) * 8);
     A(alpha, (size_t)(m + 2) * 8);
     A(beta, (size_t)(m + 3) * 8);
     A(tri, (size_t)(m + 8) * 8);
@@ -650,9 +718,10 @@ void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int prod
 
 size_t LanczosJob::footprint(int64_t D, int steps, bool fp32, int num_sms) {
     const int m = (int)std::min<int64_t>(std::min(steps, kLanczosMaxSteps), D);
-    const int B = std::max(1, std::min<int>(2 * num_sms, (int)((D + 255) / 256)));
+    const int B = dot_blocks(D, num_sms);
     const size_t sv = fp32 ? 4 : 8;
-    return (size_t)(m + 3) * D * sv + (size_t)D * 8 + (size_t)(m + 2) * B * 8 + (size_t)(m + 16) * 40;
+    return (size_t)(m + 3) * D * sv + (size_t)D * 8 + ((size_t)(m + 2) * B + (D + 255) / 256) * 8 +
+           (size_t)(m + 16) * 40;
 }
 
 template <typename TV>
@@ -675,6 +744,8 @@ void LanczosJob::enqueue_start(const double *start, uint64_t seed) {
     else enqueue_start_t<double>(*this, start, seed);
 }
 
+static int ctx_sms(qsd_ctx c) { return c->num_sms; }
+
 template <typename TV>
 static void enqueue_steps_t(LanczosJob &J, int n) {
     cudaStream_t s = J.s;
@@ -683,6 +754,9 @@ static void enqueue_steps_t(LanczosJob &J, int n) {
     double *alpha = J.alpha.as<double>(), *beta = J.beta.as<double>();
     const int *j = J.jdev.as<int>();
     const size_t hsm = (size_t)(J.m + 1) * 8;
+    // squares of w per 256-row block after the partial dots
+    double *psq = part + (size_t)(J.m + 2) * J.B;
+    const int nb = std::min<int>(J.nbD, 4 * ctx_sms(J.ctx));
     for (int t = 0; t < n; ++t) {
         apply_H(J.ctx, J.op, J.sub, J.diag, J.prec, 1, vc, hv, s);
         k_gemv_t<TV, TV><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, hv, part);
@@ -690,10 +764,8 @@ static void enqueue_steps_t(LanczosJob &J, int n) {
         k_gemv_sub<TV, TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, hv, w);
         k_gemv_t<TV, double><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, w, part);
         k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
-        k_gemv_sub<TV, double><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, w);
-        k_sq_partial<<<J.B, kLanczosThreads, 0, s>>>(w, J.D, part);
-        k_sqrt_sum<<<1, kLanczosThreads, 0, s>>>(part, J.B, beta, j);
-        k_next<TV><<<J.nbD, 256, 0, s>>>(w, beta, j, J.D, J.m, V, vc);
+        k_sub_sq<TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, psq);
+        k_norm_next<TV><<<nb, 256, 0, s>>>(w, psq, J.nbD, j, J.D, J.m, V, vc, beta);
         k_incr<<<1, 1, 0, s>>>(J.jdev.as<int>());
     }
     k_tridiag<<<1, kLanczosThreads, tri_smem(J.m), s>>>(alpha, beta, j, J.tri.as<double>());
@@ -762,7 +834,7 @@ void ResidJob::init(qsd_ctx c, int64_t Dn, cudaStream_t st, bool stream_ordered)
     ctx = c;
     D = Dn;
     s = st;
-    B = std::max(1, std::min<int>(2 * ctx->num_sms, (int)((D + 255) / 256)));
+    B = dot_blocks(D, ctx->num_sms);
     if (stream_ordered) {
         hu.alloc_async((size_t)D * 8, s);
         r.alloc_async((size_t)D * 8, s);

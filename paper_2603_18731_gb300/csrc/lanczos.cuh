@@ -8,6 +8,9 @@ namespace qsd {
 constexpr int kLanczosThreads = 256;
 constexpr int kLanczosMaxSteps = 700;  // the tridiagonal CTA keeps 8 m doubles in shared memory
 
+// Row blocks of the dot passes for D rows.
+int dot_blocks(int64_t D, int num_sms);
+
 // One Lanczos run on one stream: Krylov basis, tridiagonal coefficients and a
 // device step counter.  enqueue_* only enqueue work; results of a chunk are in
 // pinned host memory once the stream has passed it.
