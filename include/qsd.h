@@ -98,6 +98,10 @@ typedef struct {
     int32_t is_real;          /* every matrix element is real */
     int32_t is_hermitian;     /* term set closed under adjoint (rel. 1e-14) */
     double identity_coef;     /* real part of the constant (empty-word) term */
+    int64_t n_linear_ranges;  /* ladder ranges tabulated as a constant plus one
+                                 coefficient per occupied qubit (single
+                                 excitations of a two-body fermionic operator;
+                                 used by the factored product) */
 } qsd_op_info;
 
 /* Load H = sum_t c_t W_t (Methods, "Qubit Hamiltonians": a term is a

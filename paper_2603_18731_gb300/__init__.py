@@ -41,7 +41,7 @@ class OpInfo(C.Structure):
                 ("n_ladder_groups", C.c_int64), ("n_excitation_groups", C.c_int64),
                 ("n_excitation_shapes", C.c_int32), ("excitation_rank_index", C.c_int32),
                 ("max_group_terms", C.c_int64), ("is_real", C.c_int32),
-                ("is_hermitian", C.c_int32), ("identity_coef", C.c_double)]
+                ("is_hermitian", C.c_int32), ("identity_coef", C.c_double), ("n_linear_ranges", C.c_int64)]
 
 
 class LanczosParams(C.Structure):

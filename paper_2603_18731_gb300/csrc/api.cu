@@ -189,7 +189,7 @@ static bool use_excitation(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
 static bool use_factored(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     if (ctx->tune_mode == 1 || ctx->tune_mode == 2 || ctx->tune_mode == 3) return false;
     return sub->fac.ok && op->exc_ok && op->dense_ok && op->W <= 2 && op->exc_split == sub->fac.split &&
-           op->trec.p != nullptr;
+           op->trec.p != nullptr && op->lin_base.p != nullptr;
 }
 
 // The filter/verify scan applies to single-column products of operators whose
@@ -267,6 +267,13 @@ FacParams make_fac(qsd_op op, qsd_sub sub) {
     r.trec64 = op->trec64.p;
     r.qscale = op->qscale;
     r.qexp = op->qexp;
+    r.lin_base = op->lin_base.as<int32_t>();
+    r.lin_z = op->lin_z.as<uint64_t>();
+    r.lin_k64 = op->lin_k64.as<double>();
+    r.lin_d64 = op->lin_d64.as<double>();
+    r.lin_kq = op->lin_kq.as<int64_t>();
+    r.lin_dq = op->lin_dq.as<int64_t>();
+    r.nq = op->n_qubits;
     r.A = f.A.as<uint64_t>();
     r.B = f.B.as<uint64_t>();
     r.ptrA = f.ptrA.as<uint32_t>();

@@ -150,6 +150,136 @@ void build_dense_index(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc) 
     op->dense_ok = true;
 }
 
+// Linear ranges.  A ladder range (group g, pattern l) whose terms each test at
+// most one qubit r outside F (a projector, value v_t) and whose Z masks all
+// equal one mask Zref except, for a term, at its own r, has an element of the
+// form
+//   s(row) * (K + sum over the row's occupied qubits r of d_r),
+//   s(row) = (-1)^popc(row & Zref),
+// with c_t = phi_t, negated when Z_t and Zref differ at r and v_t = 1 (the
+// row's bit at r is then 1); K = sum of c_t over the terms without r and over
+// those with v_t = 0; d_r = (sum of c_t with v_t = 1 at r) - (sum with
+// v_t = 0 at r).
+// Single-excitation groups of a two-body fermionic operator are of this kind:
+// a constant plus one coefficient per occupied orbital, up to the sign of the
+// Jordan-Wigner string.  Tabulated for the groups whose ranges are all linear
+// and hold at least kLinearMinTerms terms somewhere; the fixed-point table
+// sums the same integers q_t as the term loop, so it gives the same element.
+constexpr int kLinearMinTerms = 6;
+
+void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc, const std::vector<double> &phi,
+                         double scale) {
+    const int W = op->W, n = op->n_qubits;
+    const int64_t G = op->G, T = op->T;
+    cudaStream_t s = ctx->stream;
+    std::vector<uint8_t> gL((size_t)G);
+    std::vector<int32_t> gptr((size_t)G * 17);
+    std::vector<uint64_t> gF((size_t)W * G), tP((size_t)W * T), tV((size_t)W * T), tZ((size_t)W * T);
+    QSD_CUDA(cudaMemcpyAsync(gL.data(), op->gL.p, (size_t)G, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(gptr.data(), op->gptr.p, (size_t)G * 17 * 4, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(gF.data(), op->gF.p, (size_t)W * G * 8, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(tP.data(), op->tP.p, (size_t)W * T * 8, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(tV.data(), op->tV.p, (size_t)W * T * 8, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaMemcpyAsync(tZ.data(), op->tZ.p, (size_t)W * T * 8, cudaMemcpyDeviceToHost, s));
+    QSD_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> base((size_t)G, -1);
+    std::vector<uint64_t> zref;
+    std::vector<double> k64, d64;
+    std::vector<int64_t> kq, dq;
+    int64_t rows = 0;
+    auto word = [&](const std::vector<uint64_t> &a, int w, int64_t t) { return a[(size_t)w * T + t]; };
+    for (int32_t g : exc) {
+        const int L = gL[(size_t)g];
+        if (L == 0) continue;
+        const int npat = 1 << L;
+        int maxlen = 0;
+        bool linear = true;
+        // per pattern: Zref, the Z mask of a term without a projector outside
+        // F (else of the first term); every term's Z may differ from it only
+        // on the term's own projector qubit
+        std::vector<uint64_t> Z((size_t)npat * W, 0);
+        for (int l = 0; l < npat && linear; ++l) {
+            const int32_t b = gptr[(size_t)g * 17 + l], e = gptr[(size_t)g * 17 + l + 1];
+            maxlen = std::max(maxlen, (int)(e - b));
+            if (e <= b) continue;
+            int32_t tref = b;
+            for (int32_t t = b; t < e && linear; ++t) {
+                int extra = 0;
+                for (int w = 0; w < W; ++w) extra += __builtin_popcountll(word(tP, w, t) & ~gF[(size_t)w * G + g]);
+                if (extra > 1) linear = false;
+                if (extra == 0 && tref == b) tref = t;
+            }
+            for (int w = 0; w < W; ++w) Z[(size_t)l * W + w] = word(tZ, w, tref);
+            for (int32_t t = b; t < e && linear; ++t)
+                for (int w = 0; w < W; ++w) {
+                    const uint64_t own = word(tP, w, t) & ~gF[(size_t)w * G + g];
+                    if ((word(tZ, w, t) ^ Z[(size_t)l * W + w]) & ~own) linear = false;
+                }
+        }
+        if (!linear || maxlen < kLinearMinTerms) continue;
+        base[(size_t)g] = (int32_t)rows;
+        for (int l = 0; l < npat; ++l) {
+            const int32_t b = gptr[(size_t)g * 17 + l], e = gptr[(size_t)g * 17 + l + 1];
+            double K = 0.0;
+            int64_t Kq = 0;
+            std::vector<double> d((size_t)n, 0.0);
+            std::vector<int64_t> dqq((size_t)n, 0);
+            for (int32_t t = b; t < e; ++t) {
+                int r = -1;
+                bool v = false, zdiff = false;
+                for (int w = 0; w < W; ++w) {
+                    const uint64_t own = word(tP, w, t) & ~gF[(size_t)w * G + g];
+                    if (own) {
+                        r = 64 * w + __builtin_ctzll(own);
+                        v = (word(tV, w, t) & own) != 0;
+                        zdiff = ((word(tZ, w, t) ^ Z[(size_t)l * W + w]) & own) != 0;
+                    }
+                }
+                // popc(row & Z_t) = popc(row & Zref) + (Z_t xor Zref at r) * row_r, and
+                // row_r = v where the term survives
+                const bool neg = r >= 0 && v && zdiff;
+                const double c = neg ? -phi[(size_t)t] : phi[(size_t)t];
+                const int64_t q0 = std::llrint(phi[(size_t)t] * scale);
+                const int64_t cq = neg ? -q0 : q0;
+                if (r < 0) {
+                    K += c;
+                    Kq += cq;
+                } else if (v) {
+                    d[(size_t)r] += c;
+                    dqq[(size_t)r] += cq;
+                } else {
+                    K += c;
+                    Kq += cq;
+                    d[(size_t)r] -= c;
+                    dqq[(size_t)r] -= cq;
+                }
+            }
+            for (int w = 0; w < W; ++w) zref.push_back(Z[(size_t)l * W + w]);
+            k64.push_back(K);
+            kq.push_back(Kq);
+            d64.insert(d64.end(), d.begin(), d.end());
+            dq.insert(dq.end(), dqq.begin(), dqq.end());
+            ++rows;
+        }
+    }
+    op->n_lin_rows = rows;
+    op->lin_base.alloc((size_t)G * 4);
+    QSD_CUDA(cudaMemcpyAsync(op->lin_base.p, base.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
+    if (rows > 0) {
+        op->lin_z.alloc(zref.size() * 8);
+        op->lin_k64.alloc(k64.size() * 8);
+        op->lin_kq.alloc(kq.size() * 8);
+        op->lin_d64.alloc(d64.size() * 8);
+        op->lin_dq.alloc(dq.size() * 8);
+        QSD_CUDA(cudaMemcpyAsync(op->lin_z.p, zref.data(), zref.size() * 8, cudaMemcpyHostToDevice, s));
+        QSD_CUDA(cudaMemcpyAsync(op->lin_k64.p, k64.data(), k64.size() * 8, cudaMemcpyHostToDevice, s));
+        QSD_CUDA(cudaMemcpyAsync(op->lin_kq.p, kq.data(), kq.size() * 8, cudaMemcpyHostToDevice, s));
+        QSD_CUDA(cudaMemcpyAsync(op->lin_d64.p, d64.data(), d64.size() * 8, cudaMemcpyHostToDevice, s));
+        QSD_CUDA(cudaMemcpyAsync(op->lin_dq.p, dq.data(), dq.size() * 8, cudaMemcpyHostToDevice, s));
+    }
+    QSD_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace
 
 void build_excitation_index(qsd_ctx ctx, qsd_op op) {
@@ -227,6 +357,7 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op) {
         }
         QSD_LAUNCH_CHECK();
         QSD_CUDA(cudaStreamSynchronize(s));
+        build_linear_ranges(ctx, op, exc, phi, scale);
     }
     op->exc_ok = true;
 }

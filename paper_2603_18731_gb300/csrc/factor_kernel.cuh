@@ -39,6 +39,13 @@ struct FacParams {
     const void *trec64;           // TermRec<W> [T], the same with the FP64 phases' bits in q
     double qscale;                // value of one fixed-point unit of the term phases, 2^-qexp
     int qexp;
+    // linear ranges: first row per group (-1: none), per row Zref [W], K and
+    // d [nq] in FP64 and fixed point
+    const int32_t *lin_base;
+    const uint64_t *lin_z;
+    const double *lin_k64, *lin_d64;
+    const int64_t *lin_kq, *lin_dq;
+    int nq;
     uint32_t nA, nB;
     int split;
 };
@@ -134,6 +141,7 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     // per warp: the found candidates of the current round, compacted
     __shared__ double camp[8][32];
     __shared__ uint32_t ccol[8][32];
+    __shared__ uint8_t occ[8][64 * W];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= p.D) return;  // warp-uniform
@@ -177,6 +185,20 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     const uint32_t total = n_exc + (uint32_t)e.n_rest;
     const uint64_t hr = e.n_rest > 0 ? key_hash<W>(key, p.nib) : 0ull;
 
+    // the row's occupied qubits, ascending (linear ranges sum their coefficients)
+    int nocc = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t bits = (uint32_t)(key[w] >> (32 * h));
+            const bool on = (bits >> lane) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, on);
+            if (on) occ[wib][nocc + __popc(m & ((1u << lane) - 1u))] = (uint8_t)(64 * w + 32 * h + lane);
+            nocc += __popc(m);
+        }
+    }
+    __syncwarp();
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x) + p.col0 + (lane % KB);
     double acc = 0.0;
     float as = 0.f, ae = 0.f;
@@ -197,18 +219,35 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
             const int32_t g = __ldg(e.dense + e.dbase[si] + (nA.y & 0xfffffu) * e.dstride[si] + (nB.y & 0xfffffu));
             if (g >= 0) {
                 const uint32_t na = (nA.y >> 24) & 7u, nb = (nB.y >> 24) & 7u;
-                int32_t tb, te;
-                if (na + nb <= 4) {
-                    // ladder table (every indexed group is ladder-only on F)
-                    const uint32_t l = ((nA.y >> 20) & 15u) | (((nB.y >> 20) & 15u) << na);
-                    tb = __ldg(p.gptr + (size_t)g * 17 + l);
-                    te = __ldg(p.gptr + (size_t)g * 17 + l + 1);
+                const uint32_t l = ((nA.y >> 20) & 15u) | (((nB.y >> 20) & 15u) << na);
+                // the linear-table row and the ladder range, loaded together
+                const bool table = na + nb <= 4;  // ladder table (every indexed group is ladder-only on F)
+                const int32_t lb = table ? __ldg(f.lin_base + g) : -1;
+                const int32_t tb = table ? __ldg(p.gptr + (size_t)g * 17 + l) : __ldg(p.grange + g);
+                const int32_t te = table ? __ldg(p.gptr + (size_t)g * 17 + l + 1) : __ldg(p.grange + g + 1);
+                if (lb >= 0) {
+                    // a linear range: sign of the common string, K plus the
+                    // coefficients of the row's occupied qubits
+                    const int64_t lr = (int64_t)lb + l;
+                    int par = 0;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(f.lin_z + lr * W + w));
+                    if (kFixed) {
+                        const int64_t *__restrict__ dr = f.lin_dq + lr * f.nq;
+                        int64_t sum = __ldg(f.lin_kq + lr);
+                        for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
+                        amp = scaled_i64_to_f64((par & 1) ? -sum : sum, f.qexp);
+                    } else {
+                        const double *__restrict__ dr = f.lin_d64 + lr * f.nq;
+                        double sum = __ldg(f.lin_k64 + lr);
+                        for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
+                        amp = (par & 1) ? -sum : sum;
+                    }
+                } else if (kFixed) {
+                    amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
                 } else {
-                    tb = __ldg(p.grange + g);
-                    te = __ldg(p.grange + g + 1);
+                    amp = ladder_terms_fp64<W>(trec, tb, te, key);
                 }
-                if (kFixed) amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
-                else amp = ladder_terms_fp64<W>(trec, tb, te, key);
                 col = nB.x * f.nA + nA.x;
             }
         } else if (t < total) {

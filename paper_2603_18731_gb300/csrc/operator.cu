@@ -696,6 +696,7 @@ void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_
     I.n_excitation_groups = op->exc_ok ? op->G_exc : 0;
     I.n_excitation_shapes = op->exc_ok ? op->n_shapes : 0;
     I.excitation_rank_index = (op->exc_ok && op->dense_ok) ? 1 : 0;
+    I.n_linear_ranges = op->n_lin_rows;
     QSD_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -90,6 +90,9 @@ def test_chem_full_size_structure(ctx, chem):
     assert info["n_terms_in"] == op.n_terms == 1_542_656
     assert info["n_groups"] == oracle.groups(op).shape[0] == 318_928
     assert info["excitation_rank_index"] == 1
+    # the single excitations (2 spins x 496 orbital pairs, two ladder patterns
+    # each, four table rows per group) are tabulated as linear ranges
+    assert info["n_linear_ranges"] >= 4 * 2 * 496
     f = sub.factored()
     assert f["is_product"] and f["n_a"] == 1500 and f["n_b"] == 1500 and f["split"] == 32
     assert ctx.product_path(h, sub, 0, 16) == 7 and ctx.product_path(h, sub, 1, 16) == 7
