@@ -274,6 +274,7 @@ FacParams make_fac(qsd_op op, qsd_sub sub) {
     r.lin_kq = op->lin_kq.as<int64_t>();
     r.lin_dq = op->lin_dq.as<int64_t>();
     r.nq = op->n_qubits;
+    r.rix = op->range_ok ? op->rix.as<uint32_t>() : nullptr;
     r.A = f.A.as<uint64_t>();
     r.B = f.B.as<uint64_t>();
     r.ptrA = f.ptrA.as<uint32_t>();

@@ -263,6 +263,43 @@ void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc
         }
     }
     op->n_lin_rows = rows;
+    // Range index: the rank index resolved by ladder integer, one 32-bit
+    // entry per (flip mask, pattern): bit 31 set: the linear-table row in bits
+    // 0-30; else the range's first term (bits 0-20) and its length (bits
+    // 21-30; 0: no term, no group).  A candidate then finds what to evaluate
+    // with one load.  Built when every indexed group has a ladder table, the
+    // terms number below 2^21 and every range holds below 2^10 terms.
+    op->range_ok = false;
+    if (op->dense_ok && T < ((int64_t)1 << 21)) {
+        const int64_t nd = (int64_t)(op->dense.bytes / 4);
+        std::vector<int32_t> dense((size_t)nd);
+        QSD_CUDA(cudaMemcpyAsync(dense.data(), op->dense.p, (size_t)nd * 4, cudaMemcpyDeviceToHost, s));
+        QSD_CUDA(cudaStreamSynchronize(s));
+        std::vector<uint32_t> rix((size_t)nd * 16, 0u);
+        bool ok = true;
+        for (int64_t i = 0; i < nd && ok; ++i) {
+            const int32_t g = dense[(size_t)i];
+            if (g < 0) continue;
+            const int L = gL[(size_t)g];
+            if (L == 0) { ok = false; break; }
+            for (int l = 0; l < (1 << L); ++l) {
+                uint32_t v;
+                if (base[(size_t)g] >= 0) {
+                    v = 0x80000000u | (uint32_t)(base[(size_t)g] + l);
+                } else {
+                    const int32_t b = gptr[(size_t)g * 17 + l], e = gptr[(size_t)g * 17 + l + 1];
+                    if (e - b >= 1024) { ok = false; break; }
+                    v = (uint32_t)b | ((uint32_t)(e - b) << 21);
+                }
+                rix[(size_t)i * 16 + l] = v;
+            }
+        }
+        if (ok) {
+            op->rix.alloc(rix.size() * 4);
+            QSD_CUDA(cudaMemcpyAsync(op->rix.p, rix.data(), rix.size() * 4, cudaMemcpyHostToDevice, s));
+            op->range_ok = true;
+        }
+    }
     op->lin_base.alloc((size_t)G * 4);
     QSD_CUDA(cudaMemcpyAsync(op->lin_base.p, base.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
     if (rows > 0) {

@@ -46,6 +46,8 @@ struct FacParams {
     const double *lin_k64, *lin_d64;
     const int64_t *lin_kq, *lin_dq;
     int nq;
+    // range index [rank entry][16] (nullptr: rank index then group tables)
+    const uint32_t *rix;
     uint32_t nA, nB;
     int split;
 };
@@ -216,19 +218,40 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
             const uint32_t s0 = sa[wib][si], s1 = sb[wib][si];
             const uint2 nA = s0 == kKeepHalf ? make_uint2(ia, 0u) : __ldg(f.nbrA + s0 + ua);
             const uint2 nB = s1 == kKeepHalf ? make_uint2(ib, 0u) : __ldg(f.nbrB + s1 + ub);
-            const int32_t g = __ldg(e.dense + e.dbase[si] + (nA.y & 0xfffffu) * e.dstride[si] + (nB.y & 0xfffffu));
-            if (g >= 0) {
-                const uint32_t na = (nA.y >> 24) & 7u, nb = (nB.y >> 24) & 7u;
-                const uint32_t l = ((nA.y >> 20) & 15u) | (((nB.y >> 20) & 15u) << na);
-                // the linear-table row and the ladder range, loaded together
-                const bool table = na + nb <= 4;  // ladder table (every indexed group is ladder-only on F)
-                const int32_t lb = table ? __ldg(f.lin_base + g) : -1;
-                const int32_t tb = table ? __ldg(p.gptr + (size_t)g * 17 + l) : __ldg(p.grange + g);
-                const int32_t te = table ? __ldg(p.gptr + (size_t)g * 17 + l + 1) : __ldg(p.grange + g + 1);
-                if (lb >= 0) {
+            const uint32_t di = e.dbase[si] + (nA.y & 0xfffffu) * e.dstride[si] + (nB.y & 0xfffffu);
+            const uint32_t na = (nA.y >> 24) & 7u;
+            const uint32_t l = ((nA.y >> 20) & 15u) | (((nB.y >> 20) & 15u) << na);
+            // what to evaluate: a linear-table row (lr >= 0) or a term range [tb, te)
+            int64_t lr = -1;
+            int32_t tb = 0, te = 0;
+            bool found = false;
+            if (f.rix) {
+                const uint32_t v = __ldg(f.rix + (size_t)di * 16 + l);
+                if (v & 0x80000000u) {
+                    lr = (int64_t)(v & 0x7fffffffu);
+                    found = true;
+                } else {
+                    tb = (int32_t)(v & 0x1fffffu);
+                    te = tb + (int32_t)(v >> 21);
+                    found = te > tb;
+                }
+            } else {
+                const int32_t g = __ldg(e.dense + di);
+                if (g >= 0) {
+                    const uint32_t nb = (nB.y >> 24) & 7u;
+                    // the linear-table row and the ladder range, loaded together
+                    const bool table = na + nb <= 4;  // ladder table (every indexed group is ladder-only on F)
+                    const int32_t lb = table ? __ldg(f.lin_base + g) : -1;
+                    tb = table ? __ldg(p.gptr + (size_t)g * 17 + l) : __ldg(p.grange + g);
+                    te = table ? __ldg(p.gptr + (size_t)g * 17 + l + 1) : __ldg(p.grange + g + 1);
+                    if (lb >= 0) lr = (int64_t)lb + l;
+                    found = true;
+                }
+            }
+            if (found) {
+                if (lr >= 0) {
                     // a linear range: sign of the common string, K plus the
                     // coefficients of the row's occupied qubits
-                    const int64_t lr = (int64_t)lb + l;
                     int par = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(f.lin_z + lr * W + w));

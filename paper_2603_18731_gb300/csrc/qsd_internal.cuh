@@ -222,6 +222,10 @@ struct qsd_op_s {
     // and fixed point) and d [n] per qubit
     int64_t n_lin_rows = 0;
     qsd::DevBuf lin_base, lin_z, lin_k64, lin_kq, lin_d64, lin_dq;
+    // range index: uint32 [dense entries][16], the rank index resolved by
+    // ladder integer (linear-table row, or first term and length)
+    bool range_ok = false;
+    qsd::DevBuf rix;
     double qscale = 1.0; // value of one fixed-point unit of trec, 2^-qexp
     int qexp = 0;
     qsd::DevBuf gmsob;   // uint16 [G] most significant flipped qubit (built by the first CSR call)
