@@ -512,8 +512,10 @@ def run_gpu(args):
     if not args.product_only and not args.no_serve:
         serve = run_serve(args, q, local)
         if args.serve_compare:
-            other = 0 if args.serve_pack_rows else 32768
+            other = 0 if args.serve_pack_rows else 4096
             serve["compare_pack_rows_%d" % other] = run_serve(args, q, local, pack_rows=other)
+        if not args.no_pack_loop:
+            serve["packing_closed_loop"] = run_pack_loop(args, q, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu and not args.product_only:
@@ -706,13 +708,62 @@ def serve_pool(n_pool: int, seed: int, dmin: float, dmax: float):
     return pool
 
 
-def run_serve(args, q, local, pack_rows=None):
-    """512 Poisson arrivals at 0.8x the measured closed-loop capacity; latency
-    from arrival to energy ready, including the request's device build."""
+def run_pack_loop(args, q, local, slots=64, n_requests=512):
+    """Where packing pays: the solver alone in closed loop (operators loaded
+    and subspaces built beforehand; 512 requests submitted at once into 64
+    slots), with packing on (every request) and off, for subspaces of
+    1e3-4e3 rows and of 1e3-3e4 rows of the three served families."""
+    import torch
+    ctx = q.create(local)
+    params = dict(precision=q.QSD_FP32_DOT2, max_steps=300, tol=1e-7, check_every=10)
+    out = {"slots": slots, "requests": n_requests, "precision": "fp32_dot2 + fp64 refinement",
+           "note": "closed loop, solver only: subspaces built and operators loaded before the timed "
+                   "region; each configuration warmed by one pass over the pool"}
+    loaded = {}
+    for dmax in (4e3, 3e4):
+        pool = serve_pool(args.serve_pool, args.serve_seed, 1e3, dmax)
+        items = []
+        for fam, op, words in pool:
+            if id(op) not in loaded:
+                loaded[id(op)] = ctx.load_operator(op)
+            items.append((loaded[id(op)], ctx.build_subspace(op.n_qubits, words)))
+        ctx.synchronize()
+        order = np.random.default_rng(args.serve_seed).integers(0, len(items), size=n_requests).tolist()
+        res = {}
+        for rows in (0, 1 << 20):
+            with q.Server(ctx, budget_bytes=64 << 30, max_active=slots) as srv:
+                srv.set_pack_rows(rows)
+                for t in [srv.submit(h, s_, **params) for h, s_ in items]:
+                    srv.wait(t)
+                t0 = time.perf_counter()
+                tickets = [srv.submit(items[i][0], items[i][1], **params) for i in order]
+                rr = [srv.wait(t) for t in tickets]
+                wall = time.perf_counter() - t0
+                st = srv.stats()
+            lat = np.array([r["t_done"] - r["t_submit"] for r in rr]) * 1e3
+            res["packed" if rows else "unpacked"] = {
+                "solves_per_s": n_requests / wall, "ok": sum(r["status"] == "OK" for r in rr),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "packed_chunks": st["packed_chunks"]}
+        res["packed_over_unpacked"] = res["packed"]["solves_per_s"] / res["unpacked"]["solves_per_s"]
+        out["rows_1e3_%de3" % int(dmax / 1e3)] = res
+        for _, sub in items:
+            sub.free()
+    for h in loaded.values():
+        h.free()
+    ctx.close()
+    return out
+
+
+def run_serve(args, q, local, pack_rows=None, dmin=1e3, dmax=2e6, slots=None, n_requests=None):
+    """Poisson arrivals (512 by default) at 0.8x the measured closed-loop
+    capacity; latency from arrival to energy ready, including the request's
+    device build."""
     import torch
     pack_rows = args.serve_pack_rows if pack_rows is None else pack_rows
+    slots = args.serve_slots if slots is None else slots
     rng = np.random.default_rng(args.serve_seed)
-    pool = serve_pool(args.serve_pool, args.serve_seed, 1e3, 2e6)
+    pool = serve_pool(args.serve_pool, args.serve_seed, dmin, dmax)
     client = q.create(local)
     srvctx = q.create(local)
     budget = int(args.serve_budget_gb * (1 << 30))
@@ -758,14 +809,14 @@ def run_serve(args, q, local, pack_rows=None):
         wall = time.perf_counter() - start
         return res, wall
 
-    with q.Server(srvctx, budget_bytes=budget, max_active=args.serve_slots) as srv:
+    with q.Server(srvctx, budget_bytes=budget, max_active=slots) as srv:
         srv.set_pack_rows(pack_rows)
         host_t0 = time.perf_counter()
         # closed-loop capacity: every pool item submitted at once
         burst, t_burst = run(list(range(len(pool))), [0.0] * len(pool), srv, host_t0)
         capacity = len(pool) / t_burst
         lam = 0.8 * capacity
-        n = args.serve_requests
+        n = args.serve_requests if n_requests is None else n_requests
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n)).tolist()
         order = rng.integers(0, len(pool), size=n).tolist()
         res, wall = run(order, arrivals, srv, host_t0)
@@ -781,7 +832,7 @@ def run_serve(args, q, local, pack_rows=None):
     out = {"requests": n, "ok": len(ok), "rate_hz": lam, "closed_loop_capacity_solves_s": capacity,
            "solves_per_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-           "max_active": args.serve_slots, "budget_bytes": budget, "peak_bytes": st["peak_bytes"],
+           "max_active": slots, "budget_bytes": budget, "peak_bytes": st["peak_bytes"],
            "per_family_p50_ms": {k: float(np.percentile(v, 50)) for k, v in fams.items()},
            "phases": phases, "pack_rows": pack_rows,
            "packed_requests": st["packed_requests"], "packed_chunks": st["packed_chunks"],
@@ -898,8 +949,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-pack-rows", type=int, default=0,
+    ap.add_argument("--serve-pack-rows", type=int, default=4096,
                     help="requests up to this many rows run in packed chunks (0: never)")
+    ap.add_argument("--no-pack-loop", action="store_true",
+                    help="skip the closed-loop packing comparison")
     ap.add_argument("--serve-compare", action="store_true",
                     help="also run the served stream with packing switched the other way")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)

@@ -390,10 +390,15 @@ int qsd_apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, int precision, int32_t k,
 int qsd_apply_H_complex(qsd_ctx ctx, qsd_op op, qsd_sub sub, int32_t k,
                         const void *x, void *y);
 
-/* Packed products: y_i = H_S(ops[i], subs[i]) x_i for i < n in one launch per
- * key width (one grid over 256-row tiles of all pairs), for many small
- * subspaces whose single products would each fill only a few blocks.  Each
- * pair's result is bitwise that of qsd_apply_H on path QSD_PATH_SCAN_1.
+/* Packed products: y_i = H_S(ops[i], subs[i]) x_i for i < n, for many small
+ * subspaces whose single products would each fill only a few blocks.  Pairs
+ * are grouped by class -- the sector-factored product (QSD_PATH_FACTORED)
+ * where it applies to the pair, else the one-lane group scan
+ * (QSD_PATH_SCAN_1), by key width -- and each class runs as one persistent
+ * launch over a device tile queue (8-row tiles of factored pairs, 256-row
+ * tiles of scanned pairs): the resident grid claims tiles by atomic
+ * increments until they run out, with no block waiting on another.  Each
+ * pair's result is bitwise that of qsd_apply_H on its class's path.
  * xs[i], ys[i]: device [D_i][k] in the precision's storage type; all pairs
  * share precision and k; n <= 256 qubits per pair.  Asynchronous on the
  * context's stream.  The paper evaluates one subspace at a time; this is the
@@ -506,8 +511,8 @@ int qsd_inject_alloc_failures(int64_t n);
  * diagonal and work vectors; the subspace and operator tables are the
  * caller's) fits in `budget_bytes` next to the admitted ones (a request
  * larger than the budget runs alone).  Each admitted request has its own
- * stream (small requests: a shared stream and packed launches, see
- * qsd_server_set_pack_rows) and advances asynchronously -- graph-captured chunks of Lanczos
+ * stream (small requests: a shared pack stream and packed graph replays,
+ * see qsd_server_set_pack_rows) and advances asynchronously -- graph-captured chunks of Lanczos
  * steps, Ritz vector and FP64 residual, FP64 refinement restarts -- so the
  * work of all admitted requests overlaps on the device and requests that
  * arrive while others run start as soon as a slot and memory free up.
@@ -541,14 +546,21 @@ int qsd_server_cancel(qsd_server srv, uint64_t ticket);
 /* Forget a finished request (QSD_PENDING while it is not retired yet). */
 int qsd_server_release(qsd_server srv, uint64_t ticket);
 int qsd_server_get_stats(qsd_server srv, qsd_server_stats *stats);
-/* Requests with at most `rows` rows (and n <= 256 qubits) join the packs of
- * small requests: they share one stream and their Lanczos chunks run as
- * packed launches (one launch per kernel for all waiting members, the
- * product on the one-lane group scan).  0 (the default) disables packing.
- * Packed chunks are plain launches that advance every member together, so
- * they pay only when many more small requests are active than the device
- * runs concurrently; with a few slots the per-request streams replaying
- * captured graphs are faster.  Applies to requests admitted afterwards. */
+/* Requests with at most `rows` rows whose product can be packed (the
+ * sector-factored product, n <= 128 qubits, or a one-lane group scan of at
+ * most 4096 groups, n <= 256) join the pack of their product precision:
+ * their Lanczos chunks run together on the pack's stream, one CUDA-graph
+ * replay per chunk whose launches serve every waiting member (the products
+ * from device tile queues, as qsd_apply_H_batch; each Lanczos kernel once for
+ * all members).  A graph is captured per (product classes present, steps)
+ * on first use and replayed for any membership.  A member's Lanczos
+ * arithmetic is bitwise that of the request alone with the same product.
+ * Packed launches end with their longest member, while requests on their own
+ * streams overlap one another's kernels: measured on GB300 (closed loop, 64
+ * slots) packing pays for subspaces of a few thousand rows (about 1.4x the
+ * solves/s at 1e3-4e3 rows), breaks even near 1e4 rows and loses above
+ * (0.7x at 1e3-3e4 rows); 4096 is a good threshold.  0 (the default)
+ * disables packing.  Applies to requests admitted afterwards. */
 int qsd_server_set_pack_rows(qsd_server srv, int64_t rows);
 const char *qsd_server_last_error(qsd_server srv);
 /* Cancel what is queued or running, wait for the scheduler, free everything. */

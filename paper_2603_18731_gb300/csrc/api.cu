@@ -346,6 +346,17 @@ ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *di
     return make_params(ctx, op, sub, diag, k, x, y);
 }
 
+FacPair factored_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y) {
+    return FacPair{make_params(ctx, op, sub, diag, k, x, y), make_exc(op), make_fac(op, sub)};
+}
+
+int pack_class(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lanes8) {
+    if (use_factored(ctx, op, sub)) return kPackFacClass + op->W - 1;
+    if (op->W > kMaxWordsStatic) return -1;
+    if (lanes8 && choose_lanes(ctx, sub->D, op->G) == 8) return kPackScan8Class + op->W - 1;
+    return op->W - 1;
+}
+
 // Path for (op, sub, precision, KB): a forced choice, the tuned choice in
 // the context's cache, a fresh measurement (when allowed), or the heuristic.
 int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int KB, const void *x,
@@ -736,8 +747,9 @@ int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *
             precision > QSD_FP32_DOT2)
             fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_batch: bad n, arrays, k or precision");
         set_device(ctx);
-        // pairs by key width; empty subspaces need no work
-        std::map<int, std::vector<int>> by_w;
+        // pairs by packed class (key width; factored or scan); empty
+        // subspaces need no work
+        std::map<int, std::vector<int>> by_class;
         std::vector<const double *> diag(n);
         for (int i = 0; i < n; ++i) {
             check_pair(ctx, ops[i], subs[i]);
@@ -746,34 +758,61 @@ int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *
             if (subs[i]->D == 0) continue;
             if (!xs[i] || !ys[i]) fail(QSD_ERR_INVALID_ARG, "qsd_apply_H_batch: NULL vector");
             diag[i] = get_binding(ctx, ops[i], subs[i])->diag.as<double>();
-            by_w[ops[i]->W].push_back(i);
+            by_class[pack_class(ctx, ops[i], subs[i], false)].push_back(i);
         }
         cudaStream_t s = ctx->stream;
-        for (auto &[W, idx] : by_w) {
+        for (auto &[cls, idx] : by_class) {
+            const bool fac = cls >= kPackFacClass;
+            const int W = pack_class_width(cls);
+            const int rows = pack_class_rows(cls);
+            const size_t rec = fac ? sizeof(FacPair) : sizeof(ApplyParams);
             const int m = (int)idx.size();
-            std::vector<ApplyParams> hp(m);
-            std::vector<int64_t> t0(m);
+            // device block: queue, tile starts, parameter records
+            const size_t o_t = align_up(sizeof(TileQueue), 256), o_p = align_up(o_t + (size_t)m * 8, 256);
+            std::vector<unsigned char> h(o_p + (size_t)m * rec);
+            TileQueue *hq = reinterpret_cast<TileQueue *>(h.data());
+            int64_t *t0 = reinterpret_cast<int64_t *>(h.data() + o_t);
             int64_t tiles = 0;
             for (int j = 0; j < m; ++j) {
                 t0[j] = tiles;
-                tiles += (subs[idx[j]]->D + 255) / 256;
+                tiles += (subs[idx[j]]->D + rows - 1) / rows;
             }
             if (tiles >= (int64_t)0x7fffffff) fail(QSD_ERR_CAPACITY, "qsd_apply_H_batch: too many rows");
-            DevBuf dp, dt;
-            dp.alloc_async((size_t)m * sizeof(ApplyParams), s);
-            dt.alloc_async((size_t)m * 8, s);
-            QSD_CUDA(cudaMemcpyAsync(dt.p, t0.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+            hq->n = m;
+            hq->tiles = tiles;  // claim counters zero
+            DevBuf d;
+            d.alloc_async(h.size(), s);
+            unsigned char *dd = static_cast<unsigned char *>(d.p);
             for (int64_t c = 0; c < k;) {
                 const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
                 for (int j = 0; j < m; ++j) {
                     const int i = idx[j];
-                    hp[j] = make_params(ctx, ops[i], subs[i], diag[i], k, xs[i], ys[i]);
-                    hp[j].col0 = c;
+                    ApplyParams ap = make_params(ctx, ops[i], subs[i], diag[i], k, xs[i], ys[i]);
+                    ap.col0 = c;
+                    if (fac) {
+                        FacPair fp{ap, make_exc(ops[i]), make_fac(ops[i], subs[i])};
+                        std::memcpy(h.data() + o_p + (size_t)j * rec, &fp, rec);
+                    } else {
+                        std::memcpy(h.data() + o_p + (size_t)j * rec, &ap, rec);
+                    }
                 }
-                // pageable source: the copy is staged before the call returns
-                QSD_CUDA(cudaMemcpyAsync(dp.p, hp.data(), (size_t)m * sizeof(ApplyParams), cudaMemcpyHostToDevice,
-                                         s));
-                launch_apply_batch(dp.as<ApplyParams>(), dt.as<int64_t>(), m, tiles, W, KB, precision, s);
+                // pageable source: the copy is staged before the call returns;
+                // the queue's counters are back at zero after each launch
+                QSD_CUDA(cudaMemcpyAsync(dd, h.data(), h.size(), cudaMemcpyHostToDevice, s));
+                TileQueue *dq = reinterpret_cast<TileQueue *>(dd);
+                const int64_t *dt = reinterpret_cast<const int64_t *>(dd + o_t);
+                if (fac) {
+                    const FacPair *dp = reinterpret_cast<const FacPair *>(dd + o_p);
+                    if (precision == QSD_FP64)
+                        launch_apply_fac_queue<QSD_FP64>(dp, dt, dq, tiles, W, KB, ctx->num_sms, s);
+                    else if (precision == QSD_FP32_MIXED)
+                        launch_apply_fac_queue<QSD_FP32_MIXED>(dp, dt, dq, tiles, W, KB, ctx->num_sms, s);
+                    else
+                        launch_apply_fac_queue<QSD_FP32_DOT2>(dp, dt, dq, tiles, W, KB, ctx->num_sms, s);
+                } else {
+                    launch_apply_queue(reinterpret_cast<const ApplyParams *>(dd + o_p), dt, dq, tiles, W, 1, KB,
+                                       precision, ctx->num_sms, s);
+                }
                 c += KB;
             }
         }

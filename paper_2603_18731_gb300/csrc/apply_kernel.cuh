@@ -463,11 +463,15 @@ void launch_apply(const ApplyParams &p, int W, int R, int KB, cudaStream_t s, bo
 // Product parameters of one (operator, subspace) pair with x, y of row
 // stride k (column 0 first).
 ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y);
-// Packed group-scan products of n pairs (W <= 4, one lane per row): params
-// and tile0 (first tile of each pair, ascending, tile0[0] = 0) in device
-// memory; `tiles` blocks of 256 rows in total.
-void launch_apply_batch(const ApplyParams *params, const int64_t *tile0, int n, int64_t tiles, int W, int KB,
-                        int precision, cudaStream_t s);
+// Packed group-scan products (W <= 4, R = 1 or 8 lanes per row; R = 8 takes
+// KB = 1) served from a device tile queue (tile_queue.cuh): params [n] and
+// tile0 [n] (first tile of 256 / R rows of each pair, ascending, tile0[0] =
+// 0) and the queue in device memory.  The grid is the resident grid of the
+// variant, capped at max_tiles (pass the queue's tile count, or a bound when
+// the count is written later, as in a captured graph).
+struct TileQueue;
+void launch_apply_queue(const ApplyParams *params, const int64_t *tile0, TileQueue *q, int64_t max_tiles, int W,
+                        int R, int KB, int precision, int num_sms, cudaStream_t s);
 // Half-evaluation product (FP64, Hermitian real operators, W <= 4); zeroes
 // the launch's columns of y first.
 void launch_apply_sym(const ApplyParams &p, int W, int R, int KB, cudaStream_t s, bool hash_order = false);

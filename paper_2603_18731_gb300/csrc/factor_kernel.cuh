@@ -28,6 +28,7 @@
 #pragma once
 
 #include "excite.cuh"
+#include "tile_queue.cuh"
 
 namespace qsd {
 
@@ -50,6 +51,13 @@ struct FacParams {
     const uint32_t *rix;
     uint32_t nA, nB;
     int split;
+};
+
+// The parameters of one pair of a packed factored product.
+struct FacPair {
+    ApplyParams p;
+    ExcParams e;
+    FacParams f;
 };
 
 // Neighbour type of (dOcc, dEmp) in the low (sector 0) or high (sector 1)
@@ -133,8 +141,10 @@ __device__ __forceinline__ double scaled_i64_to_f64(int64_t v, int ex) {
     return __longlong_as_double((long long)(sign | ((uint64_t)eb << 52) | mant));
 }
 
+// Row `row` of the product (one warp; rows past D return at once).
 template <int W, int KB, int PREC>
-__global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const ExcParams e, const FacParams f) {
+__device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e, const FacParams &f,
+                                        const int64_t row) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     static_assert(32 % KB == 0, "KB divides the warp");
     constexpr int NC = 32 / KB;  // candidates per gather instruction
@@ -145,7 +155,6 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     __shared__ uint32_t ccol[8][32];
     __shared__ uint8_t occ[8][64 * W];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= p.D) return;  // warp-uniform
     const uint32_t ib = (uint32_t)(row / f.nA), ia = (uint32_t)(row - (int64_t)ib * f.nA);
     uint64_t key[W];
@@ -366,8 +375,46 @@ __global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const Ex
     }
 }
 
+template <int W, int KB, int PREC>
+__global__ void __launch_bounds__(256) k_apply_fac(const ApplyParams p, const ExcParams e, const FacParams f) {
+    fac_row<W, KB, PREC>(p, e, f, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+}
+
+// Packed factored products: tiles of 8 rows (a warp per row) of many pairs
+// from a device tile queue; each row is evaluated as by k_apply_fac.
+template <int W, int KB, int PREC>
+__global__ void __launch_bounds__(256)
+    k_apply_fac_queue(const FacPair *__restrict__ params, const int64_t *__restrict__ tile0, TileQueue *q) {
+    __shared__ FacPair sp;
+    run_tile_queue(params, tile0, q, sp, [](const FacPair &r, int, int64_t t) {
+        fac_row<W, KB, PREC>(r.p, r.e, r.f, t * 8 + (threadIdx.x >> 5));
+    });
+}
+
 // Launch the factored product for precision mode PREC (W <= 2).
 template <int PREC>
 void launch_apply_fac(const ApplyParams &p, const ExcParams &e, const FacParams &f, int W, int KB, cudaStream_t s);
+// Packed product classes: 0..3 the group scan with one lane per row of key
+// width W = class + 1 (256-row tiles), 4..7 the group scan with eight lanes
+// per row, W = class - 3 (32-row tiles; single columns), 8..9 the factored
+// product of key width W = class - 7 (8-row tiles, a warp per row).  A pair
+// takes the factored product where it applies (the path the single product
+// takes), else the scan; eight lanes per row only where asked for and where
+// the single product would take them (small subspaces, many groups).
+constexpr int kPackScan8Class = 4, kPackFacClass = 8, kPackClasses = 10;
+int pack_class(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lanes8);
+inline int pack_class_width(int c) {
+    return c >= kPackFacClass ? c - kPackFacClass + 1 : (c >= kPackScan8Class ? c - kPackScan8Class + 1 : c + 1);
+}
+inline int pack_class_lanes(int c) { return c >= kPackFacClass ? 32 : (c >= kPackScan8Class ? 8 : 1); }
+inline int pack_class_rows(int c) { return 256 / pack_class_lanes(c); }
+// The factored-product parameters of one pair with x, y of row stride k.
+FacPair factored_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y);
+
+// Packed factored products (W <= 2) of the pairs of a device tile queue
+// (8-row tiles); grid as launch_apply_queue.
+template <int PREC>
+void launch_apply_fac_queue(const FacPair *params, const int64_t *tile0, TileQueue *q, int64_t max_tiles, int W,
+                            int KB, int num_sms, cudaStream_t s);
 
 }  // namespace qsd

@@ -25,7 +25,9 @@
 #include <map>
 #include <memory>
 
+#include "factor_kernel.cuh"
 #include "lanczos.cuh"
+#include "tile_queue.cuh"
 
 namespace qsd {
 
@@ -452,22 +454,48 @@ __global__ void k_ritz(const TV *__restrict__ V, int64_t D, const int *__restric
 size_t tri_smem(int m) { return (size_t)8 * m * 8 + 64; }
 
 // ---------------------------------------------------------------- packed
-// One launch per kernel of the Lanczos step serves every job of a pack: the
-// blocks of all jobs form one grid, each block finds its job by binary search
-// over the jobs' first blocks (`first[n + 1]`, ascending) and runs the same
-// body as the single-job kernel with the job's own block index and count, so
-// a packed job computes bitwise what it computes alone.  A job takes part in
-// the steps of a chunk until its step counter reaches `jstop`.
+// One launch per kernel of the Lanczos step serves every job of a pack.  The
+// grids are fixed (a multiple of the SM count): each block walks the virtual
+// blocks of all jobs -- job i owns virtual blocks [first[i], first[i+1]) of
+// each kernel family -- and runs the single-job body with the job's own block
+// index and count, so a packed job's dots, norms and basis vectors are
+// bitwise those it computes alone.  A job takes part in the steps of a chunk
+// until its step counter reaches `jstop`.  The job count, the first arrays
+// and the descriptors live in the pack's device block, so the launches (and
+// a CUDA graph of them) do not change with the membership.
 struct PackJob {
     const void *V;
     void *vcur, *hv;
     double *w, *h, *part, *alpha, *beta, *tri;
     int *jdev;
     int64_t D;
-    int m, B, nbD, jstop;
+    int m, B, nbD, nb, jstop, pad;
 };
 
-__device__ __forceinline__ int find_job(const int *__restrict__ first, int n, int b) {
+// Each block stages the launch family's first array and every job's step
+// (-1 once the job has finished its part of the chunk) in shared memory, so
+// that resolving a virtual block costs a few shared-memory reads instead of
+// a chain of dependent global loads.
+constexpr int kPackMaxJobs = 256;
+
+struct PackStage {
+    int first[kPackMaxJobs + 1];
+    int j[kPackMaxJobs];
+};
+
+__device__ __forceinline__ int stage_pack(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                                          const int *__restrict__ np, PackStage &st) {
+    const int n = *np;
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) st.first[k] = first[k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int j = *jobs[k].jdev;
+        st.j[k] = j < jobs[k].jstop ? j : -1;
+    }
+    __syncthreads();
+    return n;
+}
+
+__device__ __forceinline__ int find_job(const int *first, int n, int b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -479,95 +507,257 @@ __device__ __forceinline__ int find_job(const int *__restrict__ first, int n, in
 
 // which = 0: u = hv (type TV); 1: u = w (double)
 template <typename TV, typename TU>
-__global__ void kp_gemv_t(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n, int which) {
-    __shared__ double sh[kGemvSh];
-    const int i = find_job(first, n, blockIdx.x);
-    const PackJob &J = jobs[i];
-    const int j = *J.jdev;
-    if (j >= J.jstop) return;  // block-uniform
-    const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
-    gemv_t_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, u, J.part, blockIdx.x - first[i], J.B, sh);
+__global__ void kq_gemv_t(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                          const int *__restrict__ np, int which) {
+    __shared__ PackStage st;
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i];
+        if (j < 0) continue;  // block-uniform
+        const PackJob &J = jobs[i];
+        const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
+        gemv_t_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, u, J.part, b - st.first[i], J.B, nullptr);
+    }
 }
 
-__global__ void kp_reduce_rows(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
+__global__ void kq_reduce_rows(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                               const int *__restrict__ np) {
+    __shared__ PackStage st;
     __shared__ double sh[32];
-    const int i = find_job(first, n, blockIdx.x);
-    const PackJob &J = jobs[i];
-    const int j = *J.jdev;
-    if (j >= J.jstop) return;
-    reduce_rows_body(J.part, j, J.B, J.h, J.alpha, blockIdx.x - first[i], sh);
-}
-
-template <typename TV, typename TU>
-__global__ void kp_gemv_sub(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n, int which) {
-    extern __shared__ double hs[];
-    const int i = find_job(first, n, blockIdx.x);
-    const PackJob &J = jobs[i];
-    const int j = *J.jdev;
-    if (j >= J.jstop) return;
-    const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
-    gemv_sub_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, J.h, u, J.w, blockIdx.x - first[i], hs);
-}
-
-__global__ void kp_sq_partial(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
-    __shared__ double sh[32];
-    const int i = find_job(first, n, blockIdx.x);
-    const PackJob &J = jobs[i];
-    if (*J.jdev >= J.jstop) return;
-    sq_partial_body(J.w, J.D, J.part, blockIdx.x - first[i], J.B, sh);
-}
-
-// one block per job
-__global__ void kp_sqrt_sum(const PackJob *__restrict__ jobs) {
-    __shared__ double sh[32];
-    const PackJob &J = jobs[blockIdx.x];
-    const int j = *J.jdev;
-    if (j >= J.jstop) return;
-    sqrt_sum_body(J.part, J.B, J.beta + j + 1, sh);
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i], row = b - st.first[i];
+        if (j < 0 || row > j) continue;
+        const PackJob &J = jobs[i];
+        reduce_rows_body(J.part, j, J.B, J.h, J.alpha, row, sh);  // ends on a barrier
+    }
 }
 
 template <typename TV>
-__global__ void kp_next(const PackJob *__restrict__ jobs, const int *__restrict__ first, int n) {
-    const int i = find_job(first, n, blockIdx.x);
-    const PackJob &J = jobs[i];
-    const int j = *J.jdev;
-    if (j >= J.jstop) return;
-    next_body<TV>(J.w, J.beta[j + 1], j + 1, J.D, J.m, static_cast<TV *>(const_cast<void *>(J.V)),
-                  static_cast<TV *>(J.vcur), blockIdx.x - first[i]);
+__global__ void kq_gemv_sub(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                            const int *__restrict__ np) {
+    extern __shared__ double hs[];
+    __shared__ PackStage st;
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i];
+        if (j < 0) continue;
+        const PackJob &J = jobs[i];
+        gemv_sub_body<TV, TV>(static_cast<const TV *>(J.V), J.D, j + 1, J.h, static_cast<const TV *>(J.hv), J.w,
+                              b - st.first[i], hs);
+        __syncthreads();  // hs is reloaded next round
+    }
 }
 
-__global__ void kp_incr(const PackJob *__restrict__ jobs, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && *jobs[i].jdev < jobs[i].jstop) *jobs[i].jdev += 1;
+// k_sub_sq for every job: w -= V h, squares of w per 256-row block
+template <typename TV>
+__global__ void kq_sub_sq(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                          const int *__restrict__ np) {
+    extern __shared__ double hs[];
+    __shared__ PackStage st;
+    __shared__ double sh[32];
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i];
+        if (j < 0) continue;
+        const PackJob &J = jobs[i];
+        const int nvec = j + 1, vb = b - st.first[i];
+        const TV *__restrict__ V = static_cast<const TV *>(J.V);
+        const int64_t D = J.D;
+        double *w = J.w;
+        for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = J.h[k];
+        __syncthreads();
+        const int64_t r = (int64_t)vb * blockDim.x + threadIdx.x;
+        double sq = 0.0;
+        if (r < D) {
+            double acc = w[r];
+            for (int k = 0; k < nvec; ++k) acc = fma(-(double)V[(size_t)k * D + r], hs[k], acc);
+            w[r] = acc;
+            sq = acc * acc;
+        }
+        sq = block_sum(sq, sh);  // ends on a barrier: hs is free again
+        if (threadIdx.x == 0) J.part[(size_t)(J.m + 2) * J.B + vb] = sq;
+    }
 }
 
-__global__ void kp_tridiag(const PackJob *__restrict__ jobs) {
+// k_norm_next for every job (job i's virtual grid: nb blocks)
+template <typename TV>
+__global__ void kq_norm_next(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                             const int *__restrict__ np) {
+    __shared__ PackStage st;
+    __shared__ double sh[32];
+    __shared__ double nrm_s;
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i];
+        if (j < 0) continue;
+        const PackJob &J = jobs[i];
+        const int vb = b - st.first[i], nbD = J.nbD, nb = J.nb, m = J.m;
+        const int64_t D = J.D;
+        const double *__restrict__ part = J.part + (size_t)(m + 2) * J.B;
+        double t = 0.0;
+        for (int k = threadIdx.x; k < nbD; k += blockDim.x) t += part[k];
+        t = block_sum(t, sh);
+        if (threadIdx.x == 0) nrm_s = sqrt(t);
+        __syncthreads();
+        const double nrm = nrm_s;
+        const int j1 = j + 1;
+        if (vb == 0 && threadIdx.x == 0) J.beta[j1] = nrm;
+        TV *V = static_cast<TV *>(const_cast<void *>(J.V));
+        TV *vc = static_cast<TV *>(J.vcur);
+        const double *__restrict__ w = J.w;
+        for (int64_t r = (int64_t)vb * blockDim.x + threadIdx.x; r < D; r += (int64_t)nb * blockDim.x) {
+            const TV v = (TV)(nrm > 0.0 ? w[r] / nrm : 0.0);
+            if (j1 <= m) V[(size_t)j1 * D + r] = v;
+            vc[r] = v;
+        }
+        __syncthreads();  // nrm_s is rewritten next round
+    }
+}
+
+__global__ void kq_incr(const PackJob *__restrict__ jobs, const int *__restrict__ np) {
+    const int n = *np;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (*jobs[i].jdev < jobs[i].jstop) *jobs[i].jdev += 1;
+}
+
+// block i < n: the tridiagonal problem of job i, then its four results to out[4 i]
+__global__ void kq_tridiag(const PackJob *__restrict__ jobs, const int *__restrict__ np, double *out) {
     extern __shared__ double sm[];
+    if ((int)blockIdx.x >= *np) return;
     const PackJob &J = jobs[blockIdx.x];
     tridiag_body(J.alpha, J.beta, *J.jdev, J.tri, sm);
+    __syncthreads();
+    if (threadIdx.x < 4) out[4 * (size_t)blockIdx.x + threadIdx.x] = J.tri[threadIdx.x];
 }
 
 }  // namespace
 
-// Layout of the pack's device block: jobs, then the first-block arrays
-// (B tiles, m+1 tiles, 256-row tiles), then per key width the product
-// parameters and their tile starts.
-void enqueue_packed_chunk(qsd_ctx ctx, const std::vector<LanczosJob *> &jobs, cudaStream_t s, PackBuffers &pb) {
+bool packable(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
+    const int c = pack_class(ctx, op, sub, true);
+    return c >= kPackFacClass || (c >= 0 && op->G <= kPackMaxScanGroups);
+}
+
+namespace {
+
+// Fixed layout of a pack's device block (and of its pinned staging) for
+// `cap` members: header (member count), descriptors, the first virtual block
+// of each job per kernel family (B dot blocks, m + 1 reduction blocks,
+// 256-row blocks, normalisation blocks), one tile queue and the first tiles
+// per product class, the product parameters per class, the results.
+struct PackLayout {
+    size_t o_jobs, o_first, o_q, o_t0, o_par[kPackClasses], o_out, bytes;
+    explicit PackLayout(int cap) {
+        o_jobs = 256;
+        o_first = align_up(o_jobs + (size_t)cap * sizeof(PackJob), 256);
+        o_q = align_up(o_first + (size_t)4 * (cap + 1) * sizeof(int), 256);
+        o_t0 = align_up(o_q + (size_t)kPackClasses * sizeof(TileQueue), 256);
+        size_t o = align_up(o_t0 + (size_t)kPackClasses * cap * 8, 256);
+        for (int c = 0; c < kPackClasses; ++c) {
+            o_par[c] = o;
+            o = align_up(o + (size_t)cap * rec(c), 256);
+        }
+        o_out = o;
+        bytes = align_up(o_out + (size_t)cap * 4 * sizeof(double), 256);
+    }
+    static size_t rec(int c) { return c >= kPackFacClass ? sizeof(FacPair) : sizeof(ApplyParams); }
+};
+
+constexpr int kPackGridPerSm = 4;  // blocks of the packed Lanczos kernels per SM
+
+// The launches of one chunk of `steps` steps for the product classes in
+// `mask` (captured into a graph by Pack::enqueue_chunk).
+template <typename TV>
+void enqueue_pack_steps(qsd_ctx ctx, unsigned char *d, const PackLayout &L, int cap, int prec, unsigned mask,
+                        int steps, double *host_out, cudaStream_t s) {
+    const PackJob *dj = reinterpret_cast<const PackJob *>(d + L.o_jobs);
+    const int *np = reinterpret_cast<const int *>(d);
+    const int *fB = reinterpret_cast<const int *>(d + L.o_first), *fM = fB + (cap + 1), *fD = fB + 2 * (cap + 1),
+              *fN = fB + 3 * (cap + 1);
+    TileQueue *q = reinterpret_cast<TileQueue *>(d + L.o_q);
+    const int64_t *t0 = reinterpret_cast<const int64_t *>(d + L.o_t0);
+    const int G = kPackGridPerSm * ctx->num_sms;
+    const size_t hsm = (size_t)(kLanczosMaxSteps + 1) * 8;
+    constexpr int64_t kAnyTiles = (int64_t)1 << 40;  // the resident grid: the tile count is in the queue
+    for (int t = 0; t < steps; ++t) {
+        for (int c = 0; c < kPackClasses; ++c) {
+            if (!(mask >> c & 1u)) continue;
+            const int64_t *tc = t0 + (size_t)c * cap;
+            if (c >= kPackFacClass) {
+                const FacPair *par = reinterpret_cast<const FacPair *>(d + L.o_par[c]);
+                const int W = pack_class_width(c);
+                if (prec == QSD_FP64) launch_apply_fac_queue<QSD_FP64>(par, tc, q + c, kAnyTiles, W, 1, ctx->num_sms, s);
+                else if (prec == QSD_FP32_MIXED)
+                    launch_apply_fac_queue<QSD_FP32_MIXED>(par, tc, q + c, kAnyTiles, W, 1, ctx->num_sms, s);
+                else launch_apply_fac_queue<QSD_FP32_DOT2>(par, tc, q + c, kAnyTiles, W, 1, ctx->num_sms, s);
+            } else {
+                launch_apply_queue(reinterpret_cast<const ApplyParams *>(d + L.o_par[c]), tc, q + c, kAnyTiles,
+                                   pack_class_width(c), pack_class_lanes(c), 1, prec, ctx->num_sms, s);
+            }
+        }
+        kq_gemv_t<TV, TV><<<G, kLanczosThreads, 0, s>>>(dj, fB, np, 0);
+        kq_reduce_rows<<<2 * G, 128, 0, s>>>(dj, fM, np);
+        kq_gemv_sub<TV><<<G, 256, hsm, s>>>(dj, fD, np);
+        kq_gemv_t<TV, double><<<G, kLanczosThreads, 0, s>>>(dj, fB, np, 1);
+        kq_reduce_rows<<<2 * G, 128, 0, s>>>(dj, fM, np);
+        kq_sub_sq<TV><<<G, 256, hsm, s>>>(dj, fD, np);
+        kq_norm_next<TV><<<G, 256, 0, s>>>(dj, fN, np);
+        kq_incr<<<1, 256, 0, s>>>(dj, np);
+    }
+    double *dout = reinterpret_cast<double *>(d + L.o_out);
+    kq_tridiag<<<cap, kLanczosThreads, tri_smem(kLanczosMaxSteps), s>>>(dj, np, dout);
+    QSD_LAUNCH_CHECK();
+    QSD_CUDA(cudaMemcpyAsync(host_out, dout, (size_t)cap * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+
+void Pack::init(qsd_ctx c, int capacity, cudaStream_t st) {
+    if (capacity > kPackMaxJobs) fail(QSD_ERR_INVALID_ARG, "pack: more members than the packed kernels stage");
+    ctx = c;
+    cap = std::max(capacity, 1);
+    s = st;
+    const PackLayout L(cap);
+    bytes = L.bytes;
+    dev.alloc_async(bytes, s);
+    QSD_CUDA(cudaMallocHost(reinterpret_cast<void **>(&host), bytes));
+    std::memset(host, 0, bytes);
+}
+
+void Pack::release() {
+    if (s) cudaStreamSynchronize(s);
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    dev.release();
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    if (s) cudaStreamSynchronize(s);
+    members.clear();
+    s = nullptr;
+}
+
+Pack::~Pack() { release(); }
+
+void Pack::enqueue_chunk(const std::vector<LanczosJob *> &jobs) {
     const int n = (int)jobs.size();
     if (n == 0) return;
+    if (n > cap) fail(QSD_ERR_INTERNAL, "packed chunk: more jobs than the pack holds");
+    const PackLayout L(cap);
     const bool fp32 = jobs[0]->fp32;
     const int prec = jobs[0]->prec;
-    int steps = 0, maxm = 0;
+    int steps = 0;
     std::vector<PackJob> pj(n);
-    std::vector<int> fB(n + 1), fM(n + 1), fD(n + 1);
-    fB[0] = fM[0] = fD[0] = 0;
-    std::map<int, std::vector<int>> by_w;
+    std::vector<int> first(4 * (cap + 1), 0);
+    int *fB = first.data(), *fM = fB + (cap + 1), *fD = fB + 2 * (cap + 1), *fN = fB + 3 * (cap + 1);
+    std::vector<std::vector<int>> by_class(kPackClasses);
     for (int i = 0; i < n; ++i) {
         LanczosJob &J = *jobs[i];
         if (J.fp32 != fp32 || J.prec != prec) fail(QSD_ERR_INTERNAL, "packed chunk: mixed precisions");
-        const int len = std::min(J.check_every, J.m - J.steps_done);
+        if (J.m > kLanczosMaxSteps) fail(QSD_ERR_INTERNAL, "packed chunk: basis larger than the packed kernels hold");
+        const int cls = pack_class(ctx, J.op, J.sub, true);
+        if (cls < 0) fail(QSD_ERR_INTERNAL, "packed chunk: product cannot be packed");
+        const int len = std::max(std::min(J.check_every, J.m - J.steps_done), 0);
         steps = std::max(steps, len);
-        maxm = std::max(maxm, J.m);
         PackJob &P = pj[i];
         P.V = J.V.p;
         P.vcur = J.vcur.p;
@@ -583,100 +773,100 @@ void enqueue_packed_chunk(qsd_ctx ctx, const std::vector<LanczosJob *> &jobs, cu
         P.m = J.m;
         P.B = J.B;
         P.nbD = J.nbD;
-        P.jstop = J.steps_done + std::max(len, 0);
+        P.nb = std::min<int>(J.nbD, 4 * ctx->num_sms);  // the single job's normalisation grid
+        P.jstop = J.steps_done + len;
+        P.pad = 0;
         fB[i + 1] = fB[i] + J.B;
         fM[i + 1] = fM[i] + J.m + 1;
         fD[i + 1] = fD[i] + J.nbD;
-        by_w[J.op->W].push_back(i);
+        fN[i + 1] = fN[i] + P.nb;
+        by_class[cls].push_back(i);
     }
     if (steps <= 0) return;
-    // host staging (pinned, reused once the previous chunk of this pack has
-    // passed), one copy to the device block
-    const size_t o_jobs = 0, o_f = align_up((size_t)n * sizeof(PackJob), 256);
-    const size_t o_params = align_up(o_f + (size_t)3 * (n + 1) * sizeof(int), 256);
-    size_t bytes = o_params;
-    for (auto &kv : by_w) bytes += align_up(kv.second.size() * (sizeof(ApplyParams) + 8), 256) + 256;
-    pb.reserve(bytes, s);
-    unsigned char *h = pb.host, *d = static_cast<unsigned char *>(pb.dev.p);
-    std::memcpy(h + o_jobs, pj.data(), (size_t)n * sizeof(PackJob));
-    int *hf = reinterpret_cast<int *>(h + o_f);
-    std::memcpy(hf, fB.data(), (size_t)(n + 1) * 4);
-    std::memcpy(hf + (n + 1), fM.data(), (size_t)(n + 1) * 4);
-    std::memcpy(hf + 2 * (n + 1), fD.data(), (size_t)(n + 1) * 4);
-    struct WLaunch { int W, m; int64_t tiles; size_t o_p, o_t; };
-    std::vector<WLaunch> wl;
-    size_t o = o_params;
-    for (auto &[W, idx] : by_w) {
-        const int m = (int)idx.size();
-        WLaunch L{W, m, 0, o, align_up(o + (size_t)m * sizeof(ApplyParams), 256)};
-        ApplyParams *hp = reinterpret_cast<ApplyParams *>(h + L.o_p);
-        int64_t *ht = reinterpret_cast<int64_t *>(h + L.o_t);
-        for (int k = 0; k < m; ++k) {
+    // staging: header, descriptors, first arrays, queues, first tiles (one
+    // copy), then each present class's parameters where they changed
+    unsigned char *h = host, *d = static_cast<unsigned char *>(dev.p);
+    std::memset(h, 0, L.o_par[0]);
+    *reinterpret_cast<int *>(h) = n;
+    std::memcpy(h + L.o_jobs, pj.data(), (size_t)n * sizeof(PackJob));
+    std::memcpy(h + L.o_first, first.data(), first.size() * sizeof(int));
+    TileQueue *hq = reinterpret_cast<TileQueue *>(h + L.o_q);
+    int64_t *ht0 = reinterpret_cast<int64_t *>(h + L.o_t0);
+    unsigned mask = 0;
+    std::vector<unsigned char> rec;
+    std::vector<std::pair<size_t, size_t>> dirty;
+    for (int c = 0; c < kPackClasses; ++c) {
+        const std::vector<int> &idx = by_class[c];
+        if (idx.empty()) continue;
+        mask |= 1u << c;
+        const int rows = pack_class_rows(c);
+        const size_t rb = PackLayout::rec(c);
+        rec.assign(idx.size() * rb, 0);
+        int64_t tiles = 0;
+        for (size_t k = 0; k < idx.size(); ++k) {
             LanczosJob &J = *jobs[idx[k]];
-            hp[k] = product_params(ctx, J.op, J.sub, J.diag, 1, J.vcur.p, J.hv.p);
-            ht[k] = L.tiles;
-            L.tiles += (J.D + 255) / 256;
+            ht0[(size_t)c * cap + k] = tiles;
+            tiles += (J.D + rows - 1) / rows;
+            if (c >= kPackFacClass) {
+                const FacPair fp = factored_params(ctx, J.op, J.sub, J.diag, 1, J.vcur.p, J.hv.p);
+                std::memcpy(rec.data() + k * rb, &fp, rb);
+            } else {
+                const ApplyParams ap = product_params(ctx, J.op, J.sub, J.diag, 1, J.vcur.p, J.hv.p);
+                std::memcpy(rec.data() + k * rb, &ap, rb);
+            }
         }
-        o = align_up(L.o_t + (size_t)m * 8, 256);
-        wl.push_back(L);
-    }
-    QSD_CUDA(cudaMemcpyAsync(d, h, o, cudaMemcpyHostToDevice, s));
-    const PackJob *dj = reinterpret_cast<const PackJob *>(d + o_jobs);
-    const int *dfB = reinterpret_cast<const int *>(d + o_f), *dfM = dfB + (n + 1), *dfD = dfB + 2 * (n + 1);
-    const size_t hsm = (size_t)(maxm + 1) * 8;
-    for (int t = 0; t < steps; ++t) {
-        for (const WLaunch &L : wl)
-            launch_apply_batch(reinterpret_cast<const ApplyParams *>(d + L.o_p),
-                               reinterpret_cast<const int64_t *>(d + L.o_t), L.m, L.tiles, L.W, 1, prec, s);
-        if (fp32) {
-            kp_gemv_t<float, float><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 0);
-            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
-            kp_gemv_sub<float, float><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 0);
-            kp_gemv_t<float, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 1);
-            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
-            kp_gemv_sub<float, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 1);
-        } else {
-            kp_gemv_t<double, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 0);
-            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
-            kp_gemv_sub<double, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 0);
-            kp_gemv_t<double, double><<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n, 1);
-            kp_reduce_rows<<<fM[n], 128, 0, s>>>(dj, dfM, n);
-            kp_gemv_sub<double, double><<<fD[n], 256, hsm, s>>>(dj, dfD, n, 1);
+        hq[c].n = (int32_t)idx.size();
+        hq[c].tiles = tiles;  // claim counters zero
+        if (std::memcmp(h + L.o_par[c], rec.data(), rec.size()) != 0) {
+            std::memcpy(h + L.o_par[c], rec.data(), rec.size());
+            dirty.emplace_back(L.o_par[c], rec.size());
         }
-        kp_sq_partial<<<fB[n], kLanczosThreads, 0, s>>>(dj, dfB, n);
-        kp_sqrt_sum<<<n, kLanczosThreads, 0, s>>>(dj);
-        if (fp32) kp_next<float><<<fD[n], 256, 0, s>>>(dj, dfD, n);
-        else kp_next<double><<<fD[n], 256, 0, s>>>(dj, dfD, n);
-        kp_incr<<<(n + 127) / 128, 128, 0, s>>>(dj, n);
     }
-    kp_tridiag<<<n, kLanczosThreads, tri_smem(maxm), s>>>(dj);
-    QSD_LAUNCH_CHECK();
+    QSD_CUDA(cudaMemcpyAsync(d, h, L.o_par[0], cudaMemcpyHostToDevice, s));
+    for (auto &[o, len] : dirty) QSD_CUDA(cudaMemcpyAsync(d + o, h + o, len, cudaMemcpyHostToDevice, s));
+    // the chunk: a graph per (classes present, steps), captured on first use
+    static_assert(kPackClasses <= 16, "class mask in the low 16 bits of the graph key");
+    const uint32_t key = mask | ((uint32_t)steps << 16);
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+        if (graphs.size() >= 64) {
+            for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+            graphs.clear();
+        }
+        double *hout = reinterpret_cast<double *>(h + L.o_out);
+        cudaGraph_t g = nullptr;
+        QSD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            if (fp32) enqueue_pack_steps<float>(ctx, d, L, cap, prec, mask, steps, hout, s);
+            else enqueue_pack_steps<double>(ctx, d, L, cap, prec, mask, steps, hout, s);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        QSD_CUDA(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        QSD_CUDA(e);
+        it = graphs.emplace(key, ge).first;
+        ++graph_builds;
+    }
+    QSD_CUDA(cudaGraphLaunch(it->second, s));
     for (int i = 0; i < n; ++i) {
-        LanczosJob &J = *jobs[i];
-        QSD_CUDA(cudaMemcpyAsync(J.hpin, J.tri.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        J.steps_done = pj[i].jstop;
-        ++J.chunks;
+        jobs[i]->steps_done = pj[i].jstop;
+        ++jobs[i]->chunks;
     }
+    members = jobs;
+    ++chunks;
 }
 
-void PackBuffers::reserve(size_t bytes, cudaStream_t s) {
-    if (bytes <= cap) return;
-    if (host) cudaFreeHost(host);
-    host = nullptr;
-    cap = 0;
-    dev.alloc_async(bytes, s);
-    QSD_CUDA(cudaMallocHost(reinterpret_cast<void **>(&host), bytes));
-    cap = bytes;
+void Pack::finish_chunk() {
+    const PackLayout L(cap);
+    const double *out = reinterpret_cast<const double *>(host + L.o_out);
+    for (size_t i = 0; i < members.size(); ++i) std::memcpy(members[i]->hpin, out + 4 * i, 4 * sizeof(double));
+    members.clear();
 }
-
-void PackBuffers::release() {
-    dev.release();
-    if (host) cudaFreeHost(host);
-    host = nullptr;
-    cap = 0;
-}
-
-PackBuffers::~PackBuffers() { release(); }
 
 // ---------------------------------------------------------------- job
 LanczosJob::~LanczosJob() {

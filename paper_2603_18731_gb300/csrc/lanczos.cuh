@@ -1,6 +1,9 @@
 // Lanczos state shared by the synchronous solver and the request server.
 #pragma once
 
+#include <map>
+#include <vector>
+
 #include "apply_kernel.cuh"
 
 namespace qsd {
@@ -44,26 +47,43 @@ struct LanczosJob {
     bool converged(double tol) const;
 };
 
-// Device block and pinned staging of a pack's descriptors (grown on demand;
-// reused once the stream has passed the previous chunk that used them).
-struct PackBuffers {
+// A pack: Lanczos jobs of one product precision advanced together, one
+// chunk of steps at a time, by CUDA-graph replays whose launches serve every
+// member (lanczos.cu).  The device block and its pinned staging have fixed
+// offsets for `cap` members, so a graph captured for one chunk shape (the
+// product classes present and the number of steps) replays for any
+// membership: a chunk costs the copy of the changed descriptors and one graph
+// launch.  Members' results (theta, estimate, beta_m, m) reach their hpin in
+// finish_chunk, once the stream has passed the chunk.
+struct Pack {
+    qsd_ctx ctx = nullptr;
+    int cap = 0;
+    cudaStream_t s = nullptr;
     DevBuf dev;
-    unsigned char *host = nullptr;
-    size_t cap = 0;
-    PackBuffers() = default;
-    PackBuffers(const PackBuffers &) = delete;
-    PackBuffers &operator=(const PackBuffers &) = delete;
-    ~PackBuffers();
-    void reserve(size_t bytes, cudaStream_t s);
-    void release();  // before the stream of `dev` is destroyed
+    unsigned char *host = nullptr;  // pinned staging (same layout)
+    size_t bytes = 0;
+    std::map<uint32_t, cudaGraphExec_t> graphs;  // by (classes present, steps)
+    std::vector<LanczosJob *> members;           // of the chunk in flight
+    int64_t chunks = 0, graph_builds = 0;
+
+    Pack() = default;
+    Pack(const Pack &) = delete;
+    Pack &operator=(const Pack &) = delete;
+    ~Pack();
+    void init(qsd_ctx c, int capacity, cudaStream_t st);
+    void release();  // before `s` is destroyed; waits for s
+    // One chunk for jobs (at most cap; shared basis type and product
+    // precision; each packable): min(check_every, m - steps_done) steps each.
+    void enqueue_chunk(const std::vector<LanczosJob *> &jobs);
+    // After the stream has passed the chunk: the members' results to their hpin.
+    void finish_chunk();
 };
 
-// One chunk of steps for every job of a pack with packed launches on stream
-// s: the product of all jobs (group scan, one launch per key width) and each
-// Lanczos kernel once for all jobs.  Jobs share the basis type and product
-// precision and have W <= 4; each advances min(check_every, m - steps_done)
-// steps and its tridiagonal results reach its hpin as after enqueue_chunk.
-void enqueue_packed_chunk(qsd_ctx ctx, const std::vector<LanczosJob *> &jobs, cudaStream_t s, PackBuffers &pb);
+// Whether the product of (op, sub) can run in a pack: the factored product
+// (W <= 2) or a group scan of at most kPackMaxScanGroups groups (W <= 4; one
+// or eight lanes per row, as the single product would choose).
+constexpr int64_t kPackMaxScanGroups = 4096;
+bool packable(qsd_ctx ctx, qsd_op op, qsd_sub sub);
 
 // FP64 Rayleigh quotient and residual of a vector, enqueued on a stream.
 struct ResidJob {

@@ -15,13 +15,15 @@
 // overlaps on the device and a request arriving while others run starts as
 // soon as a slot and memory free up.
 //
-// Small requests (at most `pack_rows` rows, W <= 4) share one stream and are
-// packed: whenever a pack's previous chunk has passed, one chunk of Lanczos
-// steps is enqueued for all its members that wait for one, with one launch
-// per kernel for all of them (enqueue_packed_chunk), so many small solves
+// Small requests (at most `pack_rows` rows, with a packable product: the
+// factored product or a group scan of few groups) are packed: whenever a
+// pack's previous chunk has passed, one chunk of Lanczos steps is enqueued
+// for all its members that wait for one -- a CUDA-graph replay whose
+// launches serve every member (the products from device tile queues, each
+// Lanczos kernel once for all), on the pack's stream -- so many small solves
 // cost the launches of one.  Requests join and leave a pack at chunk
-// boundaries; their other pieces (start, Ritz vector, residual) run on the
-// same stream between chunks.  All device memory of a request is
+// boundaries; their other pieces (start, Ritz vector, residual) run on their
+// own streams between chunks, ordered by the host.  All device memory of a request is
 // stream-ordered (cudaMallocAsync / cudaFreeAsync), so admitting and retiring
 // requests never synchronises the device.
 #include <algorithm>
@@ -61,6 +63,7 @@ struct Request {
     bool admitted = false;
     bool packed = false;             // small request: chunks run in packed launches
     LanczosJob *want = nullptr;      // packed: job waiting for the pack's next chunk
+    int in_pack = -1;                // packed: the pack whose chunk in flight holds the job
     std::unique_ptr<LanczosJob> J, K;
     std::unique_ptr<ResidJob> R;
     DevBuf diag, u, start;
@@ -103,7 +106,8 @@ struct qsd_server_s {
     // packs of small requests, one per product precision
     int64_t pack_rows = 0;  // packing off unless asked for (qsd_server_set_pack_rows)
     cudaStream_t pack_stream = nullptr;
-    qsd::PackBuffers pack_buf[3];
+    qsd::Pack pack[3];
+    std::vector<qsd::Request *> pack_members[3];  // of each pack's chunk in flight
     cudaEvent_t pack_ev[3] = {nullptr, nullptr, nullptr};
     bool pack_inflight[3] = {false, false, false};
     int64_t packed_requests = 0, packed_chunks = 0;
@@ -273,7 +277,7 @@ void scheduler(qsd_server_s *S) {
                 S->queue.pop_front();
                 r->slot = S->free_slots.back();
                 S->free_slots.pop_back();
-                r->packed = r->sub->D <= S->pack_rows && r->op->W <= kMaxWordsStatic;
+                r->packed = r->sub->D <= S->pack_rows && packable(S->ctx, r->op, r->sub);
                 r->s = S->streams[r->slot];
                 if (r->packed) ++S->packed_requests;
                 S->used += r->footprint;
@@ -307,7 +311,7 @@ void scheduler(qsd_server_s *S) {
                     if (!r->inflight || cudaEventQuery(r->ev) != cudaErrorNotReady) done.push_back(r);
                     continue;
                 }
-                if (!r->inflight) continue;
+                if (r->in_pack >= 0 || !r->inflight) continue;  // packed: advanced with its chunk
                 const cudaError_t q = cudaEventQuery(r->ev);
                 if (q == cudaErrorNotReady) continue;
                 r->inflight = false;
@@ -325,16 +329,37 @@ void scheduler(qsd_server_s *S) {
                 }
             }
         }
-        // packed chunks: every pack whose previous chunk has passed takes all
-        // its members that wait for a chunk.  A member's own stream is idle
-        // here (its last piece has passed), and its next piece follows only
-        // once the chunk has passed, so the host orders the two streams.
-        // Only this thread touches the members, so the launches are
-        // enqueued without holding the lock.
+        // packed chunks: once a pack's chunk has passed, its members' results
+        // move to their pinned words and each member advances (its next
+        // piece on its own stream, or a wish for the next chunk); then every
+        // pack takes all its members that wait for a chunk.  A member's own
+        // stream is idle while it waits, and its next piece follows only once
+        // the chunk has passed, so the host orders the two streams.  Only
+        // this thread touches the members.
         for (int k = 0; k < 3; ++k) {
             if (S->pack_inflight[k]) {
-                if (cudaEventQuery(S->pack_ev[k]) == cudaErrorNotReady) continue;
+                const cudaError_t q = cudaEventQuery(S->pack_ev[k]);
+                if (q == cudaErrorNotReady) continue;
+                if (q == cudaSuccess) S->pack[k].finish_chunk();
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (Request *r : S->pack_members[k]) {
+                    r->in_pack = -1;
+                    r->inflight = false;
+                    if (q != cudaSuccess) {
+                        S->last_error = cudaGetErrorString(q);
+                        finish(S, r, QSD_ERR_CUDA);
+                        continue;
+                    }
+                    try {
+                        advance(S, r);
+                    } catch (const Error &e) {
+                        S->last_error = e.what();
+                        finish(S, r, e.code);
+                    }
+                }
+                S->pack_members[k].clear();
                 S->pack_inflight[k] = false;
+                progressed = true;
             }
             std::vector<Request *> members;
             std::vector<LanczosJob *> jobs;
@@ -350,9 +375,9 @@ void scheduler(qsd_server_s *S) {
             std::string err;
             int code = QSD_OK;
             try {
-                enqueue_packed_chunk(S->ctx, jobs, S->pack_stream, S->pack_buf[k]);
+                if (!S->pack[k].host) S->pack[k].init(S->ctx, S->max_active, S->pack_stream);
+                S->pack[k].enqueue_chunk(jobs);
                 QSD_CUDA(cudaEventRecord(S->pack_ev[k], S->pack_stream));
-                for (Request *r : members) QSD_CUDA(cudaEventRecord(r->ev, S->pack_stream));
             } catch (const Error &e) {
                 err = e.what();
                 code = e.code;
@@ -360,10 +385,11 @@ void scheduler(qsd_server_s *S) {
             std::lock_guard<std::mutex> lk(S->mu);
             if (code == QSD_OK) {
                 S->pack_inflight[k] = true;
+                S->pack_members[k] = members;
                 ++S->packed_chunks;
                 for (Request *r : members) {
                     r->want = nullptr;
-                    r->inflight = true;
+                    r->in_pack = k;
                 }
             } else {
                 S->last_error = err;
@@ -572,8 +598,7 @@ int qsd_server_destroy(qsd_server S) {
     if (S->pack_stream) {
         // the packs' device blocks are stream-ordered on the pack stream:
         // free them while it exists
-        cudaStreamSynchronize(S->pack_stream);
-        for (auto &pb : S->pack_buf) pb.release();
+        for (auto &pk : S->pack) pk.release();
         cudaStreamSynchronize(S->pack_stream);
         cudaStreamDestroy(S->pack_stream);
     }

@@ -1,7 +1,9 @@
-"""Packed products of many (operator, subspace) pairs in one launch.
+"""Packed products of many (operator, subspace) pairs from device tile queues.
 
-Each pair's result must equal the single-pair product on the one-lane group
-scan bit for bit, and the oracle within the FP64 / FP32 parity bounds.
+Each pair's result must equal, bit for bit, the single-pair product on the
+path the pack uses for it -- the sector-factored product for a product
+subspace with an indexed operator, else the one-lane group scan -- and the
+oracle within the FP64 / FP32 parity bounds.
 """
 import numpy as np
 import pytest
@@ -48,9 +50,15 @@ def test_batch_matches_single_and_oracle(ctx, k):
         with torch.cuda.stream(ctx.stream):
             xs = [torch.as_tensor(x, device=ctx.device).to(dt).contiguous() for x in xs_np]
         ys = ctx.apply_H_batch(ops, subs, xs, precision=prec)
+        factored = [ctx.product_path(h, s, prec, k) == 7 for h, s in zip(ops, subs)]
+        assert any(factored)  # the fermionic pair: a product subspace
         ctx.set_tuning(1, 1)
         ctx.set_tuning(2, 1)
         singles = [ctx.apply_H(h, s, x, precision=prec) for h, s, x in zip(ops, subs, xs)]
+        ctx.set_tuning(1, 4)  # the factored product where it applies
+        for i, f in enumerate(factored):
+            if f:
+                singles[i] = ctx.apply_H(ops[i], subs[i], xs[i], precision=prec)
         ctx.set_tuning(1, 0)
         ctx.set_tuning(2, 0)
         ctx.synchronize()

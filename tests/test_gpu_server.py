@@ -3,6 +3,7 @@ Hamiltonians and subspace sizes run concurrently and each result equals the
 same request solved alone and the oracle's ground energy; admission respects
 the memory budget; cancellation and submit-time errors."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -122,3 +123,41 @@ def test_server_packs_small_requests(ctx, precision):
                 assert 0 < st["packed_chunks"] < steps // params["check_every"]
             else:
                 assert st["packed_requests"] == 0 and st["packed_chunks"] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_server_pack_holds_every_product_class(ctx, precision):
+    # one pack serves requests of every product class at once -- 200-qubit
+    # Ising (group scan, four key words), 4x4 XXZ (group scan, one word) and
+    # an 8-orbital product subspace (factored product) -- with members
+    # joining and leaving at chunk boundaries; each result equals the
+    # request alone (the single product takes the same path class)
+    import paper_2603_18731_gb300 as q
+    cases = []
+    op = wl.ising_heavy_hex(200, seed=4)
+    cases.append(("ising200", op, wl.flip_subspace(200, 3000, max_flips=8, seed=2)))
+    op = wl.xxz_square(4, 4)
+    cases.append(("xxz", op, wl.xxz_walk_subspace(4, 4, count=1500, max_len=8, seed=3)))
+    h1, eri = wl.chem_integrals(8, seed=6)
+    op = wl.molecular_qubit_operator(h1, eri)
+    a = wl.excitation_strings(8, 3, 40, 3, 11)
+    b = wl.excitation_strings(8, 3, 30, 3, 12)
+    cases.append(("chem8", op, wl.product_subspace(a, b, 8)))
+    handles = [(name, ctx.load_operator(op), ctx.build_subspace(op.n_qubits, w)) for name, op, w in cases]
+    assert ctx.product_path(handles[2][1], handles[2][2], precision) == 7
+    params = dict(precision=precision, max_steps=200, tol=1e-9, check_every=10)
+    alone = {name: ctx.lanczos_ground_state(h, s, **params)[0] for name, h, s in handles}
+    with q.Server(ctx, budget_bytes=1 << 30, max_active=12) as srv:
+        srv.set_pack_rows(1 << 20)
+        tickets = []
+        for rep in range(3):
+            for name, h, s in handles:
+                tickets.append((name, srv.submit(h, s, **params)))
+            time.sleep(0.002)  # later members join a pack already running
+        for name, t in tickets:
+            r = srv.wait(t, timeout_s=120)
+            assert r["status"] == "OK", (name, r)
+            assert abs(r["energy"] - alone[name]) <= 1e-12 * abs(alone[name]), (name, r["energy"], alone[name])
+        st = srv.stats()
+        assert st["packed_requests"] == len(tickets) and st["failed"] == 0
+        assert st["packed_chunks"] > 0
