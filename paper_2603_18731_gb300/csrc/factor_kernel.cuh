@@ -118,16 +118,16 @@ __device__ __forceinline__ double ladder_terms_fp64(const TermRec<W> *__restrict
 // v * 2^-ex rounded to the nearest double (ties to even), by integer
 // operations on the IEEE-754 encoding: the 53 leading bits of |v| become the
 // significand (the bits below decide the rounding), the exponent is the
-// position of the leading bit minus ex.  Results below the normal range take
-// the hardware conversion.  Keeps the conversion off the FP64 pipe, which
-// the accumulation of the found columns saturates.
+// position of the leading bit minus ex.  The operator's fixed-point exponent
+// is at most 1000 and |v| >= 1, so the result is always a normal number.
+// Keeps the conversion off the FP64 pipe, which the accumulation of the
+// found columns saturates.
 __device__ __forceinline__ double scaled_i64_to_f64(int64_t v, int ex) {
     if (v == 0) return 0.0;
     const uint64_t sign = v < 0 ? (1ull << 63) : 0ull;
     const uint64_t u = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
     const int lz = __clzll((long long)u);
-    const int e = 63 - lz - ex;  // |v| 2^-ex lies in [2^e, 2^(e+1))
-    if (e < -1022) return __ll2double_rn(v) * exp2((double)-ex);
+    const int e = 63 - lz - ex;  // |v| 2^-ex lies in [2^e, 2^(e+1)), e >= -1000
     const uint64_t m = u << lz;  // leading one at bit 63
     uint64_t mant = (m >> 11) & ((1ull << 52) - 1);
     const uint64_t rest = m & 0x7ffull;
@@ -151,12 +151,15 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
     __shared__ uint32_t pre[8][kMaxShapes + 1];  // per warp: first candidate of each shape
     __shared__ uint32_t sa[8][kMaxShapes], sb[8][kMaxShapes], lb[8][kMaxShapes];
     // per warp: the found candidates of the current round, compacted
-    __shared__ double camp[8][32];
-    __shared__ uint32_t ccol[8][32];
+    // (the pending found candidates of earlier rounds, fewer than 32 / KB, first)
+    __shared__ double camp[8][64];
+    __shared__ uint32_t ccol[8][64];
     __shared__ uint8_t occ[8][64 * W];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (row >= p.D) return;  // warp-uniform
-    const uint32_t ib = (uint32_t)(row / f.nA), ia = (uint32_t)(row - (int64_t)ib * f.nA);
+    // D = |A| |B| <= 2^32: 32-bit division (a 64-bit one runs on the FP64 pipe)
+    const uint32_t r32 = (uint32_t)row;
+    const uint32_t ib = r32 / f.nA, ia = r32 - ib * f.nA;
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
@@ -214,6 +217,7 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
     double acc = 0.0;
     float as = 0.f, ae = 0.f;
     int si = 0;
+    int pend = 0;  // FP64 accumulation: found candidates not yet gathered (warp-uniform)
     for (uint32_t base = 0; base < total; base += 32) {
         // 1. one candidate per lane: its element (0: none) and column
         const uint32_t t = base + (uint32_t)lane;
@@ -330,25 +334,48 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
             }
             continue;
         }
-        // FP64 accumulation: the found candidates compacted in candidate
-        // order, KB lanes per candidate and NC candidates per load
-        // instruction, so that every FP64 FMA runs at full lanes but the last
+        // FP64 accumulation: the found candidates appended, in candidate
+        // order, behind those pending from earlier rounds; whole groups of
+        // NC are gathered (KB lanes per candidate, NC candidates per load
+        // instruction), so every FP64 FMA runs at full lanes, and the rest
+        // (fewer than NC) moves to the front for the next round
         if (nz) {
-            const int slot = __popc(found & ((1u << lane) - 1u));
+            const int slot = pend + __popc(found & ((1u << lane) - 1u));
             camp[wib][slot] = amp;
             ccol[wib][slot] = col;
         }
         __syncwarp();
-        const int nf = __popc(found);
-        for (int i0 = 0; i0 < nf; i0 += NC) {
+        const int tot = pend + __popc(found), full = tot - tot % NC;
+        for (int i0 = 0; i0 < full; i0 += NC) {
             const int src = i0 + lane / KB;
-            if (src < nf) {
-                const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
-                if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
-                else acc = fma(camp[wib][src], (double)xv, acc);
+            const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
+            if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
+            else acc = fma(camp[wib][src], (double)xv, acc);
+        }
+        pend = tot - full;
+        if (pend > 0 && full > 0) {
+            double a = 0.0;
+            uint32_t c = 0;
+            if (lane < pend) {
+                a = camp[wib][full + lane];
+                c = ccol[wib][full + lane];
+            }
+            __syncwarp();
+            if (lane < pend) {
+                camp[wib][lane] = a;
+                ccol[wib][lane] = c;
             }
         }
         __syncwarp();
+    }
+    if (KB > 1 && PREC != QSD_FP32_DOT2 && pend > 0) {
+        // the last pending candidates: one partial gather
+        const int src = lane / KB;
+        if (src < pend) {
+            const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
+            if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
+            else acc = fma(camp[wib][src], (double)xv, acc);
+        }
     }
     // lanes with the same column (lane % KB) hold parts of its sum
 #pragma unroll
