@@ -264,13 +264,10 @@ FacParams make_fac(qsd_op op, qsd_sub sub) {
     const Factored &f = sub->fac;
     FacParams r{};
     r.trec = op->trec.p;
-    r.trec64 = op->trec64.p;
     r.qscale = op->qscale;
     r.qexp = op->qexp;
     r.lin_base = op->lin_base.as<int32_t>();
     r.lin_z = op->lin_z.as<uint64_t>();
-    r.lin_k64 = op->lin_k64.as<double>();
-    r.lin_d64 = op->lin_d64.as<double>();
     r.lin_kq = op->lin_kq.as<int64_t>();
     r.lin_dq = op->lin_dq.as<int64_t>();
     r.nq = op->n_qubits;

@@ -66,9 +66,8 @@ __global__ void k_term_records(int64_t T, const uint64_t *__restrict__ tP, const
         r.V[w] = tV[(size_t)w * T + t];
         r.Z[w] = tZ[(size_t)w * T + t];
     }
-    // scale > 0: fixed point (a power of two: the product is exact); 0: the
-    // FP64 phase's bits
-    r.q = scale > 0.0 ? __double2ll_rn(tphi[t] * scale) : __double_as_longlong(tphi[t]);
+    // fixed point (scale a power of two: the product is exact)
+    r.q = __double2ll_rn(tphi[t] * scale);
     out[t] = r;
 }
 
@@ -162,9 +161,10 @@ void build_dense_index(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc) 
 // v_t = 0 at r).
 // Single-excitation groups of a two-body fermionic operator are of this kind:
 // a constant plus one coefficient per occupied orbital, up to the sign of the
-// Jordan-Wigner string.  Tabulated for the groups whose ranges are all linear
-// and hold at least kLinearMinTerms terms somewhere; the fixed-point table
-// sums the same integers q_t as the term loop, so it gives the same element.
+// Jordan-Wigner string.  Tabulated, in the fixed point of the term records,
+// for the groups whose ranges are all linear and hold at least
+// kLinearMinTerms terms somewhere; the table sums the same integers q_t as
+// the term loop, so it gives the same element.
 constexpr int kLinearMinTerms = 6;
 
 void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc, const std::vector<double> &phi,
@@ -184,7 +184,6 @@ void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc
     QSD_CUDA(cudaStreamSynchronize(s));
     std::vector<int32_t> base((size_t)G, -1);
     std::vector<uint64_t> zref;
-    std::vector<double> k64, d64;
     std::vector<int64_t> kq, dq;
     int64_t rows = 0;
     auto word = [&](const std::vector<uint64_t> &a, int w, int64_t t) { return a[(size_t)w * T + t]; };
@@ -220,9 +219,7 @@ void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc
         base[(size_t)g] = (int32_t)rows;
         for (int l = 0; l < npat; ++l) {
             const int32_t b = gptr[(size_t)g * 17 + l], e = gptr[(size_t)g * 17 + l + 1];
-            double K = 0.0;
             int64_t Kq = 0;
-            std::vector<double> d((size_t)n, 0.0);
             std::vector<int64_t> dqq((size_t)n, 0);
             for (int32_t t = b; t < e; ++t) {
                 int r = -1;
@@ -238,26 +235,19 @@ void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc
                 // popc(row & Z_t) = popc(row & Zref) + (Z_t xor Zref at r) * row_r, and
                 // row_r = v where the term survives
                 const bool neg = r >= 0 && v && zdiff;
-                const double c = neg ? -phi[(size_t)t] : phi[(size_t)t];
                 const int64_t q0 = std::llrint(phi[(size_t)t] * scale);
                 const int64_t cq = neg ? -q0 : q0;
                 if (r < 0) {
-                    K += c;
                     Kq += cq;
                 } else if (v) {
-                    d[(size_t)r] += c;
                     dqq[(size_t)r] += cq;
                 } else {
-                    K += c;
                     Kq += cq;
-                    d[(size_t)r] -= c;
                     dqq[(size_t)r] -= cq;
                 }
             }
             for (int w = 0; w < W; ++w) zref.push_back(Z[(size_t)l * W + w]);
-            k64.push_back(K);
             kq.push_back(Kq);
-            d64.insert(d64.end(), d.begin(), d.end());
             dq.insert(dq.end(), dqq.begin(), dqq.end());
             ++rows;
         }
@@ -304,14 +294,10 @@ void build_linear_ranges(qsd_ctx ctx, qsd_op op, const std::vector<int32_t> &exc
     QSD_CUDA(cudaMemcpyAsync(op->lin_base.p, base.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
     if (rows > 0) {
         op->lin_z.alloc(zref.size() * 8);
-        op->lin_k64.alloc(k64.size() * 8);
         op->lin_kq.alloc(kq.size() * 8);
-        op->lin_d64.alloc(d64.size() * 8);
         op->lin_dq.alloc(dq.size() * 8);
         QSD_CUDA(cudaMemcpyAsync(op->lin_z.p, zref.data(), zref.size() * 8, cudaMemcpyHostToDevice, s));
-        QSD_CUDA(cudaMemcpyAsync(op->lin_k64.p, k64.data(), k64.size() * 8, cudaMemcpyHostToDevice, s));
         QSD_CUDA(cudaMemcpyAsync(op->lin_kq.p, kq.data(), kq.size() * 8, cudaMemcpyHostToDevice, s));
-        QSD_CUDA(cudaMemcpyAsync(op->lin_d64.p, d64.data(), d64.size() * 8, cudaMemcpyHostToDevice, s));
         QSD_CUDA(cudaMemcpyAsync(op->lin_dq.p, dq.data(), dq.size() * 8, cudaMemcpyHostToDevice, s));
     }
     QSD_CUDA(cudaStreamSynchronize(s));
@@ -379,19 +365,14 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op) {
         op->qscale = std::ldexp(1.0, -ex);
         op->qexp = ex;
         op->trec.alloc((size_t)T * rb);
-        op->trec64.alloc((size_t)T * rb);
-        for (int pass = 0; pass < 2; ++pass) {
-            DevBuf &dst = pass ? op->trec64 : op->trec;
-            const double sc = pass ? 0.0 : scale;
-            if (W == 1)
-                k_term_records<1><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
-                                                                     op->tZ.as<uint64_t>(), op->tphi.as<double>(), sc,
-                                                                     dst.as<TermRec<1>>());
-            else
-                k_term_records<2><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
-                                                                     op->tZ.as<uint64_t>(), op->tphi.as<double>(), sc,
-                                                                     dst.as<TermRec<2>>());
-        }
+        if (W == 1)
+            k_term_records<1><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
+                                                                 op->trec.as<TermRec<1>>());
+        else
+            k_term_records<2><<<blocks_for(T, 256), 256, 0, s>>>(T, op->tP.as<uint64_t>(), op->tV.as<uint64_t>(),
+                                                                 op->tZ.as<uint64_t>(), op->tphi.as<double>(), scale,
+                                                                 op->trec.as<TermRec<2>>());
         QSD_LAUNCH_CHECK();
         QSD_CUDA(cudaStreamSynchronize(s));
         build_linear_ranges(ctx, op, exc, phi, scale);

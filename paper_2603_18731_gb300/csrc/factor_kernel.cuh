@@ -37,14 +37,12 @@ struct FacParams {
     const uint32_t *ptrA, *ptrB;  // [8 n + 1] neighbour list starts by (string, type)
     const uint2 *nbrA, *nbrB;     // (neighbour index, rank | pattern << 20 | bits << 24)
     const void *trec;             // TermRec<W> [T], fixed-point phases
-    const void *trec64;           // TermRec<W> [T], the same with the FP64 phases' bits in q
     double qscale;                // value of one fixed-point unit of the term phases, 2^-qexp
     int qexp;
     // linear ranges: first row per group (-1: none), per row Zref [W], K and
-    // d [nq] in FP64 and fixed point
+    // d [nq] in fixed point
     const int32_t *lin_base;
     const uint64_t *lin_z;
-    const double *lin_k64, *lin_d64;
     const int64_t *lin_kq, *lin_dq;
     int nq;
     // range index [rank entry][16] (nullptr: rank index then group tables)
@@ -69,14 +67,12 @@ __device__ __forceinline__ int shape_type(uint32_t occ, uint32_t emp) {
 constexpr uint32_t kKeepHalf = 0xffffffffu;
 
 // Element of group g at the row from the terms [b, e) of its ladder range:
-// each term's projector test (the ladder bits already match) and sign.
-// Two forms.  Fixed point (block products with FP64 accumulation, which
-// saturate the FP64 pipe -- 1/64 of the FP32 rate on GB300 -- with their k
-// FMAs per found column): the terms' phases in 64-bit fixed point, summed
-// exactly in integers and converted once by integer operations, exact to
-// within the rounding of each phase to a multiple of 2^-e.  FP64 adds
-// (single-column and DOT2 products, whose FP64 pipe has room): fewer
-// instructions per term than the 64-bit integer sum.
+// each term's projector test (the ladder bits already match) and sign, the
+// phases in 64-bit fixed point, summed exactly in integers and converted once
+// by integer operations -- exact to within the rounding of each phase to a
+// multiple of 2^-e.  The element thus never touches the FP64 pipe (1/64 of
+// the FP32 rate on GB300), which is left to the accumulation's FMAs; a sum of
+// FP64 adds instead kept that pipe 73 % busy in the single-column product.
 template <int W>
 __device__ __forceinline__ int64_t ladder_terms_fixed(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
                                                       const uint64_t (&key)[W]) {
@@ -94,25 +90,6 @@ __device__ __forceinline__ int64_t ladder_terms_fixed(const TermRec<W> *__restri
         sum += ok ? v : 0;
     }
     return sum;
-}
-
-template <int W>
-__device__ __forceinline__ double ladder_terms_fp64(const TermRec<W> *__restrict__ tr, int32_t b, int32_t e,
-                                                    const uint64_t (&key)[W]) {
-    double amp = 0.0;
-    for (int32_t t = b; t < e; ++t) {
-        const TermRec<W> r = load_term<W>(tr + t);
-        bool ok = true;
-        int par = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            ok &= (key[w] & r.P[w]) == r.V[w];
-            par ^= __popcll(key[w] & r.Z[w]);
-        }
-        const double ph = __longlong_as_double(r.q);  // this array holds the FP64 phases
-        if (ok) amp += (par & 1) ? -ph : ph;
-    }
-    return amp;
 }
 
 // v * 2^-ex rounded to the nearest double (ties to even), by integer
@@ -163,9 +140,7 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
     uint64_t key[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) key[w] = __ldg(p.keys + (size_t)w * p.D + row);
-    // fixed-point element sums where the FP64 pipe is the bottleneck
-    constexpr bool kFixed = PREC != QSD_FP32_DOT2 && KB > 1;
-    const TermRec<W> *__restrict__ trec = static_cast<const TermRec<W> *>(kFixed ? f.trec : f.trec64);
+    const TermRec<W> *__restrict__ trec = static_cast<const TermRec<W> *>(f.trec);
     // lane s < n_shapes: the candidate lists of shape s and their product size
     uint32_t cnt = 0;
     if (lane < e.n_shapes) {
@@ -268,21 +243,12 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
                     int par = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(f.lin_z + lr * W + w));
-                    if (kFixed) {
-                        const int64_t *__restrict__ dr = f.lin_dq + lr * f.nq;
-                        int64_t sum = __ldg(f.lin_kq + lr);
-                        for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
-                        amp = scaled_i64_to_f64((par & 1) ? -sum : sum, f.qexp);
-                    } else {
-                        const double *__restrict__ dr = f.lin_d64 + lr * f.nq;
-                        double sum = __ldg(f.lin_k64 + lr);
-                        for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
-                        amp = (par & 1) ? -sum : sum;
-                    }
-                } else if (kFixed) {
-                    amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
+                    const int64_t *__restrict__ dr = f.lin_dq + lr * f.nq;
+                    int64_t sum = __ldg(f.lin_kq + lr);
+                    for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
+                    amp = scaled_i64_to_f64((par & 1) ? -sum : sum, f.qexp);
                 } else {
-                    amp = ladder_terms_fp64<W>(trec, tb, te, key);
+                    amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
                 }
                 col = nB.x * f.nA + nA.x;
             }

@@ -216,12 +216,11 @@ struct qsd_op_s {
     qsd::DevBuf tphi_im; // double [T]
     qsd::DevBuf tflag;   // uint8  [T] bit0: P != 0, bit1: Z != 0
     qsd::DevBuf trec;    // TermRec<W> [T]: P, V, Z, fixed-point phase (W <= 2, excitation index built)
-    qsd::DevBuf trec64;  // TermRec<W> [T]: P, V, Z and the FP64 phase's bits
     // linear ranges (W <= 2): lin_base[g] = first table row of group g (-1:
-    // none), row = lin_base[g] + ladder integer; per row Zref [W], K (FP64
-    // and fixed point) and d [n] per qubit
+    // none), row = lin_base[g] + ladder integer; per row Zref [W], K and d [n]
+    // per qubit in the fixed point of trec
     int64_t n_lin_rows = 0;
-    qsd::DevBuf lin_base, lin_z, lin_k64, lin_kq, lin_d64, lin_dq;
+    qsd::DevBuf lin_base, lin_z, lin_kq, lin_dq;
     // range index: uint32 [dense entries][16], the rank index resolved by
     // ladder integer (linear-table row, or first term and length)
     bool range_ok = false;
