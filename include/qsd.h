@@ -320,6 +320,13 @@ int qsd_ramps(qsd_ctx ctx, qsd_op op, qsd_sub start, double E, double tau, int32
                                       each group's 32 lookups share cache lines.  Per row
                                       the result is bitwise that of index order (same
                                       groups, same order).  No counterpart in the paper. */
+#define QSD_TUNE_LINEAR_HALVES  6  /* sector-factored product: 1 (default) per (operator,
+                                      subspace) pair, tables of the linear ranges' sums
+                                      over each half string (built on the first product
+                                      outside a stream capture, freed with either handle);
+                                      a single-excitation element then costs two loads
+                                      instead of one per occupied qubit.  Bitwise the
+                                      same products either way.  0: no tables. */
 
 /* Set a product-path choice on a context (later products of this context
  * use it).  Results are identical up to summation order for every choice; a

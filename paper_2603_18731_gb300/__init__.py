@@ -258,9 +258,13 @@ class Context:
 
     # -- ABI calls
     def set_tuning(self, knob: int, value: int):
-        """knob 1: product path (0 auto, 1 group scan, 2 excitation index);
-        knob 2: lanes per row of the group scan (0 auto, 1, 8); knob 3:
-        autotuning of the product path on first use (1 on, 0 off)."""
+        """knob 1: product path (0 auto, 1 group scan, 2 excitation index,
+        3 half evaluation, 4 factored, 5 filter/verify); knob 2: lanes per
+        row of the group scan (0 auto, 1, 8); knob 3: autotuning of the
+        product path on first use (1 on, 0 off); knob 4: the autotuner may
+        pick the half evaluation; knob 5: row order of the lane-per-row scans
+        (0 auto, 1 index, 2 hash); knob 6: half-sum tables of the factored
+        product's linear ranges (1 on, 0 off).  See QSD_TUNE_* in qsd.h."""
         self._check(lib().qsd_set_tuning(self.handle, int(knob), int(value)))
 
     def product_path(self, op: "Operator", sub: "Subspace", precision: int = 0, k: int = 1) -> int:

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include "apply_fv.cuh"
 #include "factor_kernel.cuh"
@@ -146,6 +147,50 @@ Binding *get_binding(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
     return b;
 }
 
+// ------------------------------------------------ linear half-sum tables
+// Per (operator, subspace) pair, shared by every context that runs the pair's
+// factored product; dropped when either handle is freed.
+namespace {
+struct HalvesEntry {
+    DevBuf sa, sb;
+    bool built = false;
+};
+bool capturing(cudaStream_t s);  // below
+std::mutex g_halves_mu;
+std::map<std::pair<const void *, const void *>, std::unique_ptr<HalvesEntry>> g_halves;
+}  // namespace
+
+LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s) {
+    LinearHalves out;
+    if (!ctx->linear_halves || op->n_lin_rows <= 0 || !sub->fac.ok) return out;
+    std::lock_guard<std::mutex> lk(g_halves_mu);
+    const auto key = std::make_pair((const void *)op, (const void *)sub);
+    auto it = g_halves.find(key);
+    if (it == g_halves.end()) {
+        if (capturing(s)) return out;  // never allocate or build inside a capture
+        auto e = std::make_unique<HalvesEntry>();
+        e->built = build_linear_halves(ctx, op, sub, s, e->sa, e->sb);
+        it = g_halves.emplace(key, std::move(e)).first;
+    }
+    if (it->second->built) {
+        out.sa = it->second->sa.as<int64_t>();
+        out.sb = it->second->sb.as<int64_t>();
+    }
+    return out;
+}
+
+void drop_linear_halves(const void *handle) {
+    std::lock_guard<std::mutex> lk(g_halves_mu);
+    for (auto it = g_halves.begin(); it != g_halves.end();) {
+        if (it->first.first == handle || it->first.second == handle) it = g_halves.erase(it);
+        else ++it;
+    }
+}
+
+void prepare_product(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s) {
+    if (sub->fac.ok && op->n_lin_rows > 0) (void)linear_halves(ctx, op, sub, s);
+}
+
 void drop_bindings(qsd_ctx ctx, const void *handle) {
     if (ctx->csr.op == handle || ctx->csr.sub == handle) ctx->csr.clear();
     {
@@ -260,9 +305,13 @@ ExcParams make_exc(qsd_op op) {
     return e;
 }
 
-FacParams make_fac(qsd_op op, qsd_sub sub) {
+FacParams make_fac(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t stream) {
     const Factored &f = sub->fac;
     FacParams r{};
+    const LinearHalves lh = linear_halves(ctx, op, sub, stream);
+    r.lsA = lh.sa;
+    r.lsB = lh.sb;
+    r.nlr = op->n_lin_rows;
     r.trec = op->trec.p;
     r.qscale = op->qscale;
     r.qexp = op->qexp;
@@ -344,7 +393,7 @@ ApplyParams product_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *di
 }
 
 FacPair factored_params(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int k, const void *x, void *y) {
-    return FacPair{make_params(ctx, op, sub, diag, k, x, y), make_exc(op), make_fac(op, sub)};
+    return FacPair{make_params(ctx, op, sub, diag, k, x, y), make_exc(op), make_fac(ctx, op, sub, ctx->stream)};
 }
 
 int pack_class(qsd_ctx ctx, qsd_op op, qsd_sub sub, bool lanes8) {
@@ -468,7 +517,7 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
         const int path = product_path(ctx, op, sub, diag, precision, KB, x, y, k, c, stream, may_tune);
         if ((path == 2 || path == 7) && !have_e) {
             e = make_exc(op);
-            f = make_fac(op, sub);
+            f = make_fac(ctx, op, sub, stream);
             have_e = true;
         }
         launch_path(path, p, e, f, op->W, precision, KB, stream);
@@ -607,6 +656,7 @@ int qsd_free_op(qsd_op op) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     drop_bindings(ctx, op);
+    drop_linear_halves(op);
     delete op;
     return QSD_OK;
 }
@@ -693,6 +743,7 @@ int qsd_free_sub(qsd_sub sub) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     drop_bindings(ctx, sub);
+    drop_linear_halves(sub);
     delete sub;
     return QSD_OK;
 }
@@ -787,7 +838,7 @@ int qsd_apply_H_batch(qsd_ctx ctx, int32_t n, const qsd_op *ops, const qsd_sub *
                     ApplyParams ap = make_params(ctx, ops[i], subs[i], diag[i], k, xs[i], ys[i]);
                     ap.col0 = c;
                     if (fac) {
-                        FacPair fp{ap, make_exc(ops[i]), make_fac(ops[i], subs[i])};
+                        FacPair fp{ap, make_exc(ops[i]), make_fac(ctx, ops[i], subs[i], s)};
                         std::memcpy(h.data() + o_p + (size_t)j * rec, &fp, rec);
                     } else {
                         std::memcpy(h.data() + o_p + (size_t)j * rec, &ap, rec);
@@ -908,6 +959,10 @@ int qsd_set_tuning(qsd_ctx ctx, int32_t knob, int64_t value) {
             std::lock_guard<std::mutex> lk2(ctx->tune_mu);
             ctx->tune_cache.clear();
         }
+        return QSD_OK;
+    case QSD_TUNE_LINEAR_HALVES:
+        if (value != 0 && value != 1) return QSD_ERR_INVALID_ARG;
+        ctx->linear_halves = (int)value;
         return QSD_OK;
     case QSD_TUNE_ROW_ORDER:
         if (value < 0 || value > 2) return QSD_ERR_INVALID_ARG;

@@ -140,6 +140,27 @@ bool build_neighbours(qsd_ctx ctx, const uint64_t *L, int64_t n, int64_t cap, De
     return true;
 }
 
+// Half sums of the linear ranges (see qsd_internal.cuh): thread (i, l) adds
+// the fixed-point coefficients d_l of the qubits set in string i (qubits
+// offset + bit), plus K_l when kq is given.  Sums wrap modulo 2^64 like the
+// product's own integer sums, so S_A + S_B is bitwise K + sum over the row.
+__global__ void k_linear_halves(const uint64_t *__restrict__ strs, int64_t n, int offset,
+                                const int64_t *__restrict__ dq, const int64_t *__restrict__ kq, int nq,
+                                int64_t nlr, int64_t *out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nlr) return;
+    const int64_t i = idx / nlr, l = idx - i * nlr;
+    uint64_t str = strs[i];
+    uint64_t sum = kq ? (uint64_t)kq[l] : 0ull;
+    const int64_t *__restrict__ d = dq + (size_t)l * nq + offset;
+    while (str) {
+        const int b = __ffsll((long long)str) - 1;
+        str &= str - 1ull;
+        sum += (uint64_t)d[b];
+    }
+    out[(size_t)i * nlr + l] = (int64_t)sum;
+}
+
 }  // namespace
 
 void build_factored(qsd_ctx ctx, qsd_sub sub) {
@@ -184,6 +205,25 @@ void build_factored(qsd_ctx ctx, qsd_sub sub) {
     f.nA = nA;
     f.nB = nB;
     f.ok = true;
+}
+
+bool build_linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s, DevBuf &sa, DevBuf &sb) {
+    const Factored &f = sub->fac;
+    const int64_t nlr = op->n_lin_rows;
+    if (!f.ok || nlr <= 0 || op->lin_dq.p == nullptr || op->exc_split != f.split) return false;
+    // at most 1 GiB per pair (the 32-orbital workload: 3968 rows x 3000 strings x 8 B = 95 MB)
+    if ((double)nlr * (double)(f.nA + f.nB) * 8.0 > (double)(1ull << 30)) return false;
+    sa.alloc((size_t)(f.nA * nlr) * 8);
+    sb.alloc((size_t)(f.nB * nlr) * 8);
+    const int nq = op->n_qubits;
+    k_linear_halves<<<blocks_for(f.nA * nlr, 256), 256, 0, s>>>(f.A.as<uint64_t>(), f.nA, 0, op->lin_dq.as<int64_t>(),
+                                                                op->lin_kq.as<int64_t>(), nq, nlr, sa.as<int64_t>());
+    k_linear_halves<<<blocks_for(f.nB * nlr, 256), 256, 0, s>>>(f.B.as<uint64_t>(), f.nB, f.split,
+                                                                op->lin_dq.as<int64_t>(), nullptr, nq, nlr,
+                                                                sb.as<int64_t>());
+    QSD_LAUNCH_CHECK();
+    QSD_CUDA(cudaStreamSynchronize(s));
+    return true;
 }
 
 }  // namespace qsd

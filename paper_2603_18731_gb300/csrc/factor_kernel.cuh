@@ -47,6 +47,10 @@ struct FacParams {
     int nq;
     // range index [rank entry][16] (nullptr: rank index then group tables)
     const uint32_t *rix;
+    // half sums of the linear ranges, [nA][nlr] (K included) and [nB][nlr]
+    // (nullptr: sum the row's occupied qubits' coefficients)
+    const int64_t *lsA, *lsB;
+    int64_t nlr;
     uint32_t nA, nB;
     int split;
 };
@@ -243,10 +247,18 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
                     int par = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) par ^= __popcll(key[w] & __ldg(f.lin_z + lr * W + w));
-                    const int64_t *__restrict__ dr = f.lin_dq + lr * f.nq;
-                    int64_t sum = __ldg(f.lin_kq + lr);
-                    for (int i = 0; i < nocc; ++i) sum += __ldg(dr + occ[wib][i]);
-                    amp = scaled_i64_to_f64((par & 1) ? -sum : sum, f.qexp);
+                    // (sums modulo 2^64, exact when the element fits)
+                    uint64_t sum;
+                    if (f.lsA) {
+                        sum = (uint64_t)__ldg(f.lsA + (size_t)ia * f.nlr + lr) +
+                              (uint64_t)__ldg(f.lsB + (size_t)ib * f.nlr + lr);
+                    } else {
+                        const int64_t *__restrict__ dr = f.lin_dq + lr * f.nq;
+                        sum = (uint64_t)__ldg(f.lin_kq + lr);
+                        for (int i = 0; i < nocc; ++i) sum += (uint64_t)__ldg(dr + occ[wib][i]);
+                    }
+                    const int64_t v = (int64_t)sum;
+                    amp = scaled_i64_to_f64((par & 1) ? -v : v, f.qexp);
                 } else {
                     amp = scaled_i64_to_f64(ladder_terms_fixed<W>(trec, tb, te, key), f.qexp);
                 }

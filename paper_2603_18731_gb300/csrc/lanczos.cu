@@ -888,6 +888,8 @@ void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int prod
     s = st;
     B = dot_blocks(D, ctx->num_sms);
     nbD = blocks_for(D, 256);
+    // whatever the product builds on first use, before any chunk is captured
+    prepare_product(ctx, op, sub, st);
     const size_t sv = fp32 ? 4 : 8;
     auto A = [&](DevBuf &b, size_t n) {
         if (stream_ordered) b.alloc_async(n, s);

@@ -112,6 +112,7 @@ struct qsd_ctx_s {
     int allow_sym = 0;    // the autotuner may pick the half-evaluation product
     int row_order = 0;    // lane-per-row scans: 0 auto, 1 index order, 2 hash order
     int autotune = 1;     // measure the product paths on first use and cache the fastest
+    int linear_halves = 1;  // factored product: half sums of the linear ranges per pair
     std::mutex tune_mu;
     std::map<std::tuple<const void *, const void *, int, int>, int> tune_cache;
     cudaStream_t stream = nullptr;
@@ -487,6 +488,25 @@ void build_excitation_index(qsd_ctx ctx, qsd_op op);
 // Sector-factored index of the subspace at split n / 2 (n <= 128), kept only
 // when the subspace is the product of its distinct halves.
 void build_factored(qsd_ctx ctx, qsd_sub sub);
+// Half sums of the operator's linear ranges over the subspace's two half
+// lists: sa [nA][n_lin_rows] = K + sum of d over the qubits set in A[i],
+// sb [nB][n_lin_rows] = sum of d over the qubits set in B[i] (shifted by the
+// split), int64 fixed point.  A linear candidate of row (ia, ib) then sums
+// two entries instead of one per occupied qubit.  False (nothing allocated)
+// when the pair has no linear ranges or the tables would exceed 1 GiB;
+// synchronises s.
+bool build_linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s, DevBuf &sa, DevBuf &sb);
+// The pair's half-sum tables, built on first use on stream s outside a stream
+// capture (nullptr pointers: not built, or disabled); cached per (operator,
+// subspace) until either is freed.
+struct LinearHalves {
+    const int64_t *sa = nullptr, *sb = nullptr;
+};
+LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s);
+// Everything a product of (op, sub) builds on first use, done now (outside any
+// capture): call before capturing products into a graph.
+void prepare_product(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s);
+void drop_linear_halves(const void *handle);
 // Candidate flip masks per row of the excitation path for the subspace's
 // first string, or -1 when the operator has no excitation index.
 double excitation_candidates(qsd_op op, qsd_sub sub);

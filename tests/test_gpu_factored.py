@@ -156,3 +156,33 @@ def test_factored_ground_energy(ctx, prec):
     e, info = ctx.lanczos_ground_state(h, sub, precision=prec, max_steps=300, tol=1e-9, check=False)
     e_ref = oracle.ground_energy(op, keys)
     assert abs(e - e_ref) <= (1e-10 if prec == 0 else 1e-7) * abs(e_ref), (e, e_ref, info)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("k", [1, 16])
+def test_linear_half_sums_are_bitwise_the_term_sums(ctx, prec, k):
+    # the per-pair half-sum tables of the linear ranges (K plus the
+    # coefficients of each half string's occupied qubits) give the same
+    # fixed-point integers as summing the row's coefficients: bitwise equal
+    # products, on a fresh pair (tables off, then built on first use)
+    import torch
+    import paper_2603_18731_gb300 as q
+    op, words, _, _ = chem_case(10, 4, 60, 50, seed=11)
+    h = ctx.load_operator(op)
+    sub = ctx.build_subspace(20, words)
+    assert h.info()["n_linear_ranges"] > 0
+    rng = np.random.default_rng(3 + k)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
+    xt = to_cuda(ctx, x, torch.float64 if prec == q.QSD_FP64 else torch.float32)
+    ctx.set_tuning(6, 0)
+    y_off = ctx.apply_H(h, sub, xt, precision=prec)
+    ctx.set_tuning(6, 1)
+    y_on = ctx.apply_H(h, sub, xt, precision=prec)
+    ctx.synchronize()
+    assert torch.equal(y_on, y_off)
+    keys = oracle.sort_unique(words)
+    xr = x if prec == q.QSD_FP64 else x.astype(np.float32).astype(np.float64)
+    tol = FP64_TOL if prec == q.QSD_FP64 else FP32_TOL
+    assert rel_err(y_on.cpu().double().numpy(), oracle.apply(op, keys, xr).real) <= tol
+    sub.free()
+    h.free()

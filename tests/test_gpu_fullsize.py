@@ -98,6 +98,22 @@ def test_chem_full_size_structure(ctx, chem):
     assert ctx.product_path(h, sub, 0, 16) == 7 and ctx.product_path(h, sub, 1, 16) == 7
 
 
+def test_chem_full_size_linear_half_sums_bitwise(ctx, chem):
+    # 3,968 linear-range rows over 1500 + 1500 half strings: the half-sum
+    # tables give bitwise the product that sums each row's coefficients
+    import torch
+    op, h, sub, keys = chem
+    x = np.random.default_rng(5).normal(size=sub.dim)
+    with torch.cuda.stream(ctx.stream):
+        xt = torch.as_tensor(x, device=ctx.device)
+    y_on = ctx.apply_H(h, sub, xt)
+    ctx.set_tuning(6, 0)
+    y_off = ctx.apply_H(h, sub, xt)
+    ctx.set_tuning(6, 1)
+    ctx.synchronize()
+    assert torch.equal(y_on, y_off)
+
+
 @pytest.mark.parametrize("prec,k", [(0, 1), (0, 16), (1, 16)])
 def test_chem_full_size_sampled_rows(ctx, chem, prec, k):
     op, h, sub, keys = chem
