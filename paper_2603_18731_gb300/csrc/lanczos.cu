@@ -34,7 +34,8 @@ namespace qsd {
 // Row blocks of the dot passes: about 1024 rows per block (four rows per
 // thread per vector) for large subspaces, at most four blocks per SM; small
 // subspaces keep at least min(D / 256, 2 per SM) blocks (measured on GB300:
-// XXZ 300,000 rows 304 blocks, Ising 1 M rows 608, TFIM 4096 rows 16).
+// XXZ 300,000 rows 304 blocks, Ising 1 M rows 608, TFIM 4096 rows 16; 256-row
+// blocks, up to eight per SM, made the XXZ pass slower, 31.9 against 27.2 us).
 int dot_blocks(int64_t D, int num_sms) {
     const int64_t by_rows = (D + 1023) / 1024;
     const int64_t floor_blocks = std::min<int64_t>((D + 255) / 256, 2 * (int64_t)num_sms);
@@ -72,7 +73,10 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t i) {
 
 __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, int *jdev) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *jdev = 0;
+    if (i == 0) {
+        jdev[0] = 0;  // the step
+        jdev[2] = 0;  // the block count of k_sub_sq
+    }
     if (i >= D) return;
     w[i] = v0 ? v0[i] : uniform_pm1(seed, (uint64_t)i);
 }
@@ -83,30 +87,57 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
 
 // partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j.
 // Warp w of the block takes the vectors i = w, w + 8, ...: its lanes stride
-// the block's rows (coalesced; the block's slice of u stays in L1 across the
-// vectors), four loads in flight per lane, and one warp reduction per vector
-// -- no block barrier.  A fixed order: the result is deterministic.
+// the block's rows (coalesced; the block's slice of u stays in L1), four rows
+// per lane per round, and one warp reduction per vector -- no block barrier.
+// The vectors go two at a time, then one (each round loads u once for both:
+// 12 loads in flight per lane, no predicated loads);
+// per vector the sum runs in the same fixed order whatever the grouping, so
+// the result is deterministic.
+template <int G, typename TV, typename TU>
+__device__ __forceinline__ void gemv_t_group(const TV *__restrict__ V, int64_t D, int i0, int nw,
+                                             const TU *__restrict__ u, int64_t r0, int64_t r1, double *partial,
+                                             int vb, int B) {
+    const int lane = threadIdx.x & 31;
+    const TV *__restrict__ vi[G];
+    double s0[G], s1[G], s2[G], s3[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        vi[g] = V + (size_t)(i0 + g * nw) * D;
+        s0[g] = s1[g] = s2[g] = s3[g] = 0.0;
+    }
+    int64_t r = r0 + lane;
+    for (; r + 96 < r1; r += 128) {
+        const double u0 = (double)u[r], u1 = (double)u[r + 32], u2 = (double)u[r + 64], u3 = (double)u[r + 96];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            s0[g] = fma((double)vi[g][r], u0, s0[g]);
+            s1[g] = fma((double)vi[g][r + 32], u1, s1[g]);
+            s2[g] = fma((double)vi[g][r + 64], u2, s2[g]);
+            s3[g] = fma((double)vi[g][r + 96], u3, s3[g]);
+        }
+    }
+    for (; r < r1; r += 32) {
+        const double u0 = (double)u[r];
+#pragma unroll
+        for (int g = 0; g < G; ++g) s0[g] = fma((double)vi[g][r], u0, s0[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const double t = warp_sum((s0[g] + s1[g]) + (s2[g] + s3[g]));
+        if (lane == 0) partial[(size_t)(i0 + g * nw) * B + vb] = t;
+    }
+}
+
 template <typename TV, typename TU>
 __device__ void gemv_t_body(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u,
                             double *partial, int vb, int B, double *sh) {
     (void)sh;
     const int64_t chunk = (D + B - 1) / B;
     const int64_t r0 = (int64_t)vb * chunk, r1 = min(D, r0 + chunk);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < nvec; i += nw) {
-        const TV *__restrict__ vi = V + (size_t)i * D;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int64_t r = r0 + lane;
-        for (; r + 96 < r1; r += 128) {
-            s0 = fma((double)vi[r], (double)u[r], s0);
-            s1 = fma((double)vi[r + 32], (double)u[r + 32], s1);
-            s2 = fma((double)vi[r + 64], (double)u[r + 64], s2);
-            s3 = fma((double)vi[r + 96], (double)u[r + 96], s3);
-        }
-        for (; r < r1; r += 32) s0 = fma((double)vi[r], (double)u[r], s0);
-        const double t = warp_sum((s0 + s1) + (s2 + s3));
-        if (lane == 0) partial[(size_t)i * B + vb] = t;
-    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int i = warp;
+    for (; i + nw < nvec; i += 2 * nw) gemv_t_group<2>(V, D, i, nw, u, r0, r1, partial, vb, B);
+    if (i < nvec) gemv_t_group<1>(V, D, i, nw, u, r0, r1, partial, vb, B);
 }
 constexpr int kGemvSh = 32;
 
@@ -206,16 +237,19 @@ __global__ void k_incr(int *jdev) { *jdev += 1; }
 
 // ---- fused tail of one step (single-job path)
 // The second Gram-Schmidt subtraction also sums w^2 per 256-row block
-// (k_sub_sq), and every block of k_norm_next sums those partials itself (in
-// block order, so all agree) before writing v_{j+1} = w / beta_{j+1}: 8
-// launches per step instead of 11, with the subtraction's full grid.
+// (k_sub_sq); the last of its blocks to finish (an atomic count, no waiting)
+// sums those partials in block order into beta_{j+1}, and k_norm_next writes
+// v_{j+1} = w beta_{j+1}^-1: 8 launches per step, the subtraction's full
+// grid, and the norm summed once.
 
-// w[r] -= sum_{i<=j} V[i][r] h[i]; part[b] = sum over the block's rows of w^2
+// w[r] -= sum_{i<=j} V[i][r] h[i]; part[b] = sum over the block's rows of
+// w^2; the last block: beta[j+1] = sqrt(sum_b part[b]), count back to 0
 template <typename TV>
 __global__ void k_sub_sq(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                         const double *__restrict__ h, double *w, double *part) {
+                         const double *__restrict__ h, double *w, double *part, unsigned *count, double *beta) {
     extern __shared__ double hs[];
     __shared__ double sh[32];
+    __shared__ bool last;
     const int nvec = *jdev + 1;
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
@@ -228,23 +262,32 @@ __global__ void k_sub_sq(const TV *__restrict__ V, int64_t D, const int *__restr
         sq = acc * acc;
     }
     sq = block_sum(sq, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = sq;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sq;
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+#pragma unroll 8
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) {
+        beta[nvec] = sqrt(t);
+        *count = 0u;
+    }
 }
 
 template <typename TV>
-__global__ void k_norm_next(const double *__restrict__ w, const double *__restrict__ part, int B,
-                            const int *__restrict__ jdev, int64_t D, int m, TV *V, TV *vcur, double *beta) {
-    __shared__ double sh[32];
-    __shared__ double nrm;
-    double t = 0.0;
-    for (int b = threadIdx.x; b < B; b += blockDim.x) t += part[b];
-    t = block_sum(t, sh);
-    if (threadIdx.x == 0) nrm = sqrt(t);
-    __syncthreads();
+__global__ void k_norm_next(const double *__restrict__ w, const int *__restrict__ jdev, int64_t D, int m, TV *V,
+                            TV *vcur, const double *__restrict__ beta) {
     const int j1 = *jdev + 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) beta[j1] = nrm;
+    const double nrm = beta[j1];
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x) {
-        const TV v = (TV)(nrm > 0.0 ? w[r] / nrm : 0.0);
+        const TV v = (TV)(w[r] * inv);
         if (j1 <= m) V[(size_t)j1 * D + r] = v;
         vcur[r] = v;
     }
@@ -290,22 +333,31 @@ __global__ void k_residual(const double *__restrict__ hu, const double *__restri
 // rate and a division costs several of its operations; the pair (p_{k-1},
 // p_k) is rescaled by 2^-600 whenever it grows past 2^600, and by 2^600 when
 // both fall below 2^-600 (exact scalings that keep every sign).
-__device__ int sturm(const double *a, const double *b, int m, double x) {
+__device__ int sturm(const double *a, const double *bb, int m, double x) {
+    // bb[i] = b_i^2.  Signs, zeros and the rescaling tests read the IEEE
+    // encodings with integer operations: per step the FP64 pipe (1/64 of the
+    // FP32 rate, shared by the 64 points on one SM) sees one add, one
+    // multiply and one FMA.  Thresholds 2^601 and 2^-600 (exponent fields
+    // 1624 and 423): scaling by a power of two is exact and keeps every sign.
+    auto expo = [](double v) { return ((uint32_t)__double2hiint(v) >> 20) & 0x7ffu; };
     int c = 0;
     double p0 = 1.0, p1 = a[0] - x;
-    bool neg = p1 < 0.0 || (p1 == 0.0);  // p_1 of sign opposite to p_0 = 1
+    long long bits = __double_as_longlong(p1);
+    bool neg = bits < 0 || (bits << 1) == 0;  // p_1 of sign opposite to p_0 = 1 (zero included)
     c += neg;
     for (int i = 1; i < m; ++i) {
-        double p2 = fma(a[i] - x, p1, -(b[i] * b[i]) * p0);
-        if (fabs(p2) > 0x1p600 || fabs(p1) > 0x1p600) {
+        double p2 = fma(a[i] - x, p1, -bb[i] * p0);
+        const uint32_t e1 = expo(p1), e2 = expo(p2);
+        if (e2 >= 1624u || e1 >= 1624u) {
             p2 *= 0x1p-600;
             p1 *= 0x1p-600;
-        } else if (fabs(p2) < 0x1p-600 && fabs(p1) < 0x1p-600) {
+        } else if (e2 < 423u && e1 < 423u) {
             p2 *= 0x1p600;
             p1 *= 0x1p600;
         }
         const bool prev_neg = neg;
-        neg = p2 < 0.0 || (p2 == 0.0 && !prev_neg);
+        bits = __double_as_longlong(p2);
+        neg = (bits << 1) == 0 ? !prev_neg : bits < 0;
         c += (neg != prev_neg);
         p0 = p1;
         p1 = p2;
@@ -346,22 +398,26 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
         lo_hi[0] = lo - pad;
         lo_hi[1] = hi + pad;
     }
+    // b_i^2 for the Sturm counts, in the eigenvector's space (free until then)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = b[i] * b[i];
     __syncthreads();
     // multisection: the first kTriPoints threads test one interior point
     // each; the Sturm count is monotone in x, so the number of points with no
     // eigenvalue below them is the index of the subinterval that holds the
     // lowest one.  Stop at a few ulps, or when rounding stops the shrinking.
     constexpr int kTriPoints = 64;
+    constexpr double kStep = 1.0 / (kTriPoints + 1);  // point q at lo + (hi - lo) (q kStep): the same
+                                                       // expression for a point and for the bound it becomes
     for (int it = 0; it < 64; ++it) {
         const double lo = lo_hi[0], hi = lo_hi[1];
         bool below = false;
         if (threadIdx.x < kTriPoints) {
-            const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(kTriPoints + 1);
-            below = sturm(a, b, m, x) < 1;
+            const double x = lo + (hi - lo) * ((double)(threadIdx.x + 1) * kStep);
+            below = sturm(a, s, m, x) < 1;
         }
         const int k = __syncthreads_count(below);
-        const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(kTriPoints + 1);
-        const double nhi = k == kTriPoints ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(kTriPoints + 1);
+        const double nlo = k == 0 ? lo : lo + (hi - lo) * ((double)k * kStep);
+        const double nhi = k == kTriPoints ? hi : lo + (hi - lo) * ((double)(k + 1) * kStep);
         __syncthreads();
         if (threadIdx.x == 0) {
             lo_hi[0] = nlo;
@@ -407,6 +463,9 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
         }
     }
     if (fabs(D_[m - 1]) < tiny) D_[m - 1] = D_[m - 1] >= 0 ? tiny : -tiny;
+    // the pivots' reciprocals, once: the iterations below multiply (an FP64
+    // division costs several operations of the slow FP64 pipe, serially here)
+    for (int i = 0; i < m; ++i) D_[i] = 1.0 / D_[i];
     for (int i = 0; i < m; ++i) s[i] = 1.0;
     for (int iter = 0; iter < 3; ++iter) {
         for (int i = 0; i + 1 < m; ++i) {
@@ -422,12 +481,12 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
             double v = s[i];
             if (i + 1 < m) v -= U1[i] * s[i + 1];
             if (i + 2 < m) v -= U2[i] * s[i + 2];
-            s[i] = v / D_[i];
+            s[i] = v * D_[i];
         }
         double nrm = 0.0;
         for (int i = 0; i < m; ++i) nrm += s[i] * s[i];
-        nrm = sqrt(nrm);
-        for (int i = 0; i < m; ++i) s[i] /= nrm;
+        const double inv = 1.0 / sqrt(nrm);
+        for (int i = 0; i < m; ++i) s[i] *= inv;
     }
     out[0] = theta;
     out[1] = fabs(beta[m] * s[m - 1]);
@@ -596,18 +655,20 @@ __global__ void kq_norm_next(const PackJob *__restrict__ jobs, const int *__rest
         const int64_t D = J.D;
         const double *__restrict__ part = J.part + (size_t)(m + 2) * J.B;
         double t = 0.0;
+#pragma unroll 8
         for (int k = threadIdx.x; k < nbD; k += blockDim.x) t += part[k];
         t = block_sum(t, sh);
         if (threadIdx.x == 0) nrm_s = sqrt(t);
         __syncthreads();
         const double nrm = nrm_s;
+        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
         const int j1 = j + 1;
         if (vb == 0 && threadIdx.x == 0) J.beta[j1] = nrm;
         TV *V = static_cast<TV *>(const_cast<void *>(J.V));
         TV *vc = static_cast<TV *>(J.vcur);
         const double *__restrict__ w = J.w;
         for (int64_t r = (int64_t)vb * blockDim.x + threadIdx.x; r < D; r += (int64_t)nb * blockDim.x) {
-            const TV v = (TV)(nrm > 0.0 ? w[r] / nrm : 0.0);
+            const TV v = (TV)(w[r] * inv);
             if (j1 <= m) V[(size_t)j1 * D + r] = v;
             vc[r] = v;
         }
@@ -948,6 +1009,7 @@ static void enqueue_steps_t(LanczosJob &J, int n) {
     const size_t hsm = (size_t)(J.m + 1) * 8;
     // squares of w per 256-row block after the partial dots
     double *psq = part + (size_t)(J.m + 2) * J.B;
+    unsigned *count = reinterpret_cast<unsigned *>(J.jdev.as<int>() + 2);
     const int nb = std::min<int>(J.nbD, 4 * ctx_sms(J.ctx));
     for (int t = 0; t < n; ++t) {
         apply_H(J.ctx, J.op, J.sub, J.diag, J.prec, 1, vc, hv, s);
@@ -956,8 +1018,8 @@ static void enqueue_steps_t(LanczosJob &J, int n) {
         k_gemv_sub<TV, TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, hv, w);
         k_gemv_t<TV, double><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, w, part);
         k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
-        k_sub_sq<TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, psq);
-        k_norm_next<TV><<<nb, 256, 0, s>>>(w, psq, J.nbD, j, J.D, J.m, V, vc, beta);
+        k_sub_sq<TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, psq, count, beta);
+        k_norm_next<TV><<<nb, 256, 0, s>>>(w, j, J.D, J.m, V, vc, beta);
         k_incr<<<1, 1, 0, s>>>(J.jdev.as<int>());
     }
     k_tridiag<<<1, kLanczosThreads, tri_smem(J.m), s>>>(alpha, beta, j, J.tri.as<double>());
