@@ -160,14 +160,14 @@ std::mutex g_halves_mu;
 std::map<std::pair<const void *, const void *>, std::unique_ptr<HalvesEntry>> g_halves;
 }  // namespace
 
-LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s) {
+LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s, bool may_build) {
     LinearHalves out;
     if (!ctx->linear_halves || op->n_lin_rows <= 0 || !sub->fac.ok) return out;
     std::lock_guard<std::mutex> lk(g_halves_mu);
     const auto key = std::make_pair((const void *)op, (const void *)sub);
     auto it = g_halves.find(key);
     if (it == g_halves.end()) {
-        if (capturing(s)) return out;  // never allocate or build inside a capture
+        if (!may_build || capturing(s)) return out;  // never allocate or build inside a capture
         auto e = std::make_unique<HalvesEntry>();
         e->built = build_linear_halves(ctx, op, sub, s, e->sa, e->sb);
         it = g_halves.emplace(key, std::move(e)).first;
@@ -305,10 +305,10 @@ ExcParams make_exc(qsd_op op) {
     return e;
 }
 
-FacParams make_fac(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t stream) {
+FacParams make_fac(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t stream, bool may_build = true) {
     const Factored &f = sub->fac;
     FacParams r{};
-    const LinearHalves lh = linear_halves(ctx, op, sub, stream);
+    const LinearHalves lh = linear_halves(ctx, op, sub, stream, may_build);
     r.lsA = lh.sa;
     r.lsB = lh.sb;
     r.nlr = op->n_lin_rows;
@@ -504,12 +504,34 @@ int product_path(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int pr
     return best;
 }
 
+namespace {
+__global__ void k_widen(const float *__restrict__ x, int64_t n, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)x[i];
+}
+}  // namespace
+
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k, const void *x, void *y,
-             cudaStream_t stream, bool may_tune) {
+             cudaStream_t stream, bool may_tune, bool may_allocate) {
     ApplyParams p = make_params(ctx, op, sub, diag, k, x, y);
     ExcParams e{};
     FacParams f{};
     bool have_e = false;
+    // FP32-mixed block products on the factored path: x widened exactly to
+    // FP64 once (context scratch), then the FP64 block kernel with FP32 y --
+    // bitwise the same product, without a conversion per gathered value
+    // (which cost the gather loop 15 % more instructions and a block of
+    // residency per SM)
+    const double *xw = nullptr;
+    if (precision == QSD_FP32_MIXED && k >= 4 && may_allocate && stream == ctx->stream && sub->D > 0 &&
+        use_factored(ctx, op, sub) && !capturing(stream)) {
+        const int64_t n = sub->D * (int64_t)k;
+        double *buf = static_cast<double *>(ctx->scratch[4].get((size_t)n * 8));
+        k_widen<<<(unsigned)std::min<int64_t>(blocks_for(n, 256), 8 * (int64_t)ctx->num_sms), 256, 0, stream>>>(
+            static_cast<const float *>(x), n, buf);
+        QSD_LAUNCH_CHECK();
+        xw = buf;
+    }
     int64_t c = 0;
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
@@ -517,10 +539,16 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
         const int path = product_path(ctx, op, sub, diag, precision, KB, x, y, k, c, stream, may_tune);
         if ((path == 2 || path == 7) && !have_e) {
             e = make_exc(op);
-            f = make_fac(ctx, op, sub, stream);
+            f = make_fac(ctx, op, sub, stream, may_allocate);
             have_e = true;
         }
-        launch_path(path, p, e, f, op->W, precision, KB, stream);
+        if (path == 7 && xw && KB > 1) {
+            ApplyParams pw = p;
+            pw.x = xw;
+            launch_apply_fac<kPrecWideX>(pw, e, f, op->W, KB, stream);
+        } else {
+            launch_path(path, p, e, f, op->W, precision, KB, stream);
+        }
         c += KB;
     }
 }

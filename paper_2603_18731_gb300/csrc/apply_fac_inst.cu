@@ -1,7 +1,9 @@
 // Instantiations of the sector-factored product for one precision mode.
 //
-// The build compiles this file once per mode with -DQSD_PREC=0, 1 or 2
-// (QSD_FP64, QSD_FP32_MIXED, QSD_FP32_DOT2).
+// The build compiles this file once per mode with -DQSD_PREC=0, 1, 2 or 3
+// (QSD_FP64, QSD_FP32_MIXED, QSD_FP32_DOT2, and kPrecWideX: the FP32-mixed
+// block products on a widened copy of x -- block kernels only, no packed
+// variants).
 #include <algorithm>
 
 #include "factor_kernel.cuh"
@@ -21,9 +23,16 @@ void launch_kb(const ApplyParams &p, const ExcParams &e, const FacParams &f, int
     switch (KB) {
     case 16: k_apply_fac<W, 16, kPrec><<<(unsigned)blocks, 256, 0, s>>>(p, e, f); break;
     case 4: k_apply_fac<W, 4, kPrec><<<(unsigned)blocks, 256, 0, s>>>(p, e, f); break;
-    default: k_apply_fac<W, 1, kPrec><<<(unsigned)blocks, 256, 0, s>>>(p, e, f); break;
+    default:
+#if QSD_PREC == 3
+        fail(QSD_ERR_INTERNAL, "factored product on widened x: block widths 4 and 16 only");
+#else
+        k_apply_fac<W, 1, kPrec><<<(unsigned)blocks, 256, 0, s>>>(p, e, f);
+#endif
+        break;
     }
 }
+#if QSD_PREC != 3
 template <int W, int KB>
 int fac_resident_blocks() {
     static const int n = [] {
@@ -52,8 +61,10 @@ void launch_queue_kb(const FacPair *params, const int64_t *tile0, TileQueue *q, 
     default: launch_queue_one<W, 1>(params, tile0, q, max_tiles, num_sms, s); break;
     }
 }
+#endif
 }  // namespace
 
+#if QSD_PREC != 3
 template <>
 void launch_apply_fac_queue<kPrec>(const FacPair *params, const int64_t *tile0, TileQueue *q, int64_t max_tiles,
                                    int W, int KB, int num_sms, cudaStream_t s) {
@@ -63,6 +74,8 @@ void launch_apply_fac_queue<kPrec>(const FacPair *params, const int64_t *tile0, 
     else launch_queue_kb<2>(params, tile0, q, max_tiles, KB, num_sms, s);
     QSD_LAUNCH_CHECK();
 }
+
+#endif
 
 template <>
 void launch_apply_fac<kPrec>(const ApplyParams &p, const ExcParams &e, const FacParams &f, int W, int KB,

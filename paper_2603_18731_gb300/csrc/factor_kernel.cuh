@@ -55,6 +55,12 @@ struct FacParams {
     int split;
 };
 
+// Internal precision mode of the factored block products: FP64 arithmetic on
+// an FP64 copy of an FP32 x (widened exactly, once per product), FP32 y --
+// the FP32-mixed product, bitwise, with the per-value conversion out of the
+// gather loop.
+constexpr int kPrecWideX = 3;
+
 // The parameters of one pair of a packed factored product.
 struct FacPair {
     ApplyParams p;
@@ -126,7 +132,13 @@ __device__ __forceinline__ double scaled_i64_to_f64(int64_t v, int ex) {
 template <int W, int KB, int PREC>
 __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e, const FacParams &f,
                                         const int64_t row) {
-    using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
+    // x and y storage, and the arithmetic: PREC, or for kPrecWideX FP64
+    // arithmetic on an exact FP64 copy of FP32 x with FP32 y (bitwise the
+    // FP32-mixed product, without a conversion per gathered value)
+    constexpr bool kWideX = PREC == kPrecWideX;
+    constexpr int AP = kWideX ? QSD_FP64 : PREC;
+    using TIO = typename std::conditional<AP == QSD_FP64, double, float>::type;  // x
+    using TY = typename std::conditional<PREC == QSD_FP64, double, float>::type;  // y
     static_assert(32 % KB == 0, "KB divides the warp");
     constexpr int NC = 32 / KB;  // candidates per gather instruction
     __shared__ uint32_t pre[8][kMaxShapes + 1];  // per warp: first candidate of each shape
@@ -284,10 +296,10 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
             // each lane its own candidate
             if (nz) {
                 const TIO xv = __ldg(x + (size_t)col * p.ld);
-                if (PREC == QSD_FP32_DOT2) {
+                if (AP == QSD_FP32_DOT2) {
                     const float ah = (float)amp, al = (float)(amp - (double)ah);
                     dot2_add(as, ae, ah, al, (float)xv);
-                } else if (PREC == QSD_FP32_MIXED) {
+                } else if (AP == QSD_FP32_MIXED) {
                     acc = fma(amp, f32_to_f64((float)xv), acc);
                 } else {
                     acc = fma(amp, (double)xv, acc);
@@ -297,7 +309,7 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
         }
         const uint32_t found = __ballot_sync(0xffffffffu, nz);
         if (!found) continue;
-        if (PREC == QSD_FP32_DOT2) {
+        if (AP == QSD_FP32_DOT2) {
             // KB lanes per candidate, NC candidates per load instruction: the
             // element's FP32 (hi, lo) split once, in the candidate's lane, and
             // broadcast by shuffles
@@ -327,7 +339,7 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
         for (int i0 = 0; i0 < full; i0 += NC) {
             const int src = i0 + lane / KB;
             const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
-            if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
+            if (AP == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
             else acc = fma(camp[wib][src], (double)xv, acc);
         }
         pend = tot - full;
@@ -346,19 +358,19 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
         }
         __syncwarp();
     }
-    if (KB > 1 && PREC != QSD_FP32_DOT2 && pend > 0) {
+    if (KB > 1 && AP != QSD_FP32_DOT2 && pend > 0) {
         // the last pending candidates: one partial gather
         const int src = lane / KB;
         if (src < pend) {
             const TIO xv = __ldg(x + (size_t)ccol[wib][src] * p.ld);
-            if (PREC == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
+            if (AP == QSD_FP32_MIXED) acc = fma(camp[wib][src], f32_to_f64((float)xv), acc);
             else acc = fma(camp[wib][src], (double)xv, acc);
         }
     }
     // lanes with the same column (lane % KB) hold parts of its sum
 #pragma unroll
     for (int o = KB; o < 32; o <<= 1) {
-        if (PREC == QSD_FP32_DOT2) {
+        if (AP == QSD_FP32_DOT2) {
             const float s2 = __shfl_xor_sync(0xffffffffu, as, o);
             const float e2 = __shfl_xor_sync(0xffffffffu, ae, o);
             dot2_merge(as, ae, s2, e2);
@@ -369,13 +381,13 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
     if (lane < KB) {
         const double d = __ldg(p.diag + row);
         const TIO xr = __ldg(x + row * p.ld);
-        TIO *yr = static_cast<TIO *>(p.y) + row * p.ld + p.col0 + lane;
-        if (PREC == QSD_FP32_DOT2) {
+        TY *yr = static_cast<TY *>(p.y) + row * p.ld + p.col0 + lane;
+        if (AP == QSD_FP32_DOT2) {
             const float dh = (float)d, dl = (float)(d - (double)dh);
             dot2_add(as, ae, dh, dl, (float)xr);
-            *yr = (TIO)(as + ae);
+            *yr = (TY)(as + ae);
         } else {
-            *yr = (TIO)fma(d, (double)xr, acc);
+            *yr = (TY)fma(d, (double)xr, acc);
         }
     }
 }

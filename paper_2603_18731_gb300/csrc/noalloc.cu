@@ -142,7 +142,7 @@ extern "C" int qsd_rayleigh_quotient_noalloc(qsd_ctx ctx, qsd_op op, qsd_sub sub
         const int nb = (int)std::min<int64_t>(kNoAllocBlocks, (D + kNoAllocThreads - 1) / kNoAllocThreads);
         // every value below is written before it is read: nothing to clear
         compute_diagonal(ctx, op, sub, diag);
-        apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu, s);
+        apply_H(ctx, op, sub, diag, QSD_FP64, 1, u, hu, s, false, false);
         k_nb_dots<<<nb, kNoAllocThreads, 0, s>>>(u, hu, D, part_a, part_b);
         k_nb_finish<<<1, kNoAllocThreads, 0, s>>>(part_a, part_b, nb, sc, 0);  // sc[0] = u.Hu, sc[1] = u.u
         k_nb_resid<<<nb, kNoAllocThreads, 0, s>>>(u, hu, D, sc, part_a);

@@ -120,7 +120,7 @@ struct qsd_ctx_s {
     int num_sms = 0;
     std::string last_error;
     std::mutex mu;
-    qsd::Scratch scratch[4];
+    qsd::Scratch scratch[5];  // 0, 1: host-buffer products; 2, 3: residuals; 4: widened x
     // (operator, subspace) -> cached diagonal; dropped when either is freed
     std::map<std::pair<const void *, const void *>, qsd::Binding *> bindings;
     // device copy of the nibble tables of the linear key hash
@@ -502,7 +502,7 @@ bool build_linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s, De
 struct LinearHalves {
     const int64_t *sa = nullptr, *sb = nullptr;
 };
-LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s);
+LinearHalves linear_halves(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s, bool may_build = true);
 // Everything a product of (op, sub) builds on first use, done now (outside any
 // capture): call before capturing products into a graph.
 void prepare_product(qsd_ctx ctx, qsd_op op, qsd_sub sub, cudaStream_t s);
@@ -523,9 +523,11 @@ void compute_diagonal(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d);
 void compute_diagonal_on(qsd_ctx ctx, qsd_op op, qsd_sub sub, double *d, cudaStream_t s);
 // y = H_S x on `stream`.  may_tune: a product shape seen for the first time
 // may be timed on the stream to pick the fastest path (never while the
-// stream is being captured).
+// stream is being captured).  may_allocate = false: the product allocates
+// nothing (per-pair tables not yet built are not built; the product is the
+// same, bitwise).
 void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precision, int k,
-             const void *x, void *y, cudaStream_t stream, bool may_tune = false);
+             const void *x, void *y, cudaStream_t stream, bool may_tune = false, bool may_allocate = true);
 // Path of a product shape (see apply_H); measures it once when allowed.
 // CSR form of H_S (csr.cu).  Sizing call (indptr, indices, data_re NULL):
 // returns nnz and keeps the pass-1 counts; filling call: writes the arrays.

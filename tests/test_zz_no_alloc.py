@@ -85,3 +85,38 @@ def test_noalloc_rejects_subspace_above_limit():
         rc, _ = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
         assert q.STATUS[rc] == "CAPACITY"
         assert b"at most" in q.lib().qsd_last_error(ctx.handle)
+
+
+def test_noalloc_factored_pair_builds_no_tables():
+    # a product subspace with linear ranges: the allocating products build
+    # per-pair half-sum tables on first use; the allocation-free entry point
+    # must not, even on a pair it has never seen (its kernels are loaded by a
+    # first call on another subspace of the same operator), and gives the
+    # same quotient
+    import torch
+    import paper_2603_18731_gb300 as q
+    with q.create(0) as ctx:
+        h1, eri = wl.chem_integrals(8, seed=4)
+        op = wl.molecular_qubit_operator(h1, eri)
+        h = ctx.load_operator(op)
+        assert h.info()["n_linear_ranges"] > 0
+        strings = [v for v in range(1 << 8) if bin(v).count("1") == 3]
+        warm = ctx.build_subspace(16, wl.product_subspace(strings[:30], strings[:20], 8))
+        sub = ctx.build_subspace(16, wl.product_subspace(strings, strings[:40], 8))
+        assert sub.factored()["is_product"] and ctx.product_path(h, sub) == 7
+        rng = np.random.default_rng(5)
+        with torch.cuda.stream(ctx.stream):
+            uw = torch.as_tensor(rng.normal(size=warm.dim), device=ctx.device)
+            u = torch.as_tensor(rng.normal(size=sub.dim), device=ctx.device)
+        rc, _ = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, warm, uw)
+        assert rc == 0
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        rc, got = _abi_rq(ctx, "qsd_rayleigh_quotient_noalloc", h, sub, u)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert rc == 0
+        assert free1 == free0, (free0, free1)
+        rc, ref = _abi_rq(ctx, "qsd_rayleigh_quotient", h, sub, u)  # builds the tables
+        assert rc == 0
+        assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]) and abs(got[2] - ref[2]) <= TOL * abs(ref[2])
