@@ -143,8 +143,8 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
     constexpr int NC = 32 / KB;  // candidates per gather instruction
     __shared__ uint32_t pre[8][kMaxShapes + 1];  // per warp: first candidate of each shape
     __shared__ uint32_t sa[8][kMaxShapes], sb[8][kMaxShapes], lb[8][kMaxShapes];
-    // per warp: the found candidates of the current round, compacted
-    // (the pending found candidates of earlier rounds, fewer than 32 / KB, first)
+    // per warp: the found candidates of the current pass, compacted
+    // (the pending found candidates of earlier passes, fewer than 32 / KB, first)
     __shared__ double camp[8][64];
     __shared__ uint32_t ccol[8][64];
     __shared__ uint8_t occ[8][64 * W];
@@ -325,10 +325,10 @@ __device__ __forceinline__ void fac_row(const ApplyParams &p, const ExcParams &e
             continue;
         }
         // FP64 accumulation: the found candidates appended, in candidate
-        // order, behind those pending from earlier rounds; whole groups of
+        // order, behind those pending from earlier passes; whole groups of
         // NC are gathered (KB lanes per candidate, NC candidates per load
         // instruction), so every FP64 FMA runs at full lanes, and the rest
-        // (fewer than NC) moves to the front for the next round
+        // (fewer than NC) moves to the front for the next pass
         if (nz) {
             const int slot = pend + __popc(found & ((1u << lane) - 1u));
             camp[wib][slot] = amp;
