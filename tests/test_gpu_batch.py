@@ -33,6 +33,12 @@ def pairs():
     h1, eri = wl.chem_integrals(4, seed=4)
     strings = [v for v in range(16) if bin(v).count("1") == 2]
     out.append((wl.molecular_qubit_operator(h1, eri), wl.product_subspace(strings, strings, 4)))
+    # a factored pair with two-word keys (72 qubits, split 36)
+    h1, eri = wl.chem_integrals(36, seed=5)
+    eri = np.where(np.abs(eri) >= 0.02, eri, 0.0)
+    a = wl.excitation_strings(36, 4, 30, 4, 5)
+    b = wl.excitation_strings(36, 4, 25, 4, 1005)
+    out.append((wl.molecular_qubit_operator(h1, eri), wl.product_subspace(a, b, 36)))
     return out
 
 
@@ -51,7 +57,9 @@ def test_batch_matches_single_and_oracle(ctx, k):
             xs = [torch.as_tensor(x, device=ctx.device).to(dt).contiguous() for x in xs_np]
         ys = ctx.apply_H_batch(ops, subs, xs, precision=prec)
         factored = [ctx.product_path(h, s, prec, k) == 7 for h, s in zip(ops, subs)]
-        assert any(factored)  # the fermionic pair: a product subspace
+        # the fermionic pairs (one- and two-word keys) are product subspaces
+        # (so is the one-row subspace of an indexed operator)
+        assert factored[-1] and factored[-2] and subs[-1].W == 2
         ctx.set_tuning(1, 1)
         ctx.set_tuning(2, 1)
         singles = [ctx.apply_H(h, s, x, precision=prec) for h, s, x in zip(ops, subs, xs)]
