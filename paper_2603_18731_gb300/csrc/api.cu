@@ -238,10 +238,10 @@ static bool use_factored(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
 }
 
 // The filter/verify scan applies to single-column products of operators whose
-// groups are all table groups, over subspaces with a hash order (W <= 4),
-// within its shared-memory staging limits.
+// groups are all table groups, over subspaces with a hash order and an
+// occupancy filter (W <= 4), within its shared-memory staging limits.
 static bool fv_ok(qsd_ctx ctx, qsd_op op, qsd_sub sub, int KB) {
-    return KB == 1 && op->W <= kMaxWordsStatic && sub->hperm.p != nullptr && op->G >= 1 &&
+    return KB == 1 && op->W <= kMaxWordsStatic && sub->hperm.p != nullptr && sub->occ.p != nullptr && op->G >= 1 &&
            op->n_table_groups == op->G && op->G <= kFvMaxGroups && op->n_amp <= kFvMaxAmps &&
            fv_smem_bytes(op->G, op->n_amp) <= 48 * 1024 && ctx->row_order != 1;
 }

@@ -9,17 +9,18 @@
 //   filter  the warp walks the groups together (group records and amplitude
 //           tables staged in shared memory once per block); each lane takes
 //           its row's pattern on the group's support, skips a zero element
-//           (the paper's rejection of null terms before the query), and loads
-//           the bucket of r xor F.  A bucket with no matching tag that does
-//           not overflow is a miss -- the common case -- and costs nothing
-//           more.  Otherwise (row, group, bucket, tag matches) goes to a
-//           per-warp ring of candidates in shared memory.
+//           (the paper's rejection of null terms before the query), and tests
+//           the bit of h(r xor F) in the subspace's occupancy filter (128 bits
+//           per bucket, at most 1/64 set: the paper's occupancy bit-set).  A
+//           clear bit is a miss -- the common case -- and costs nothing more.
+//           Otherwise (row, group, bucket, tag) goes to a per-warp ring of
+//           candidates in shared memory.
 //   verify  whenever 32 candidates are queued, each lane takes one: the
-//           owner's key (by shuffle) xor F, the row indices of the matching
-//           slots, the full-key check, x of the found column, and the probe's
-//           continuation into the next buckets when the bucket overflowed.
-//           The found (element, x) pairs go back to their owners in queue
-//           order by shuffles.
+//           bucket's tags, the owner's key (by shuffle) xor F, the row
+//           indices of the matching slots, the full-key check, x of the found
+//           column, and the probe's continuation into the next buckets when
+//           the bucket overflowed.  The found (element, x) pairs go back to
+//           their owners in queue order by shuffles.
 // Candidates enter the ring in group order and leave it in that order, so
 // each row accumulates its elements in group order with the same operations
 // as the one-pass scan: the result is bitwise that of QSD_PATH_SCAN_HASH.
@@ -45,9 +46,9 @@ __host__ __device__ inline int64_t fv_padded_groups(int64_t G) { return (G + kFv
 // byte of h(F), nonzero-pattern mask, first amplitude} and its 8-byte support
 // (qubits, 12 bits each); the amplitudes (8 bytes each: FP64, or the FP32
 // (hi, lo) pair of DOT2); then per warp a ring of kFvRing candidates as three
-// uint32 arrays: bucket; meta = owner lane (bits 0-4), bucket overflowed (bit
-// 5), tag matches (bits 6-13), group (bits 14-31); amplitude index (bits
-// 0-23) and tag (bits 24-31).  Padding groups have an empty mask.
+// uint32 arrays: bucket; meta = owner lane (bits 0-4), group (bits 14-31);
+// amplitude index (bits 0-23) and tag (bits 24-31).  Padding groups have an
+// empty mask.
 inline size_t fv_smem_bytes(int64_t G, int64_t n_amp) {
     return (size_t)fv_padded_groups(G) * 24 + (size_t)n_amp * 8 + (size_t)kFvWarps * kFvRing * 12;
 }
@@ -69,6 +70,8 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
     const uint32_t b = mine ? q.b[slot] : 0u;
     const uint32_t at = mine ? q.a[slot] : 0u;
     const int o = (int)(meta & 31u);
+    // the bucket's tags (the filter read only its occupancy bit)
+    const uint2 tb = mine ? __ldg(reinterpret_cast<const uint2 *>(p.hv.tags) + b) : make_uint2(0u, 0u);
     uint64_t c[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = __shfl_sync(0xffffffffu, key[w], o);
@@ -80,8 +83,8 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
         const int64_t g = (int64_t)(meta >> 14);
 #pragma unroll
         for (int w = 0; w < W; ++w) c[w] ^= __ldg(p.gF + (size_t)w * p.G + g);
-        int64_t idx = verify_matches_x<W, TIO>(p.hv, b, (meta >> 6) & 0xffu, c, x + p.col0, p.ld, xv);
-        if (idx < 0 && (meta & 32u)) {
+        int64_t idx = verify_matches_x<W, TIO>(p.hv, b, tag_match(tb, at >> 24), c, x + p.col0, p.ld, xv);
+        if (idx < 0 && bucket_full(tb)) {
             idx = probe_from<W>(p.hv, b, at >> 24, c, p.err);
             if (idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
         }
@@ -171,7 +174,8 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
     __syncthreads();
 
     const TIO *__restrict__ x = static_cast<const TIO *>(p.x);
-    const uint2 *__restrict__ tags = reinterpret_cast<const uint2 *>(p.hv.tags);
+    const uint32_t *__restrict__ occ = p.hv.occ;
+    const uint32_t oshift = (uint32_t)p.hv.occ_shift;
     const uint32_t bshift = (uint32_t)p.hv.shift - 32u;
     const uint32_t lt = (1u << lane) - 1u;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -191,11 +195,10 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         uint32_t head = 0, tail = 0;  // warp-uniform ring positions
 
         for (int g0 = 0; g0 < Gp; g0 += kFvU) {
-            // phase 1: every group's bucket load in flight (tags and tag
-            // bytes kept; bucket, pattern and amplitude index are recomputed
-            // for the rare candidates)
-            uint2 tb[kFvU];
-            uint32_t tg[kFvU];
+            // phase 1: every group's filter word in flight (the word and the
+            // bit position kept; bucket, tag, pattern and amplitude index are
+            // recomputed for the rare candidates)
+            uint32_t wd[kFvU], bit[kFvU];
             uint32_t needm = 0;
 #pragma unroll
             for (int u = 0; u < kFvU; ++u) {
@@ -204,15 +207,15 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
                 if (NB == 2) l = fv_pattern2<W>(R.y, key);
                 else if (NB < 0) l = fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
                 const uint32_t need = ((R.z & live) >> l) & 1u;
-                const uint32_t t = (hr_lo ^ R.y) & 0xffu;
-                tg[u] = t ? t : 1u;
-                if (need) tb[u] = __ldg(tags + ((hr_hi ^ R.x) >> bshift));
+                const uint32_t bi = (hr_hi ^ R.x) >> oshift;
+                bit[u] = bi & 31u;
+                wd[u] = need ? __ldg(occ + (bi >> 5)) : 0u;
                 needm |= need << u;
             }
             // phase 2: misses end here; candidates enter the ring in group order
 #pragma unroll
             for (int u = 0; u < kFvU; ++u) {
-                const bool cand = ((needm >> u) & 1u) && (bucket_full(tb[u]) || tag_any(tb[u], tg[u]));
+                const bool cand = ((needm >> u) & (wd[u] >> bit[u])) & 1u;
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 if (bal == 0u) continue;  // warp-uniform: every lookup of the group missed
                 if (cand) {
@@ -220,12 +223,11 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
                     const uint32_t l = NB == 0 ? 0u
                                        : NB == 2 ? fv_pattern2<W>(R.y, key)
                                                  : fv_pattern<W>(recB[g0 + u], (R.y >> 8) & 7u, key);
-                    const uint32_t full = bucket_full(tb[u]) ? 1u : 0u;
-                    const uint32_t match = tag_match(tb[u], tg[u]);
+                    const uint32_t t = (hr_lo ^ R.y) & 0xffu;
                     const uint32_t slot = (tail + (uint32_t)__popc(bal & lt)) & (kFvRing - 1);
                     q.b[slot] = (hr_hi ^ R.x) >> bshift;
-                    q.m[slot] = (uint32_t)lane | (full << 5) | (match << 6) | ((uint32_t)(g0 + u) << 14);
-                    q.a[slot] = (R.w + l) | (tg[u] << 24);
+                    q.m[slot] = (uint32_t)lane | ((uint32_t)(g0 + u) << 14);
+                    q.a[slot] = (R.w + l) | ((t ? t : 1u) << 24);
                 }
                 tail += (uint32_t)__popc(bal);
                 __syncwarp();

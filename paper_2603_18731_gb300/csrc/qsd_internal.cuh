@@ -164,6 +164,8 @@ struct qsd_sub_s {
     qsd::DevBuf keys;   // uint64 [W][D]
     qsd::DevBuf tags;   // uint8 [8 * n_buckets], 0 = empty
     qsd::DevBuf sidx;   // uint32 [8 * n_buckets]
+    qsd::DevBuf occ;    // uint32 occupancy filter (HashView::occ), W <= 4 and n_buckets <= 2^25
+    int occ_shift = 0;
     // hash order (W <= 4): the rows in bucket order and their keys
     qsd::DevBuf rhash;  // uint64 [D] hash h of each row (W <= 4)
     qsd::DevBuf hperm;  // uint32 [D] row at each position
@@ -362,7 +364,17 @@ struct HashView {
     int64_t D;
     uint64_t bmask;
     int shift;
+    // occupancy filter (nullptr: none): bit (hi32(h) >> occ_shift) is set for
+    // the hash h of every key -- the top log2(n_buckets) + 7 bits of h, 128
+    // bits per bucket, so at load <= 1/4 at most 1/64 of the bits are set;
+    // a clear bit proves the key absent
+    const uint32_t *occ;
+    int occ_shift;
 };
+
+// Occupancy filter bits per bucket (log2) and the largest bucket count it covers.
+constexpr int kOccBitsPerBucketLog2 = 7;
+constexpr int kOccMaxBucketsLog2 = 32 - kOccBitsPerBucketLog2;
 
 // Index of the verified key among the matching slots of bucket b, or -1.
 template <int W>
@@ -476,12 +488,15 @@ void subspace_index(qsd_ctx ctx, qsd_sub sub, int64_t n, const uint64_t *q, int6
 void subspace_keys_aos(qsd_ctx ctx, qsd_sub sub, uint64_t *out_dev);
 struct HashTable {
     DevBuf tags, sidx;
+    DevBuf occ;  // uint32 occupancy filter words (with_filter), else empty
     int64_t n_buckets = 0;
     int shift = 63;
+    int occ_shift = 0;
 };
 // Hash table over n keys given as SoA words keys[w*n + i] (table layout of
 // the subspace index); hash_out (optional, [n], W <= 4): each key's hash h.
-HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n, uint64_t *hash_out = nullptr);
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t n, uint64_t *hash_out = nullptr,
+                     bool with_filter = false);
 // The subspace's rows in bucket order (hperm, hkeys; W <= 4).
 void build_hash_order(qsd_ctx ctx, qsd_sub sub);
 void build_excitation_index(qsd_ctx ctx, qsd_op op);
@@ -512,7 +527,7 @@ void drop_linear_halves(const void *handle);
 double excitation_candidates(qsd_op op, qsd_sub sub);
 inline HashView hash_view(qsd_sub sub) {
     return HashView{sub->tags.as<uint8_t>(), sub->sidx.as<uint32_t>(), sub->keys.as<uint64_t>(), sub->D,
-                    (uint64_t)sub->n_buckets - 1, sub->bucket_shift};
+                    (uint64_t)sub->n_buckets - 1, sub->bucket_shift, sub->occ.as<uint32_t>(), sub->occ_shift};
 }
 void load_operator(qsd_ctx ctx, qsd_op op, int64_t n_terms, const int64_t *term_ptr,
                    const int32_t *op_qubit, const uint8_t *op_code, const double *coef_re,

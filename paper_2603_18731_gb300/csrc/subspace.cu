@@ -63,7 +63,7 @@ __device__ __forceinline__ bool claim_slot(uint8_t *tags, uint32_t *sidx, uint64
 template <int W>
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, const uint64_t *__restrict__ nib,
                               uint8_t *tags, uint32_t *sidx, uint64_t bucket_mask, int shift, uint64_t *hash_out,
-                              uint32_t *err) {
+                              uint32_t *occ, int occ_shift, uint32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     uint64_t x[W];
@@ -72,6 +72,10 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, int64_t D, cons
     uint32_t tag;
     const uint64_t h = key_hash<W>(x, nib);
     if (hash_out) hash_out[i] = h;
+    if (occ) {
+        const uint32_t bi = (uint32_t)(h >> 32) >> occ_shift;
+        atomicOr(occ + (bi >> 5), 1u << (bi & 31u));
+    }
     uint64_t b = hash_bucket(h, shift, tag);
     for (uint64_t step = 0; step <= bucket_mask; ++step) {
         if (claim_slot(tags, sidx, b, tag, (uint32_t)i)) return;
@@ -186,11 +190,13 @@ void build_subspace(qsd_ctx ctx, qsd_sub sub, const uint64_t *words, int64_t n_i
     if (D > 0) unique_sorted(ctx, soa.as<uint64_t>(), W, n_in, sub->keys.as<uint64_t>(), D);
     soa.release();
     if (W <= kMaxWordsStatic) sub->rhash.alloc((size_t)std::max<int64_t>(D, 1) * 8);
-    HashTable t = build_hash(ctx, sub->keys.as<uint64_t>(), W, D, sub->rhash.as<uint64_t>());
+    HashTable t = build_hash(ctx, sub->keys.as<uint64_t>(), W, D, sub->rhash.as<uint64_t>(), true);
     sub->n_buckets = t.n_buckets;
     sub->bucket_shift = t.shift;
     sub->tags = std::move(t.tags);
     sub->sidx = std::move(t.sidx);
+    sub->occ = std::move(t.occ);
+    sub->occ_shift = t.occ_shift;
     if (D > 0 && W <= kMaxWordsStatic) build_hash_order(ctx, sub);
     build_factored(ctx, sub);
     sub->key0.assign(W, 0);
@@ -232,7 +238,7 @@ void build_hash_order(qsd_ctx ctx, qsd_sub sub) {
     QSD_CUDA(cudaStreamSynchronize(s));  // start is freed on return
 }
 
-HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D, uint64_t *hash_out) {
+HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D, uint64_t *hash_out, bool with_filter) {
     cudaStream_t s = ctx->stream;
     HashTable t;
     // load factor <= 1/4 over buckets of 8 slots: a bucket overflows into the
@@ -246,6 +252,14 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D, uint64
     t.tags.alloc(cap);
     t.sidx.alloc(cap * 4);
     QSD_CUDA(cudaMemsetAsync(t.tags.p, 0, cap, s));
+    uint32_t *occ = nullptr;
+    if (with_filter && W <= kMaxWordsStatic && lg <= kOccMaxBucketsLog2) {
+        const size_t words = std::max<size_t>(1, ((size_t)t.n_buckets << kOccBitsPerBucketLog2) / 32);
+        t.occ.alloc(words * 4);
+        QSD_CUDA(cudaMemsetAsync(t.occ.p, 0, words * 4, s));
+        t.occ_shift = 32 - (lg + kOccBitsPerBucketLog2);
+        occ = t.occ.as<uint32_t>();
+    }
     if (D > 0) {
         QSD_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s));
         const uint64_t mask = (uint64_t)t.n_buckets - 1;
@@ -255,10 +269,18 @@ HashTable build_hash(qsd_ctx ctx, const uint64_t *keys, int W, int64_t D, uint64
         const int nb = blocks_for(D, 256);
         const int shift = t.shift;
         switch (W) {
-        case 1: k_hash_insert<1><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
-        case 2: k_hash_insert<2><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
-        case 3: k_hash_insert<3><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
-        case 4: k_hash_insert<4><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, ctx->d_err); break;
+        case 1:
+            k_hash_insert<1><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, occ, t.occ_shift, ctx->d_err);
+            break;
+        case 2:
+            k_hash_insert<2><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, occ, t.occ_shift, ctx->d_err);
+            break;
+        case 3:
+            k_hash_insert<3><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, occ, t.occ_shift, ctx->d_err);
+            break;
+        case 4:
+            k_hash_insert<4><<<nb, 256, 0, s>>>(keys, D, nib, tg, si, mask, shift, hash_out, occ, t.occ_shift, ctx->d_err);
+            break;
         default: k_hash_insert_dyn<<<nb, 256, 0, s>>>(keys, W, D, nib, tg, si, mask, shift, ctx->d_err);
         }
         QSD_LAUNCH_CHECK();
