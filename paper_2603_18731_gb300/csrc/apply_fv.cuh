@@ -47,19 +47,28 @@ __host__ __device__ inline int64_t fv_padded_groups(int64_t G) { return (G + kFv
 // (qubits, 12 bits each); the amplitudes (8 bytes each: FP64, or the FP32
 // (hi, lo) pair of DOT2); then per warp a ring of kFvRing candidates as three
 // uint32 arrays: bucket; meta = owner lane (bits 0-4), group (bits 14-31);
-// amplitude index (bits 0-23) and tag (bits 24-31).  Padding groups have an
-// empty mask.
+// amplitude index (bits 0-23) and tag (bits 24-31); and per warp the
+// delivery area of a verify batch: the found elements and x values by queue
+// slot (8 bytes each) and each owner lane's mask of its found slots.  Padding
+// groups have an empty mask.
+constexpr int kFvDeliverBytes = 32 * 8 * 2 + 32 * 4;
 inline size_t fv_smem_bytes(int64_t G, int64_t n_amp) {
-    return (size_t)fv_padded_groups(G) * 24 + (size_t)n_amp * 8 + (size_t)kFvWarps * kFvRing * 12;
+    return (size_t)fv_padded_groups(G) * 24 + (size_t)n_amp * 8 + (size_t)kFvWarps * (kFvRing * 12 + kFvDeliverBytes);
 }
 
 struct FvRing {
     uint32_t *b, *m, *a;
+    uint64_t *va, *vx;  // [32]: element (FP64, or the DOT2 (hi, lo) pair) and x of each found slot
+    uint32_t *own;      // [32]: per owner lane, the mask of its found slots
 };
 
 // Verify the n (1..32) oldest queued candidates of the warp (one per lane)
 // and deliver the found (element, x) pairs to their owner lanes in queue
-// order; the same operations as the one-pass scan's accumulation.
+// order; the same operations as the one-pass scan's accumulation.  Delivery:
+// the verifier lanes of each owner (one __match_any_sync) post their mask to
+// the owner, and every owner walks its own found slots in order, so the
+// accumulation takes as many rounds as the busiest owner has candidates
+// (one or two), not one round per candidate.
 template <int W, int PREC, typename TIO>
 __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q, uint32_t head, int n, int lane,
                                           const uint64_t (&key)[W], const double *amp, const float2 *ampf,
@@ -98,20 +107,38 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
             a = amp[ai];
         }
     }
-    const uint32_t tagged = (uint32_t)o | (found ? 32u : 0u);
-    const uint32_t me = (uint32_t)lane | 32u;
-    for (int t = 0; t < n; ++t) {
-        const uint32_t ot = __shfl_sync(0xffffffffu, tagged, t);
-        const TIO xt = __shfl_sync(0xffffffffu, xv, t);
+    // post: each owner's found slots (the lowest verifier lane of each owner
+    // writes the owner's mask), the elements and x values by slot
+    q.own[lane] = 0u;
+    __syncwarp();
+    const uint32_t grp = __match_any_sync(0xffffffffu, found ? (uint32_t)o : 32u + (uint32_t)lane);
+    if (found) {
+        if ((grp & ((1u << lane) - 1u)) == 0u) q.own[o] = grp;
         if (PREC == QSD_FP32_DOT2) {
-            const float aht = __shfl_sync(0xffffffffu, ah, t);
-            const float alt = __shfl_sync(0xffffffffu, al, t);
-            if (ot == me) dot2_add(as, ae, aht, alt, (float)xt);
+            q.va[lane] = ((uint64_t)__float_as_uint(al) << 32) | __float_as_uint(ah);
         } else {
-            const double at_ = __shfl_sync(0xffffffffu, a, t);
-            if (ot == me) acc = fma(at_, (double)xt, acc);
+            q.va[lane] = (uint64_t)__double_as_longlong(a);
+        }
+        if (sizeof(TIO) == 8) q.vx[lane] = (uint64_t)__double_as_longlong((double)xv);
+        else q.vx[lane] = (uint64_t)__float_as_uint((float)xv);
+    }
+    __syncwarp();
+    // walk: every owner its own found slots, in queue order
+    uint32_t mine_m = q.own[lane];
+    while (__any_sync(0xffffffffu, mine_m != 0u)) {
+        if (mine_m) {
+            const int t = __ffs(mine_m) - 1;
+            mine_m &= mine_m - 1u;
+            const uint64_t ev = q.va[t], xb = q.vx[t];
+            const TIO xt = sizeof(TIO) == 8 ? (TIO)__longlong_as_double((long long)xb) : (TIO)__uint_as_float((uint32_t)xb);
+            if (PREC == QSD_FP32_DOT2) {
+                dot2_add(as, ae, __uint_as_float((uint32_t)ev), __uint_as_float((uint32_t)(ev >> 32)), (float)xt);
+            } else {
+                acc = fma(__longlong_as_double((long long)ev), (double)xt, acc);
+            }
         }
     }
+    __syncwarp();
 }
 
 // The row's bits on a group's support (nb <= 5 qubits, 12 bits each in pos).
@@ -148,6 +175,11 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
     q.b = ring + (size_t)wib * kFvRing * 3;
     q.m = q.b + kFvRing;
     q.a = q.m + kFvRing;
+    unsigned char *dl = reinterpret_cast<unsigned char *>(ring + (size_t)kFvWarps * kFvRing * 3) +
+                        (size_t)wib * kFvDeliverBytes;
+    q.va = reinterpret_cast<uint64_t *>(dl);
+    q.vx = q.va + 32;
+    q.own = reinterpret_cast<uint32_t *>(q.vx + 32);
 
     for (int g = threadIdx.x; g < Gp; g += blockDim.x) {
         uint4 A = make_uint4(0u, 0u, 0u, 0u);
