@@ -237,11 +237,13 @@ static bool use_factored(qsd_ctx ctx, qsd_op op, qsd_sub sub) {
            op->trec.p != nullptr && op->lin_base.p != nullptr;
 }
 
-// The filter/verify scan applies to single-column products of operators whose
-// groups are all table groups, over subspaces with a hash order and an
-// occupancy filter (W <= 4), within its shared-memory staging limits.
+// The filter/verify scan applies to single-column and 16-column products of
+// operators whose groups are all table groups, over subspaces with a hash
+// order and an occupancy filter (W <= 4), within its shared-memory staging
+// limits.
 static bool fv_ok(qsd_ctx ctx, qsd_op op, qsd_sub sub, int KB) {
-    return KB == 1 && op->W <= kMaxWordsStatic && sub->hperm.p != nullptr && sub->occ.p != nullptr && op->G >= 1 &&
+    return (KB == 1 || KB == 16) && op->W <= kMaxWordsStatic && sub->hperm.p != nullptr && sub->occ.p != nullptr &&
+           op->G >= 1 &&
            op->n_table_groups == op->G && op->G <= kFvMaxGroups && op->n_amp <= kFvMaxAmps &&
            fv_smem_bytes(op->G, op->n_amp) <= 48 * 1024 && ctx->row_order != 1;
 }
@@ -344,9 +346,9 @@ void launch_path(int path, const ApplyParams &p, const ExcParams &e, const FacPa
     if (path == 8) {
         const int na = (int)p.n_amp;
         const int nb = p.table_nb;
-        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, na, W, nb, p.num_sms, stream);
-        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, na, W, nb, p.num_sms, stream);
-        else launch_apply_fv<QSD_FP32_DOT2>(p, na, W, nb, p.num_sms, stream);
+        if (precision == QSD_FP64) launch_apply_fv<QSD_FP64>(p, na, W, nb, KB, p.num_sms, stream);
+        else if (precision == QSD_FP32_MIXED) launch_apply_fv<QSD_FP32_MIXED>(p, na, W, nb, KB, p.num_sms, stream);
+        else launch_apply_fv<QSD_FP32_DOT2>(p, na, W, nb, KB, p.num_sms, stream);
         return;
     }
     if (path == 7) {

@@ -69,10 +69,13 @@ struct FvRing {
 // the owner, and every owner walks its own found slots in order, so the
 // accumulation takes as many rounds as the busiest owner has candidates
 // (one or two), not one round per candidate.
-template <int W, int PREC, typename TIO>
+// KB > 1 (a block of columns): the verifier posts the found column's index
+// and the owner gathers its KB values of x itself.
+template <int W, int PREC, typename TIO, int KB>
 __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q, uint32_t head, int n, int lane,
                                           const uint64_t (&key)[W], const double *amp, const float2 *ampf,
-                                          const TIO *__restrict__ x, double &acc, float &as, float &ae) {
+                                          const TIO *__restrict__ x, double (&acc)[KB], float (&as)[KB],
+                                          float (&ae)[KB]) {
     const uint32_t slot = (head + (uint32_t)lane) & (kFvRing - 1);
     const bool mine = lane < n;
     const uint32_t meta = mine ? q.m[slot] : 0u;
@@ -85,6 +88,7 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
 #pragma unroll
     for (int w = 0; w < W; ++w) c[w] = __shfl_sync(0xffffffffu, key[w], o);
     bool found = false;
+    int64_t fidx = -1;  // KB > 1: the found column
     TIO xv = TIO(0);
     double a = 0.0;
     float ah = 0.f, al = 0.f;
@@ -92,12 +96,14 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
         const int64_t g = (int64_t)(meta >> 14);
 #pragma unroll
         for (int w = 0; w < W; ++w) c[w] ^= __ldg(p.gF + (size_t)w * p.G + g);
-        int64_t idx = verify_matches_x<W, TIO>(p.hv, b, tag_match(tb, at >> 24), c, x + p.col0, p.ld, xv);
+        int64_t idx = KB == 1 ? verify_matches_x<W, TIO>(p.hv, b, tag_match(tb, at >> 24), c, x + p.col0, p.ld, xv)
+                              : verify_matches<W>(p.hv, b, tag_match(tb, at >> 24), c);
         if (idx < 0 && bucket_full(tb)) {
             idx = probe_from<W>(p.hv, b, at >> 24, c, p.err);
-            if (idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
+            if (KB == 1 && idx >= 0) xv = __ldg(x + idx * p.ld + p.col0);
         }
         found = idx >= 0;
+        fidx = idx;
         const uint32_t ai = at & 0xffffffu;
         if (PREC == QSD_FP32_DOT2) {
             const float2 f = ampf[ai];
@@ -119,7 +125,8 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
         } else {
             q.va[lane] = (uint64_t)__double_as_longlong(a);
         }
-        if (sizeof(TIO) == 8) q.vx[lane] = (uint64_t)__double_as_longlong((double)xv);
+        if (KB > 1) q.vx[lane] = (uint64_t)fidx;  // the owner gathers the block's columns
+        else if (sizeof(TIO) == 8) q.vx[lane] = (uint64_t)__double_as_longlong((double)xv);
         else q.vx[lane] = (uint64_t)__float_as_uint((float)xv);
     }
     __syncwarp();
@@ -130,11 +137,26 @@ __device__ __forceinline__ void fv_verify(const ApplyParams &p, const FvRing &q,
             const int t = __ffs(mine_m) - 1;
             mine_m &= mine_m - 1u;
             const uint64_t ev = q.va[t], xb = q.vx[t];
-            const TIO xt = sizeof(TIO) == 8 ? (TIO)__longlong_as_double((long long)xb) : (TIO)__uint_as_float((uint32_t)xb);
-            if (PREC == QSD_FP32_DOT2) {
-                dot2_add(as, ae, __uint_as_float((uint32_t)ev), __uint_as_float((uint32_t)(ev >> 32)), (float)xt);
+            if (KB > 1) {
+                const TIO *xc = x + (int64_t)xb * p.ld + p.col0;
+                if (PREC == QSD_FP32_DOT2) {
+                    const float h = __uint_as_float((uint32_t)ev), l = __uint_as_float((uint32_t)(ev >> 32));
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) dot2_add(as[j], ae[j], h, l, (float)__ldg(xc + j));
+                } else {
+                    const double av = __longlong_as_double((long long)ev);
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) acc[j] = fma(av, (double)__ldg(xc + j), acc[j]);
+                }
             } else {
-                acc = fma(__longlong_as_double((long long)ev), (double)xt, acc);
+                const TIO xt = sizeof(TIO) == 8 ? (TIO)__longlong_as_double((long long)xb)
+                                                : (TIO)__uint_as_float((uint32_t)xb);
+                if (PREC == QSD_FP32_DOT2) {
+                    dot2_add(as[0], ae[0], __uint_as_float((uint32_t)ev), __uint_as_float((uint32_t)(ev >> 32)),
+                             (float)xt);
+                } else {
+                    acc[0] = fma(__longlong_as_double((long long)ev), (double)xt, acc[0]);
+                }
             }
         }
     }
@@ -158,8 +180,10 @@ __device__ __forceinline__ uint32_t fv_pattern2(uint32_t y, const uint64_t (&key
 
 // NB: the support size of every group when fixed (0: one constant element,
 // e.g. X flips, so the filter reads no row bits; 2: e.g. flip-flop bonds),
-// or -1 (read per group).
-template <int W, int PREC, int NB>
+// or -1 (read per group).  KB: columns of the block (1 or 16); the filter and
+// verify passes are shared by the block's columns, every found column
+// gathers KB values of x.
+template <int W, int PREC, int NB, int KB = 1>
 __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, int n_amp, int64_t tiles) {
     using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
@@ -222,8 +246,13 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         // an inactive lane (past the last row) needs no group: its mask bit
         // is taken from an empty pattern range
         const uint32_t live = active ? 0xffffffffu : 0u;
-        double acc = 0.0;
-        float as = 0.f, ae = 0.f;
+        double acc[KB];
+        float as[KB], ae[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            acc[j] = 0.0;
+            as[j] = ae[j] = 0.f;
+        }
         uint32_t head = 0, tail = 0;  // warp-uniform ring positions
 
         for (int g0 = 0; g0 < Gp; g0 += kFvU) {
@@ -264,36 +293,41 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
                 tail += (uint32_t)__popc(bal);
                 __syncwarp();
                 if (tail - head >= 32u) {
-                    fv_verify<W, PREC, TIO>(p, q, head, 32, lane, key, amp, ampf, x, acc, as, ae);
+                    fv_verify<W, PREC, TIO, KB>(p, q, head, 32, lane, key, amp, ampf, x, acc, as, ae);
                     head += 32u;
                     __syncwarp();
                 }
             }
         }
         __syncwarp();
-        if (tail != head) fv_verify<W, PREC, TIO>(p, q, head, (int)(tail - head), lane, key, amp, ampf, x, acc, as, ae);
+        if (tail != head)
+            fv_verify<W, PREC, TIO, KB>(p, q, head, (int)(tail - head), lane, key, amp, ampf, x, acc, as, ae);
         __syncwarp();
         if (active) {
             const int64_t r = (int64_t)__ldg(p.hperm + pc);
             const double d = __ldg(p.diag + r);
-            const TIO xr = __ldg(x + r * p.ld + p.col0);
+            const TIO *xr = x + r * p.ld + p.col0;
             TIO *yr = static_cast<TIO *>(p.y) + r * p.ld + p.col0;
             if (PREC == QSD_FP32_DOT2) {
                 const float dh = (float)d, dl = (float)(d - (double)dh);
-                dot2_add(as, ae, dh, dl, (float)xr);
-                *yr = (TIO)(as + ae);
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
+                    yr[j] = (TIO)(as[j] + ae[j]);
+                }
             } else {
-                *yr = (TIO)fma(d, (double)xr, acc);
+#pragma unroll
+                for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
             }
         }
     }
 }
 
-// Launch the filter/verify product for precision mode PREC (W <= 4, k = 1,
-// hash order, every group a table group, G <= kFvMaxGroups, n_amp <=
-// kFvMaxAmps); nb: the support size of every group when fixed (0 or 2), else
-// -1.
+// Launch the filter/verify product for precision mode PREC (W <= 4, KB = 1
+// or 16 columns, hash order, every group a table group, G <= kFvMaxGroups,
+// n_amp <= kFvMaxAmps); nb: the support size of every group when fixed (0 or
+// 2), else -1.
 template <int PREC>
-void launch_apply_fv(const ApplyParams &p, int n_amp, int W, int nb, int num_sms, cudaStream_t s);
+void launch_apply_fv(const ApplyParams &p, int n_amp, int W, int nb, int KB, int num_sms, cudaStream_t s);
 
 }  // namespace qsd

@@ -3,7 +3,8 @@
 Its rows accumulate the same elements in the same group order with the same
 operations as the one-pass scan in hash order, so the two must agree bit for
 bit, in every precision mode; both must match the oracle (1e-12 FP64, 2^-22
-FP32 storage).  Cases: one- and four-word keys, spin models with constant
+FP32 storage), for single columns and blocks of 16.  Cases: one- and
+four-word keys, spin models with constant
 elements (Ising: X groups) and with support patterns (XXZ: flip-flop groups
 that vanish on aligned pairs), dimensions that leave a ragged last tile, a
 subspace smaller than one warp, and more tiles than the persistent grid.
@@ -58,7 +59,7 @@ def case(kind):
     raise ValueError(kind)
 
 
-def forced(ctx, h, sub, x, prec, path):
+def forced(ctx, h, sub, x, prec, path, k=1):
     if path == PATH_FILTER_VERIFY:
         ctx.set_tuning(1, 5)
     else:
@@ -66,7 +67,7 @@ def forced(ctx, h, sub, x, prec, path):
         ctx.set_tuning(2, 1)
         ctx.set_tuning(5, 2)
     try:
-        assert ctx.product_path(h, sub, prec, 1) == path
+        assert ctx.product_path(h, sub, prec, k) == path
         y = ctx.apply_H(h, sub, x, precision=prec)
         ctx.synchronize()
         return y.cpu().double().numpy()
@@ -78,26 +79,28 @@ def forced(ctx, h, sub, x, prec, path):
 
 @pytest.mark.parametrize("kind", ["ising60", "ising200", "xxz", "mixed", "tiny"])
 @pytest.mark.parametrize("prec", [0, 1, 2])
-def test_filter_verify_equals_scan_and_oracle(ctx, kind, prec):
+@pytest.mark.parametrize("k", [1, 16])
+def test_filter_verify_equals_scan_and_oracle(ctx, kind, prec, k):
     import torch
     op, words = case(kind)
     keys = oracle.sort_unique(words)
     h = ctx.load_operator(op)
     sub = ctx.build_subspace(op.n_qubits, words)
-    x = np.random.default_rng(prec + 7).normal(size=sub.dim)
+    rng = np.random.default_rng(prec + 7 + k)
+    x = rng.normal(size=(sub.dim, k)) if k > 1 else rng.normal(size=sub.dim)
     if prec == 0:
         xt, tol = to_cuda(ctx, x, torch.float64), FP64_TOL
     else:
         x = x.astype(np.float32).astype(np.float64)
         xt, tol = to_cuda(ctx, x, torch.float32), FP32_TOL
-    y8 = forced(ctx, h, sub, xt, prec, PATH_FILTER_VERIFY)
-    y5 = forced(ctx, h, sub, xt, prec, PATH_SCAN_HASH)
+    y8 = forced(ctx, h, sub, xt, prec, PATH_FILTER_VERIFY, k)
+    y5 = forced(ctx, h, sub, xt, prec, PATH_SCAN_HASH, k)
     assert np.array_equal(y8, y5)
     assert rel_err(y8, oracle.apply(op, keys, x).real) <= tol
 
 
 def test_filter_verify_not_offered_outside_its_limits(ctx):
-    # scan groups (fermionic ladder terms) and block products keep other paths
+    # scan groups (fermionic ladder terms) and blocks of 4 keep other paths
     h1, eri = wl.chem_integrals(6, seed=1)
     op = wl.molecular_qubit_operator(h1, eri)
     strings = [v for v in range(1 << 6) if bin(v).count("1") == 3]
@@ -111,6 +114,7 @@ def test_filter_verify_not_offered_outside_its_limits(ctx):
         h2 = ctx.load_operator(op2)
         sub2 = ctx.build_subspace(60, words2)
         assert ctx.product_path(h2, sub2, 0, 1) == PATH_FILTER_VERIFY
-        assert ctx.product_path(h2, sub2, 0, 16) != PATH_FILTER_VERIFY
+        assert ctx.product_path(h2, sub2, 0, 16) == PATH_FILTER_VERIFY
+        assert ctx.product_path(h2, sub2, 0, 4) != PATH_FILTER_VERIFY
     finally:
         ctx.set_tuning(1, 0)
