@@ -22,8 +22,9 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqsd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # source file -> (macro, values): one object per value
-VARIANTS = {name: ("QSD_PREC", (0, 1, 2)) for name in ("apply_inst.cu", "apply_exc_inst.cu", "apply_fv_inst.cu")}
-VARIANTS["apply_fac_inst.cu"] = ("QSD_PREC", (0, 1, 2, 3))  # 3: FP32-mixed blocks on widened x
+VARIANTS = {name: ("QSD_PREC", (0, 1, 2)) for name in ("apply_inst.cu", "apply_exc_inst.cu")}
+for name in ("apply_fac_inst.cu", "apply_fv_inst.cu"):
+    VARIANTS[name] = ("QSD_PREC", (0, 1, 2, 3))  # 3: FP32-mixed blocks on widened x
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xcudafe", "--diag_suppress=177"]
 

@@ -519,21 +519,14 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
     ExcParams e{};
     FacParams f{};
     bool have_e = false;
-    // FP32-mixed block products on the factored path: x widened exactly to
-    // FP64 once (context scratch), then the FP64 block kernel with FP32 y --
-    // bitwise the same product, without a conversion per gathered value
-    // (which cost the gather loop 15 % more instructions and a block of
-    // residency per SM)
+    // FP32-mixed block products on the factored and filter/verify paths: x
+    // widened exactly to FP64 once (context scratch), then the FP64 block
+    // kernel with FP32 y -- bitwise the same product, without a conversion
+    // per gathered value (which cost the factored gather loop 15 % more
+    // instructions and a block of residency per SM)
     const double *xw = nullptr;
-    if (precision == QSD_FP32_MIXED && k >= 4 && may_allocate && stream == ctx->stream && sub->D > 0 &&
-        use_factored(ctx, op, sub) && !capturing(stream)) {
-        const int64_t n = sub->D * (int64_t)k;
-        double *buf = static_cast<double *>(ctx->scratch[4].get((size_t)n * 8));
-        k_widen<<<(unsigned)std::min<int64_t>(blocks_for(n, 256), 8 * (int64_t)ctx->num_sms), 256, 0, stream>>>(
-            static_cast<const float *>(x), n, buf);
-        QSD_LAUNCH_CHECK();
-        xw = buf;
-    }
+    const bool may_widen = precision == QSD_FP32_MIXED && k >= 4 && may_allocate && stream == ctx->stream &&
+                           sub->D > 0 && !capturing(stream);
     int64_t c = 0;
     while (c < k) {
         const int KB = (k - c >= 16) ? 16 : (k - c >= 4 ? 4 : 1);
@@ -544,10 +537,20 @@ void apply_H(qsd_ctx ctx, qsd_op op, qsd_sub sub, const double *diag, int precis
             f = make_fac(ctx, op, sub, stream, may_allocate);
             have_e = true;
         }
-        if (path == 7 && xw && KB > 1) {
+        const bool wide = may_widen && ((path == 7 && KB > 1) || (path == 8 && KB == 16));
+        if (wide && !xw) {
+            const int64_t n = sub->D * (int64_t)k;
+            double *buf = static_cast<double *>(ctx->scratch[4].get((size_t)n * 8));
+            k_widen<<<(unsigned)std::min<int64_t>(blocks_for(n, 256), 8 * (int64_t)ctx->num_sms), 256, 0, stream>>>(
+                static_cast<const float *>(x), n, buf);
+            QSD_LAUNCH_CHECK();
+            xw = buf;
+        }
+        if (wide) {
             ApplyParams pw = p;
             pw.x = xw;
-            launch_apply_fac<kPrecWideX>(pw, e, f, op->W, KB, stream);
+            if (path == 7) launch_apply_fac<kPrecWideX>(pw, e, f, op->W, KB, stream);
+            else launch_apply_fv<kFvWideX>(pw, (int)pw.n_amp, op->W, pw.table_nb, KB, pw.num_sms, stream);
         } else {
             launch_path(path, p, e, f, op->W, precision, KB, stream);
         }

@@ -39,6 +39,7 @@ constexpr int kFvRing = 64;         // candidates per warp (at most 31 + 32 queu
 constexpr int kFvThreads = 256;
 constexpr int kFvWarps = kFvThreads / 32;
 constexpr int kFvU = 4;             // groups per filter batch (bucket loads in flight per lane)
+constexpr int kFvWideX = 3;         // internal mode: the FP32-mixed block on an FP64 copy of x
 
 __host__ __device__ inline int64_t fv_padded_groups(int64_t G) { return (G + kFvU - 1) / kFvU * kFvU; }
 
@@ -185,7 +186,11 @@ __device__ __forceinline__ uint32_t fv_pattern2(uint32_t y, const uint64_t (&key
 // gathers KB values of x.
 template <int W, int PREC, int NB, int KB = 1>
 __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, int n_amp, int64_t tiles) {
-    using TIO = typename std::conditional<PREC == QSD_FP64, double, float>::type;
+    // PREC, or kFvWideX: FP64 arithmetic on an exact FP64 copy of FP32 x with
+    // FP32 y (bitwise the FP32-mixed product)
+    constexpr int AP = PREC == kFvWideX ? QSD_FP64 : PREC;
+    using TIO = typename std::conditional<AP == QSD_FP64, double, float>::type;  // x
+    using TY = typename std::conditional<PREC == QSD_FP64, double, float>::type;  // y
     extern __shared__ __align__(16) unsigned char fv_smem[];
     const int G = (int)p.G;
     const int Gp = (int)fv_padded_groups(p.G);
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         recA[g] = A;
         recB[g] = B;
     }
-    if (PREC == QSD_FP32_DOT2) {
+    if (AP == QSD_FP32_DOT2) {
         for (int i = threadIdx.x; i < n_amp; i += blockDim.x) ampf[i] = __ldg(p.ampf + i);
     } else {
         for (int i = threadIdx.x; i < n_amp; i += blockDim.x) amp[i] = __ldg(p.amp + i);
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
                 tail += (uint32_t)__popc(bal);
                 __syncwarp();
                 if (tail - head >= 32u) {
-                    fv_verify<W, PREC, TIO, KB>(p, q, head, 32, lane, key, amp, ampf, x, acc, as, ae);
+                    fv_verify<W, AP, TIO, KB>(p, q, head, 32, lane, key, amp, ampf, x, acc, as, ae);
                     head += 32u;
                     __syncwarp();
                 }
@@ -301,23 +306,23 @@ __global__ void __launch_bounds__(kFvThreads) k_apply_fv(const ApplyParams p, in
         }
         __syncwarp();
         if (tail != head)
-            fv_verify<W, PREC, TIO, KB>(p, q, head, (int)(tail - head), lane, key, amp, ampf, x, acc, as, ae);
+            fv_verify<W, AP, TIO, KB>(p, q, head, (int)(tail - head), lane, key, amp, ampf, x, acc, as, ae);
         __syncwarp();
         if (active) {
             const int64_t r = (int64_t)__ldg(p.hperm + pc);
             const double d = __ldg(p.diag + r);
             const TIO *xr = x + r * p.ld + p.col0;
-            TIO *yr = static_cast<TIO *>(p.y) + r * p.ld + p.col0;
-            if (PREC == QSD_FP32_DOT2) {
+            TY *yr = static_cast<TY *>(p.y) + r * p.ld + p.col0;
+            if (AP == QSD_FP32_DOT2) {
                 const float dh = (float)d, dl = (float)(d - (double)dh);
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
                     dot2_add(as[j], ae[j], dh, dl, (float)__ldg(xr + j));
-                    yr[j] = (TIO)(as[j] + ae[j]);
+                    yr[j] = (TY)(as[j] + ae[j]);
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < KB; ++j) yr[j] = (TIO)fma(d, (double)__ldg(xr + j), acc[j]);
+                for (int j = 0; j < KB; ++j) yr[j] = (TY)fma(d, (double)__ldg(xr + j), acc[j]);
             }
         }
     }

@@ -1,7 +1,8 @@
 // Instantiations of the filter/verify product for one precision mode.
 //
-// The build compiles this file once per mode with -DQSD_PREC=0, 1 or 2
-// (QSD_FP64, QSD_FP32_MIXED, QSD_FP32_DOT2).
+// The build compiles this file once per mode with -DQSD_PREC=0, 1, 2 or 3
+// (QSD_FP64, QSD_FP32_MIXED, QSD_FP32_DOT2, and kFvWideX: the FP32-mixed
+// block of 16 on a widened copy of x -- blocks of 16 only).
 #include <algorithm>
 
 #include "apply_fv.cuh"
@@ -35,8 +36,10 @@ void launch_nb(const ApplyParams &p, int n_amp, int nb, int num_sms, cudaStream_
 template <int W>
 void launch_w(const ApplyParams &p, int n_amp, int nb, int KB, int num_sms, cudaStream_t s) {
     if (KB == 16) launch_nb<W, 16>(p, n_amp, nb, num_sms, s);
+#if QSD_PREC != 3
     else if (KB == 1) launch_nb<W, 1>(p, n_amp, nb, num_sms, s);
-    else fail(QSD_ERR_INTERNAL, "filter/verify product: block widths 1 and 16 only");
+#endif
+    else fail(QSD_ERR_INTERNAL, "filter/verify product: block widths 1 and 16 only (16 on widened x)");
 }
 }  // namespace
 
