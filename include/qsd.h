@@ -141,8 +141,10 @@ int qsd_free_op(qsd_op op);
  * hash table (load factor <= 1/4, buckets of eight 8-bit tags with a 32-bit
  * row index per slot, bucket and tag taken from one GF(2)-linear hash of the
  * string) is built for lookups; for n <= 256 the rows are also listed in
- * bucket order (4 + 8 W bytes per row) for the hash-order product.  *dim_out
- * receives D.  Synchronises.
+ * bucket order (4 + 8 W bytes per row) for the hash-order product, and an
+ * occupancy filter over the hash (128 bits per bucket, 16 bytes per bucket)
+ * lets the filter/verify product reject absent columns with one 4-byte load
+ * (the paper's occupancy bit-set).  *dim_out receives D.  Synchronises.
  * Errors: QSD_ERR_CAPACITY when D would exceed 2^32 - 2. */
 int qsd_build_subspace(qsd_ctx ctx, int32_t n_qubits, int64_t n_in,
                        const uint64_t *words, int words_on_device,
