@@ -495,7 +495,9 @@ typedef struct {
 void qsd_lanczos_default_params(qsd_lanczos_params *p);
 
 /* Lowest eigenvalue of the real symmetric H_S with a Lanczos solver on the
- * device, fully reorthogonalised (classical Gram-Schmidt twice per step).
+ * device, fully reorthogonalised: classical Gram-Schmidt twice, each
+ * vector's second pass delayed to the next step, so that a step makes one
+ * dot pass and one subtraction pass over the basis.
  * *energy receives the Ritz value (FP64).  vec_out (optional, device double
  * [D]) receives the normalised Ritz vector.  info is optional.
  * Errors: QSD_ERR_NOT_HERMITIAN, QSD_ERR_COMPLEX_UNSUPPORTED,

@@ -2,9 +2,10 @@
 //
 // The paper hands its matrix-free operator to external eigensolvers (ARPACK,
 // PRIMME; Results, and Methods "Matrix evaluation").  Here the solver runs on
-// the GPU next to the product.  Per step: y = H v_j; classical Gram-Schmidt
-// against all previous vectors, applied twice, with FP64 dots (alpha_j is the
-// v_j coefficient of both passes); beta_{j+1} = |w|; v_{j+1} = w / beta_{j+1}.
+// the GPU next to the product.  Per step: u = H q_j; the three-term
+// recurrence, then one classical Gram-Schmidt pass against all previous
+// vectors with FP64 dots (complete reorthogonalisation, below); alpha_j and
+// beta_{j+1} = |w|; q_{j+1} = w / beta_{j+1}.
 // Every `check_every` steps one CTA solves the tridiagonal problem
 // (multisection on Sturm counts for the lowest eigenvalue, inverse iteration
 // for its eigenvector) and the residual estimate beta_{j+1} |s_j| reaches the
@@ -75,7 +76,7 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         jdev[0] = 0;  // the step
-        jdev[2] = 0;  // the block count of k_sub_sq
+        jdev[2] = 0;  // the block count of k_sub1
     }
     if (i >= D) return;
     w[i] = v0 ? v0[i] : uniform_pm1(seed, (uint64_t)i);
@@ -84,19 +85,63 @@ __global__ void k_start(int64_t D, uint64_t seed, const double *v0, double *w, i
 // Kernel bodies take their block index `vb` and block count `vg` as
 // arguments, so that a packed launch (below) can run the same arithmetic for
 // several jobs in one grid.
+//
+// One step j (j = the step counter): u = H q_j (the product); alpha0 =
+// q_j.u; the three-term recurrence w = u - alpha0 q_j - beta_j q_{j-1};
+// then one classical Gram-Schmidt pass of w against q_0..q_j, c = Q^T w,
+// w -= Q c; alpha_j = alpha0 + c_j, beta_{j+1} = |w|, q_{j+1} = w /
+// beta_{j+1}.  This is complete reorthogonalisation in the form of Golub and
+// Van Loan (Matrix Computations, the Lanczos chapter): the recurrence is
+// the first pass for the two vectors whose large coefficients cancel, the
+// full pass is their second, and w's coefficients on the older vectors are
+// of the order of the rounding error already, so one pass leaves them at
+// working precision.  2 D (j + 2) FP64 FMAs per step, half those of
+// classical Gram-Schmidt applied twice to u: the GB300's FP64 pipe (2 FMAs
+// per SM and cycle) bounds these passes.
 
-// partial[i * B + b] = sum over the block's rows of V[i][r] u[r], i <= j.
+// Rows [r0, r1) of row block vb of B.
+__device__ __forceinline__ void row_chunk(int64_t D, int vb, int B, int64_t &r0, int64_t &r1) {
+    const int64_t chunk = (D + B - 1) / B;
+    r0 = (int64_t)vb * chunk;
+    r1 = min(D, r0 + chunk);
+}
+
+// partial[vb] = sum over the block's rows of q[r] u[r] (block sum, fixed order)
+template <typename TV>
+__device__ void adot_body(const TV *__restrict__ q, const TV *__restrict__ u, int64_t D, double *partial, int vb,
+                          int B, double *sh) {
+    int64_t r0, r1;
+    row_chunk(D, vb, B, r0, r1);
+    const int64_t st = blockDim.x;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t r = r0 + threadIdx.x;
+    for (; r + st < r1; r += 2 * st) {
+        s0 = fma((double)q[r], (double)u[r], s0);
+        s1 = fma((double)q[r + st], (double)u[r + st], s1);
+    }
+    if (r < r1) s0 = fma((double)q[r], (double)u[r], s0);
+    const double t = block_sum(s0 + s1, sh);
+    if (threadIdx.x == 0) partial[vb] = t;
+}
+
+template <typename TV>
+__global__ void k_adot(const TV *__restrict__ q, const TV *__restrict__ u, int64_t D, double *partial) {
+    __shared__ double sh[32];
+    adot_body<TV>(q, u, D, partial, blockIdx.x, gridDim.x, sh);
+}
+
+// partial[i * B + vb] = sum over the block's rows of V[i][r] w[r].
 // Warp w of the block takes the vectors i = w, w + 8, ...: its lanes stride
-// the block's rows (coalesced; the block's slice of u stays in L1), four rows
+// the block's rows (coalesced; the block's slice of w stays in L1), four rows
 // per lane per round, and one warp reduction per vector -- no block barrier.
-// The vectors go two at a time, then one (each round loads u once for both:
-// 12 loads in flight per lane, no predicated loads);
-// per vector the sum runs in the same fixed order whatever the grouping, so
-// the result is deterministic.
-template <int G, typename TV, typename TU>
-__device__ __forceinline__ void gemv_t_group(const TV *__restrict__ V, int64_t D, int i0, int nw,
-                                             const TU *__restrict__ u, int64_t r0, int64_t r1, double *partial,
-                                             int vb, int B) {
+// The vectors go two at a time, then one (each round loads w once for both:
+// 12 loads in flight per lane, no predicated loads); per vector the sum runs
+// in the same fixed order whatever the grouping, so the result is
+// deterministic.  w has no __restrict__: the same block wrote it (plain
+// loads, coherent within the block after its barrier).
+template <int G, typename TV>
+__device__ __forceinline__ void dot_group(const TV *__restrict__ V, int64_t D, int i0, int nw, const double *w,
+                                          int64_t r0, int64_t r1, double *partial, int vb, int B) {
     const int lane = threadIdx.x & 31;
     const TV *__restrict__ vi[G];
     double s0[G], s1[G], s2[G], s3[G];
@@ -107,7 +152,7 @@ __device__ __forceinline__ void gemv_t_group(const TV *__restrict__ V, int64_t D
     }
     int64_t r = r0 + lane;
     for (; r + 96 < r1; r += 128) {
-        const double u0 = (double)u[r], u1 = (double)u[r + 32], u2 = (double)u[r + 64], u3 = (double)u[r + 96];
+        const double u0 = w[r], u1 = w[r + 32], u2 = w[r + 64], u3 = w[r + 96];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             s0[g] = fma((double)vi[g][r], u0, s0[g]);
@@ -117,7 +162,7 @@ __device__ __forceinline__ void gemv_t_group(const TV *__restrict__ V, int64_t D
         }
     }
     for (; r < r1; r += 32) {
-        const double u0 = (double)u[r];
+        const double u0 = w[r];
 #pragma unroll
         for (int g = 0; g < G; ++g) s0[g] = fma((double)vi[g][r], u0, s0[g]);
     }
@@ -128,64 +173,74 @@ __device__ __forceinline__ void gemv_t_group(const TV *__restrict__ V, int64_t D
     }
 }
 
-template <typename TV, typename TU>
-__device__ void gemv_t_body(const TV *__restrict__ V, int64_t D, int nvec, const TU *__restrict__ u,
-                            double *partial, int vb, int B, double *sh) {
-    (void)sh;
-    const int64_t chunk = (D + B - 1) / B;
-    const int64_t r0 = (int64_t)vb * chunk, r1 = min(D, r0 + chunk);
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Row block vb of the step's dot pass.  Every block sums the B partials of
+// q_j.u in fixed order into alpha0 (block 0 keeps it in sc[0]), writes its
+// rows of w = u - alpha0 q_j - beta_j q_{j-1}, and after a barrier takes
+// partial[i * B + vb] for i <= j.  a0s: a shared double of the caller.
+template <typename TV>
+__device__ void dot1_body(const TV *__restrict__ V, int64_t D, int j, const TV *__restrict__ u,
+                          const double *__restrict__ pa, double bj, double *w, double *partial, double *sc, int vb,
+                          int B, double *sh, double &a0s) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) t += pa[b];
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) {
+        a0s = t;
+        if (vb == 0) sc[0] = t;
+    }
+    __syncthreads();
+    const double a0 = a0s;
+    int64_t r0, r1;
+    row_chunk(D, vb, B, r0, r1);
+    const TV *__restrict__ qj = V + (size_t)j * D;
+    if (j > 0) {
+        const TV *__restrict__ qp = V + (size_t)(j - 1) * D;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+            w[r] = fma(-bj, (double)qp[r], fma(-a0, (double)qj[r], (double)u[r]));
+    } else {
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) w[r] = fma(-a0, (double)qj[r], (double)u[r]);
+    }
+    __syncthreads();  // the block's rows of w, visible to all its threads
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, nvec = j + 1;
     int i = warp;
-    for (; i + nw < nvec; i += 2 * nw) gemv_t_group<2>(V, D, i, nw, u, r0, r1, partial, vb, B);
-    if (i < nvec) gemv_t_group<1>(V, D, i, nw, u, r0, r1, partial, vb, B);
-}
-constexpr int kGemvSh = 32;
-
-template <typename TV, typename TU>
-__global__ void k_gemv_t(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                         const TU *__restrict__ u, double *partial) {
-    __shared__ double sh[kGemvSh];
-    gemv_t_body<TV, TU>(V, D, *jdev + 1, u, partial, blockIdx.x, gridDim.x, sh);
+    for (; i + nw < nvec; i += 2 * nw) dot_group<2, TV>(V, D, i, nw, w, r0, r1, partial, vb, B);
+    if (i < nvec) dot_group<1, TV>(V, D, i, nw, w, r0, r1, partial, vb, B);
 }
 
-// h[i] = sum_b partial[i][b] in fixed order (block i; blocks past j exit);
-// alpha[j] += h[j]
-__device__ void reduce_rows_body(const double *__restrict__ partial, int j, int B, double *h, double *alpha, int i,
-                                 double *sh) {
-    if (i > j) return;
+template <typename TV>
+__global__ void k_dot1(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev, const TV *__restrict__ u,
+                       const double *__restrict__ pa, const double *__restrict__ beta, double *w, double *partial,
+                       double *sc) {
+    __shared__ double sh[32];
+    __shared__ double a0s;
+    const int j = *jdev;
+    dot1_body<TV>(V, D, j, u, pa, j > 0 ? beta[j] : 0.0, w, partial, sc, blockIdx.x, gridDim.x, sh, a0s);
+}
+
+// h[i] = sum_b partial[i][b] in fixed order (block i; blocks past j exit)
+__device__ void reduce_body(const double *__restrict__ partial, int B, double *h, int i, double *sh) {
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += partial[(size_t)i * B + b];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-        h[i] = s;
-        if (i == j) alpha[j] += s;
-    }
+    if (threadIdx.x == 0) h[i] = s;
 }
 
-__global__ void k_reduce_rows(const double *__restrict__ partial, const int *__restrict__ jdev, int B, double *h,
-                              double *alpha) {
+__global__ void k_reduce(const double *__restrict__ partial, const int *__restrict__ jdev, int B, double *h) {
     __shared__ double sh[32];
-    reduce_rows_body(partial, *jdev, B, h, alpha, blockIdx.x, sh);
+    if ((int)blockIdx.x > *jdev) return;
+    reduce_body(partial, B, h, blockIdx.x, sh);
 }
 
-// w[r] = u[r] - sum_{i<=j} V[i][r] h[i]
-template <typename TV, typename TU>
-__device__ void gemv_sub_body(const TV *__restrict__ V, int64_t D, int nvec, const double *__restrict__ h,
-                              const TU *u, double *w, int vb, double *hs) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
-    __syncthreads();
-    const int64_t r = (int64_t)vb * blockDim.x + threadIdx.x;
-    if (r >= D) return;
-    double acc = (double)u[r];
+// Row r of the subtraction pass: w[r] -= sum_{i<=j} V[i][r] c_i (c in
+// shared memory); returns w[r]^2 (0 past the end).
+template <typename TV>
+__device__ __forceinline__ double sub_row(const TV *__restrict__ V, int64_t D, int nvec, const double *hs, double *w,
+                                          int64_t r) {
+    if (r >= D) return 0.0;
+    double acc = w[r];
     for (int i = 0; i < nvec; ++i) acc = fma(-(double)V[(size_t)i * D + r], hs[i], acc);
     w[r] = acc;
-}
-
-template <typename TV, typename TU>
-__global__ void k_gemv_sub(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                           const double *__restrict__ h, const TU *u, double *w) {
-    extern __shared__ double hs[];
-    gemv_sub_body<TV, TU>(V, D, *jdev + 1, h, u, w, blockIdx.x, hs);
+    return acc * acc;
 }
 
 __device__ void sq_partial_body(const double *__restrict__ w, int64_t D, double *partial, int vb, int vg,
@@ -233,34 +288,25 @@ __global__ void k_next(const double *__restrict__ w, const double *__restrict__ 
     next_body<TV>(w, nrm[j1], j1, D, m, V, vcur, blockIdx.x);
 }
 
-__global__ void k_incr(int *jdev) { *jdev += 1; }
 
-// ---- fused tail of one step (single-job path)
-// The second Gram-Schmidt subtraction also sums w^2 per 256-row block
-// (k_sub_sq); the last of its blocks to finish (an atomic count, no waiting)
-// sums those partials in block order into beta_{j+1}, and k_norm_next writes
-// v_{j+1} = w beta_{j+1}^-1: 8 launches per step, the subtraction's full
-// grid, and the norm summed once.
-
-// w[r] -= sum_{i<=j} V[i][r] h[i]; part[b] = sum over the block's rows of
-// w^2; the last block: beta[j+1] = sqrt(sum_b part[b]), count back to 0
+// ---- subtraction pass and normalisation (single-job path)
+// The subtraction pass also sums w^2 per 256-row block; the last of its
+// blocks to finish (an atomic count, no waiting) sums those partials in block
+// order into beta_{j+1} = |w| and advances the step counter (every block has
+// read it by then), and k_norm_next writes q_{j+1} = w beta_{j+1}^-1: 6
+// launches per step (product, q_j.u, dot pass, its sums, subtraction,
+// normalisation).  Block 0 also writes alpha_j = alpha0 + c_j.
 template <typename TV>
-__global__ void k_sub_sq(const TV *__restrict__ V, int64_t D, const int *__restrict__ jdev,
-                         const double *__restrict__ h, double *w, double *part, unsigned *count, double *beta) {
+__global__ void k_sub1(const TV *__restrict__ V, int64_t D, int *jdev, const double *__restrict__ h, double *w,
+                       double *part, unsigned *count, double *alpha, double *beta, const double *__restrict__ sc) {
     extern __shared__ double hs[];
     __shared__ double sh[32];
     __shared__ bool last;
-    const int nvec = *jdev + 1;
+    const int j = *jdev, nvec = j + 1;
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double sq = 0.0;
-    if (r < D) {
-        double acc = w[r];
-        for (int i = 0; i < nvec; ++i) acc = fma(-(double)V[(size_t)i * D + r], hs[i], acc);
-        w[r] = acc;
-        sq = acc * acc;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) alpha[j] = sc[0] + hs[j];
+    double sq = sub_row<TV>(V, D, nvec, hs, w, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     sq = block_sum(sq, sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = sq;
@@ -277,13 +323,16 @@ __global__ void k_sub_sq(const TV *__restrict__ V, int64_t D, const int *__restr
     if (threadIdx.x == 0) {
         beta[nvec] = sqrt(t);
         *count = 0u;
+        *jdev = nvec;
     }
 }
 
+// q_{j1} = w / beta_{j1} into V[j1] (when j1 <= m) and vcur, j1 = the
+// advanced step counter
 template <typename TV>
 __global__ void k_norm_next(const double *__restrict__ w, const int *__restrict__ jdev, int64_t D, int m, TV *V,
                             TV *vcur, const double *__restrict__ beta) {
-    const int j1 = *jdev + 1;
+    const int j1 = *jdev;
     const double nrm = beta[j1];
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x) {
@@ -377,26 +426,48 @@ __global__ void k_tridiag(const double *__restrict__ alpha, const double *__rest
     tridiag_body(alpha, beta, *jdev, out, sm);
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The serial parts run on lane 0 of warp 0; the loops without a chain
+// (bounds, scale, pivot reciprocals, normalisation) are spread over warp 0's
+// lanes: on the GB300 a lone FP64 instruction costs about as much of the FP64
+// pipe as a full warp's.
 __device__ void tridiag_body(const double *__restrict__ alpha, const double *__restrict__ beta, int m, double *out,
                              double *sm) {
     if (m <= 0) return;
     double *a = sm, *b = sm + m, *s = sm + 2 * m;
     __shared__ double lo_hi[2];
+    const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         a[i] = alpha[i];
         b[i] = i ? beta[i] : 0.0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // Gershgorin bounds (min and max are exact in any order)
         double lo = a[0], hi = a[0];
-        for (int i = 0; i < m; ++i) {
+        for (int i = lane; i < m; i += 32) {
             const double rad = (i ? fabs(b[i]) : 0.0) + (i + 1 < m ? fabs(b[i + 1]) : 0.0);
             lo = fmin(lo, a[i] - rad);
             hi = fmax(hi, a[i] + rad);
         }
-        const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
-        lo_hi[0] = lo - pad;
-        lo_hi[1] = hi + pad;
+        lo = warp_min(lo);
+        hi = warp_max(hi);
+        if (lane == 0) {
+            const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+            lo_hi[0] = lo - pad;
+            lo_hi[1] = hi + pad;
+        }
     }
     // b_i^2 for the Sturm counts, in the eigenvector's space (free until then)
     for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = b[i] * b[i];
@@ -426,73 +497,93 @@ __device__ void tridiag_body(const double *__restrict__ alpha, const double *__r
         __syncthreads();
         if (nhi - nlo <= 4e-16 * fmax(fabs(nlo), fabs(nhi)) + 1e-300 || (nlo == lo && nhi == hi)) break;
     }
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
     const double theta = 0.5 * (lo_hi[0] + lo_hi[1]);
     // Inverse iteration (T - theta I) s = rhs.  Gaussian elimination with
     // partial pivoting on the tridiagonal matrix gives an upper factor with
     // two super-diagonals (D_, U1, U2), multipliers Lm and swap flags piv.
     double scale = 0.0;
-    for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(a[i]) + fabs(b[i]));
+    for (int i = lane; i < m; i += 32) scale = fmax(scale, fabs(a[i]) + fabs(b[i]));
+    scale = warp_max(scale);
     const double tiny = 1e-14 * fmax(scale, 1e-300);
     double *D_ = sm + 3 * m, *U1 = sm + 4 * m, *U2 = sm + 5 * m, *Lm = sm + 6 * m;
     int *piv = reinterpret_cast<int *>(sm + 7 * m);
-    for (int i = 0; i < m; ++i) {
+    for (int i = lane; i < m; i += 32) {
         D_[i] = a[i] - theta;
         U1[i] = i + 1 < m ? b[i + 1] : 0.0;
         U2[i] = 0.0;
+        s[i] = 1.0;
     }
-    for (int i = 0; i + 1 < m; ++i) {
-        const double sub = b[i + 1];  // entry (i+1, i)
-        if (fabs(sub) > fabs(D_[i])) {
-            // row i+1 (still original: sub, D_[i+1], U1[i+1]) becomes the pivot row
-            piv[i] = 1;
-            const double mult = D_[i] / sub;
-            Lm[i] = mult;
-            const double u0 = U1[i], w0 = U2[i];
-            D_[i] = sub;
-            U1[i] = D_[i + 1];
-            U2[i] = U1[i + 1];
-            D_[i + 1] = u0 - mult * U1[i];
-            U1[i + 1] = w0 - mult * U2[i];
-        } else {
-            piv[i] = 0;
-            if (fabs(D_[i]) < tiny) D_[i] = D_[i] >= 0 ? tiny : -tiny;
-            const double mult = sub / D_[i];
-            Lm[i] = mult;
-            D_[i + 1] -= mult * U1[i];
-        }
-    }
-    if (fabs(D_[m - 1]) < tiny) D_[m - 1] = D_[m - 1] >= 0 ? tiny : -tiny;
-    // the pivots' reciprocals, once: the iterations below multiply (an FP64
-    // division costs several operations of the slow FP64 pipe, serially here)
-    for (int i = 0; i < m; ++i) D_[i] = 1.0 / D_[i];
-    for (int i = 0; i < m; ++i) s[i] = 1.0;
-    for (int iter = 0; iter < 3; ++iter) {
+    __syncwarp();
+    if (lane == 0) {
         for (int i = 0; i + 1 < m; ++i) {
-            if (piv[i]) {
-                const double t = s[i];
-                s[i] = s[i + 1];
-                s[i + 1] = t - Lm[i] * s[i];
+            const double sub = b[i + 1];  // entry (i+1, i)
+            if (fabs(sub) > fabs(D_[i])) {
+                // row i+1 (still original: sub, D_[i+1], U1[i+1]) becomes the pivot row
+                piv[i] = 1;
+                const double mult = D_[i] / sub;
+                Lm[i] = mult;
+                const double u0 = U1[i], w0 = U2[i];
+                D_[i] = sub;
+                U1[i] = D_[i + 1];
+                U2[i] = U1[i + 1];
+                D_[i + 1] = u0 - mult * U1[i];
+                U1[i + 1] = w0 - mult * U2[i];
             } else {
-                s[i + 1] -= Lm[i] * s[i];
+                piv[i] = 0;
+                if (fabs(D_[i]) < tiny) D_[i] = D_[i] >= 0 ? tiny : -tiny;
+                const double mult = sub / D_[i];
+                Lm[i] = mult;
+                D_[i + 1] -= mult * U1[i];
             }
         }
-        for (int i = m - 1; i >= 0; --i) {
-            double v = s[i];
-            if (i + 1 < m) v -= U1[i] * s[i + 1];
-            if (i + 2 < m) v -= U2[i] * s[i + 2];
-            s[i] = v * D_[i];
-        }
-        double nrm = 0.0;
-        for (int i = 0; i < m; ++i) nrm += s[i] * s[i];
-        const double inv = 1.0 / sqrt(nrm);
-        for (int i = 0; i < m; ++i) s[i] *= inv;
+        if (fabs(D_[m - 1]) < tiny) D_[m - 1] = D_[m - 1] >= 0 ? tiny : -tiny;
     }
-    out[0] = theta;
-    out[1] = fabs(beta[m] * s[m - 1]);
-    out[2] = beta[m];
-    out[3] = (double)m;
-    for (int i = 0; i < m; ++i) out[4 + i] = s[i];
+    __syncwarp();
+    // the pivots' reciprocals, once: the iterations below multiply
+    for (int i = lane; i < m; i += 32) D_[i] = 1.0 / D_[i];
+    __syncwarp();
+    // up to three iterations; the solve's residual is |rhs| / |x| exactly,
+    // so once |x| >= |rhs| / (1e-15 scale) the normalised s is an
+    // eigenvector to working precision (one iteration when theta is within
+    // a few ulps of the eigenvalue and the start has a fair component on it)
+    double rhs2 = (double)m;  // |rhs|^2 of the first iteration (all ones)
+    for (int iter = 0; iter < 3; ++iter) {
+        if (lane == 0) {
+            for (int i = 0; i + 1 < m; ++i) {
+                if (piv[i]) {
+                    const double t = s[i];
+                    s[i] = s[i + 1];
+                    s[i + 1] = t - Lm[i] * s[i];
+                } else {
+                    s[i + 1] -= Lm[i] * s[i];
+                }
+            }
+            for (int i = m - 1; i >= 0; --i) {
+                double v = s[i];
+                if (i + 1 < m) v -= U1[i] * s[i + 1];
+                if (i + 2 < m) v -= U2[i] * s[i + 2];
+                s[i] = v * D_[i];
+            }
+        }
+        __syncwarp();
+        double nrm = 0.0;
+        for (int i = lane; i < m; i += 32) nrm = fma(s[i], s[i], nrm);
+        nrm = warp_sum(nrm);  // the same value in every lane
+        const double inv = 1.0 / sqrt(nrm);
+        for (int i = lane; i < m; i += 32) s[i] *= inv;
+        __syncwarp();
+        const double q = 1e-15 * scale;
+        if (nrm * (q * q) >= rhs2) break;
+        rhs2 = 1.0;
+    }
+    if (lane == 0) {
+        out[0] = theta;
+        out[1] = fabs(beta[m] * s[m - 1]);
+        out[2] = beta[m];
+        out[3] = (double)m;
+    }
+    for (int i = lane; i < m; i += 32) out[4 + i] = s[i];
 }
 
 // u[r] = sum_{i < m} V[i][r] s[i], m = *jdev
@@ -564,23 +655,42 @@ __device__ __forceinline__ int find_job(const int *first, int n, int b) {
     return lo;
 }
 
-// which = 0: u = hv (type TV); 1: u = w (double)
-template <typename TV, typename TU>
-__global__ void kq_gemv_t(const PackJob *__restrict__ jobs, const int *__restrict__ first,
-                          const int *__restrict__ np, int which) {
+// q_j.u for every job (job i's virtual grid: its B dot-pass row blocks)
+template <typename TV>
+__global__ void kq_adot(const PackJob *__restrict__ jobs, const int *__restrict__ first, const int *__restrict__ np) {
     __shared__ PackStage st;
+    __shared__ double sh[32];
     const int n = stage_pack(jobs, first, np, st), total = st.first[n];
     for (int b = blockIdx.x; b < total; b += gridDim.x) {
         const int i = find_job(st.first, n, b), j = st.j[i];
         if (j < 0) continue;  // block-uniform
         const PackJob &J = jobs[i];
-        const TU *u = which ? reinterpret_cast<const TU *>(J.w) : static_cast<const TU *>(J.hv);
-        gemv_t_body<TV, TU>(static_cast<const TV *>(J.V), J.D, j + 1, u, J.part, b - st.first[i], J.B, nullptr);
+        adot_body<TV>(static_cast<const TV *>(J.vcur), static_cast<const TV *>(J.hv), J.D,
+                      J.part + (size_t)(J.m + 1) * J.B, b - st.first[i], J.B, sh);  // ends on a barrier
     }
 }
 
-__global__ void kq_reduce_rows(const PackJob *__restrict__ jobs, const int *__restrict__ first,
-                               const int *__restrict__ np) {
+// the dot pass for every job
+template <typename TV>
+__global__ void kq_dot1(const PackJob *__restrict__ jobs, const int *__restrict__ first, const int *__restrict__ np) {
+    __shared__ PackStage st;
+    __shared__ double sh[32];
+    __shared__ double a0s;
+    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = find_job(st.first, n, b), j = st.j[i];
+        if (j < 0) continue;
+        const PackJob &J = jobs[i];
+        const int m = J.m;
+        dot1_body<TV>(static_cast<const TV *>(J.V), J.D, j, static_cast<const TV *>(J.hv),
+                      J.part + (size_t)(m + 1) * J.B, j > 0 ? J.beta[j] : 0.0, J.w, J.part, J.h + (m + 1),
+                      b - st.first[i], J.B, sh, a0s);
+        __syncthreads();  // a0s and sh are rewritten next round
+    }
+}
+
+__global__ void kq_reduce(const PackJob *__restrict__ jobs, const int *__restrict__ first,
+                          const int *__restrict__ np) {
     __shared__ PackStage st;
     __shared__ double sh[32];
     const int n = stage_pack(jobs, first, np, st), total = st.first[n];
@@ -588,30 +698,14 @@ __global__ void kq_reduce_rows(const PackJob *__restrict__ jobs, const int *__re
         const int i = find_job(st.first, n, b), j = st.j[i], row = b - st.first[i];
         if (j < 0 || row > j) continue;
         const PackJob &J = jobs[i];
-        reduce_rows_body(J.part, j, J.B, J.h, J.alpha, row, sh);  // ends on a barrier
+        reduce_body(J.part, J.B, J.h, row, sh);  // ends on a barrier
     }
 }
 
+// the subtraction pass for every job: w -= V c, squares of w per 256-row
+// block; a job's block 0 writes its alpha_j
 template <typename TV>
-__global__ void kq_gemv_sub(const PackJob *__restrict__ jobs, const int *__restrict__ first,
-                            const int *__restrict__ np) {
-    extern __shared__ double hs[];
-    __shared__ PackStage st;
-    const int n = stage_pack(jobs, first, np, st), total = st.first[n];
-    for (int b = blockIdx.x; b < total; b += gridDim.x) {
-        const int i = find_job(st.first, n, b), j = st.j[i];
-        if (j < 0) continue;
-        const PackJob &J = jobs[i];
-        gemv_sub_body<TV, TV>(static_cast<const TV *>(J.V), J.D, j + 1, J.h, static_cast<const TV *>(J.hv), J.w,
-                              b - st.first[i], hs);
-        __syncthreads();  // hs is reloaded next round
-    }
-}
-
-// k_sub_sq for every job: w -= V h, squares of w per 256-row block
-template <typename TV>
-__global__ void kq_sub_sq(const PackJob *__restrict__ jobs, const int *__restrict__ first,
-                          const int *__restrict__ np) {
+__global__ void kq_sub1(const PackJob *__restrict__ jobs, const int *__restrict__ first, const int *__restrict__ np) {
     extern __shared__ double hs[];
     __shared__ PackStage st;
     __shared__ double sh[32];
@@ -620,26 +714,19 @@ __global__ void kq_sub_sq(const PackJob *__restrict__ jobs, const int *__restric
         const int i = find_job(st.first, n, b), j = st.j[i];
         if (j < 0) continue;
         const PackJob &J = jobs[i];
-        const int nvec = j + 1, vb = b - st.first[i];
-        const TV *__restrict__ V = static_cast<const TV *>(J.V);
-        const int64_t D = J.D;
-        double *w = J.w;
+        const int nvec = j + 1, vb = b - st.first[i], m = J.m;
         for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = J.h[k];
         __syncthreads();
-        const int64_t r = (int64_t)vb * blockDim.x + threadIdx.x;
-        double sq = 0.0;
-        if (r < D) {
-            double acc = w[r];
-            for (int k = 0; k < nvec; ++k) acc = fma(-(double)V[(size_t)k * D + r], hs[k], acc);
-            w[r] = acc;
-            sq = acc * acc;
-        }
+        if (vb == 0 && threadIdx.x == 0) J.alpha[j] = J.h[m + 1] + hs[j];
+        double sq = sub_row<TV>(static_cast<const TV *>(J.V), J.D, nvec, hs, J.w,
+                                (int64_t)vb * blockDim.x + threadIdx.x);
         sq = block_sum(sq, sh);  // ends on a barrier: hs is free again
-        if (threadIdx.x == 0) J.part[(size_t)(J.m + 2) * J.B + vb] = sq;
+        if (threadIdx.x == 0) J.part[(size_t)(m + 2) * J.B + vb] = sq;
     }
 }
 
-// k_norm_next for every job (job i's virtual grid: nb blocks)
+// k_norm_next for every job (job i's virtual grid: nb blocks); each block
+// sums the job's squares in the order of k_sub1's last block
 template <typename TV>
 __global__ void kq_norm_next(const PackJob *__restrict__ jobs, const int *__restrict__ first,
                              const int *__restrict__ np) {
@@ -756,12 +843,10 @@ void enqueue_pack_steps(qsd_ctx ctx, unsigned char *d, const PackLayout &L, int 
                                    pack_class_width(c), pack_class_lanes(c), 1, prec, ctx->num_sms, s);
             }
         }
-        kq_gemv_t<TV, TV><<<G, kLanczosThreads, 0, s>>>(dj, fB, np, 0);
-        kq_reduce_rows<<<2 * G, 128, 0, s>>>(dj, fM, np);
-        kq_gemv_sub<TV><<<G, 256, hsm, s>>>(dj, fD, np);
-        kq_gemv_t<TV, double><<<G, kLanczosThreads, 0, s>>>(dj, fB, np, 1);
-        kq_reduce_rows<<<2 * G, 128, 0, s>>>(dj, fM, np);
-        kq_sub_sq<TV><<<G, 256, hsm, s>>>(dj, fD, np);
+        kq_adot<TV><<<G, kLanczosThreads, 0, s>>>(dj, fB, np);
+        kq_dot1<TV><<<G, kLanczosThreads, 0, s>>>(dj, fB, np);
+        kq_reduce<<<2 * G, 128, 0, s>>>(dj, fM, np);
+        kq_sub1<TV><<<G, 256, hsm, s>>>(dj, fD, np);
         kq_norm_next<TV><<<G, 256, 0, s>>>(dj, fN, np);
         kq_incr<<<1, 256, 0, s>>>(dj, np);
     }
@@ -953,14 +1038,15 @@ void LanczosJob::init(qsd_ctx c, qsd_op o, qsd_sub su, const double *d, int prod
     prepare_product(ctx, op, sub, st);
     const size_t sv = fp32 ? 4 : 8;
     auto A = [&](DevBuf &b, size_t n) {
-        if (stream_ordered) b.alloc_async(n, s);
+        if (pool) b.alloc_pool(n, pool, s);
+        else if (stream_ordered) b.alloc_async(n, s);
         else b.alloc(n);
     };
     A(V, (size_t)(m + 1) * D * sv);
     A(vcur, (size_t)D * sv);
     A(hv, (size_t)D * sv);
     A(w, (size_t)D * 8);
-    A(h, (size_t)(m + 2) * 8);
+    A(h, ((size_t)m + 9) * 8);
     A(part, ((size_t)(m + 2) * B + nbD) * 8);
     A(alpha, (size_t)(m + 2) * 8);
     A(beta, (size_t)(m + 3) * 8);
@@ -1007,20 +1093,19 @@ static void enqueue_steps_t(LanczosJob &J, int n) {
     double *alpha = J.alpha.as<double>(), *beta = J.beta.as<double>();
     const int *j = J.jdev.as<int>();
     const size_t hsm = (size_t)(J.m + 1) * 8;
-    // squares of w per 256-row block after the partial dots
-    double *psq = part + (size_t)(J.m + 2) * J.B;
-    unsigned *count = reinterpret_cast<unsigned *>(J.jdev.as<int>() + 2);
+    // part: the dot pass's partials ((m + 1) B), those of q_j.u (B), the
+    // squares of w per 256-row block (nbD); h: c_0..c_m, then alpha0
+    double *pa = part + (size_t)(J.m + 1) * J.B, *psq = part + (size_t)(J.m + 2) * J.B, *sc = h + (J.m + 1);
+    int *jm = J.jdev.as<int>();
+    unsigned *count = reinterpret_cast<unsigned *>(jm + 2);
     const int nb = std::min<int>(J.nbD, 4 * ctx_sms(J.ctx));
     for (int t = 0; t < n; ++t) {
         apply_H(J.ctx, J.op, J.sub, J.diag, J.prec, 1, vc, hv, s);
-        k_gemv_t<TV, TV><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, hv, part);
-        k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
-        k_gemv_sub<TV, TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, hv, w);
-        k_gemv_t<TV, double><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, w, part);
-        k_reduce_rows<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h, alpha);
-        k_sub_sq<TV><<<J.nbD, 256, hsm, s>>>(V, J.D, j, h, w, psq, count, beta);
+        k_adot<TV><<<J.B, kLanczosThreads, 0, s>>>(vc, hv, J.D, pa);
+        k_dot1<TV><<<J.B, kLanczosThreads, 0, s>>>(V, J.D, j, hv, pa, beta, w, part, sc);
+        k_reduce<<<J.m + 1, 128, 0, s>>>(part, j, J.B, h);
+        k_sub1<TV><<<J.nbD, 256, hsm, s>>>(V, J.D, jm, h, w, psq, count, alpha, beta, sc);
         k_norm_next<TV><<<nb, 256, 0, s>>>(w, j, J.D, J.m, V, vc, beta);
-        k_incr<<<1, 1, 0, s>>>(J.jdev.as<int>());
     }
     k_tridiag<<<1, kLanczosThreads, tri_smem(J.m), s>>>(alpha, beta, j, J.tri.as<double>());
     QSD_LAUNCH_CHECK();
@@ -1089,10 +1174,10 @@ void ResidJob::init(qsd_ctx c, int64_t Dn, cudaStream_t st, bool stream_ordered)
     D = Dn;
     s = st;
     B = dot_blocks(D, ctx->num_sms);
-    if (stream_ordered) {
-        hu.alloc_async((size_t)D * 8, s);
-        r.alloc_async((size_t)D * 8, s);
-        part.alloc_async((size_t)2 * B * 8 + 64, s);
+    if (pool || stream_ordered) {
+        hu.alloc_pool((size_t)D * 8, pool, s);
+        r.alloc_pool((size_t)D * 8, pool, s);
+        part.alloc_pool((size_t)2 * B * 8 + 64, pool, s);
     } else {
         hu.alloc((size_t)D * 8);
         r.alloc((size_t)D * 8);
@@ -1166,12 +1251,17 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
     const bool graphs = p.use_graphs != 0;
     int applies = 0, total_steps = 0, restarts = 0;
     bool timeout = false;
-    DevBuf u((size_t)D * 8);
+    // workspace from the context's pool: a repeated solve maps nothing
+    cudaMemPool_t pool = ctx->pool;
+    DevBuf u;
+    u.alloc_pool((size_t)D * 8, pool, s);
     ResidJob R;
+    R.pool = pool;
     R.init(ctx, D, s, false);
 
     // main phase: FP64, or FP32 until FP32 round-off limits the estimate
     LanczosJob J;
+    J.pool = pool;
     J.init(ctx, op, sub, diag, p.precision, p.max_steps, p.check_every, s, false);
     // pick the product paths now: graph capture must not time anything
     QSD_CUDA(cudaMemsetAsync(J.vcur.p, 0, J.vcur.bytes, s));
@@ -1204,10 +1294,12 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
     if (mixed && !converged && !timeout) {
         // FP64 restarts from the current Ritz vector
         LanczosJob K;
+        K.pool = pool;
         K.init(ctx, op, sub, diag, QSD_FP64, std::max(p.refine_steps, 2), p.check_every, s, false);
         double prev = rq;
         const double rtol = p.refine_tol > 0 ? p.refine_tol : 1e-10;
-        DevBuf start((size_t)D * 8);
+        DevBuf start;
+        start.alloc_pool((size_t)D * 8, pool, s);
         while (!converged && restarts < std::max(p.max_refine, 0)) {
             if (late()) { timeout = true; break; }
             QSD_CUDA(cudaMemcpyAsync(start.p, u.p, (size_t)D * 8, cudaMemcpyDeviceToDevice, s));

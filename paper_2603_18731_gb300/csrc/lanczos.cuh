@@ -31,6 +31,7 @@ struct LanczosJob {
     DevBuf V, vcur, hv, w, h, part, alpha, beta, tri, jdev;
     double *hpin = nullptr;  // [theta, estimate, beta_m, m]
     bool own_pin = true;     // false: hpin lent by the caller (set before init)
+    cudaMemPool_t pool = nullptr;  // set before init: the buffers come from it (stream-ordered)
     cudaGraphExec_t graph = nullptr;
 
     LanczosJob() = default;
@@ -94,6 +95,7 @@ struct ResidJob {
     DevBuf hu, r, part;
     double *hpin = nullptr;  // [u^T H u, u^T u, |H u - theta u|]
     bool own_pin = true;     // false: hpin lent by the caller (set before init)
+    cudaMemPool_t pool = nullptr;  // set before init: the buffers come from it (stream-ordered)
 
     ResidJob() = default;
     ResidJob(const ResidJob &) = delete;

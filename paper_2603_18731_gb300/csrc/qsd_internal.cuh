@@ -66,6 +66,8 @@ struct DevBuf {
     }
     ~DevBuf() { release(); }
     void alloc(size_t n);
+    // stream-ordered from `pool` (nullptr: the device's default pool)
+    void alloc_pool(size_t n, cudaMemPool_t pool, cudaStream_t s);
     void alloc_async(size_t n, cudaStream_t s);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
@@ -129,6 +131,9 @@ struct qsd_ctx_s {
     qsd::CsrState csr;
     uint32_t *d_err = nullptr;   // device error word of the last kernels
     uint32_t *h_err = nullptr;   // pinned mirror
+    // stream-ordered pool of the eigensolver's workspace: freed blocks up to
+    // its release threshold stay mapped for the next solve on the context
+    cudaMemPool_t pool = nullptr;
 };
 
 namespace qsd {
