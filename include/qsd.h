@@ -71,10 +71,14 @@ typedef struct qsd_sub_s *qsd_sub;
 /* ------------------------------------------------------------- contexts */
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * to enqueue on (e.g. a PyTorch stream), or NULL for a stream owned by the
- * context.  *out receives the handle. */
+ * context.  *out receives the handle.  The context owns a stream-ordered
+ * memory pool for the eigensolver's workspace: blocks freed at the end of a
+ * solve stay mapped, up to 1/16 of the device's memory, so that the next
+ * solve on the context allocates without mapping memory again. */
 int qsd_create(int device, void *cuda_stream, qsd_ctx *out);
 
-/* Destroy a context.  Operators and subspaces made on it must be freed first. */
+/* Destroy a context (and its pool).  Operators and subspaces made on it must
+ * be freed first. */
 int qsd_destroy(qsd_ctx ctx);
 
 /* Message of the last failed call on `ctx` (or of the calling thread's last
@@ -495,9 +499,12 @@ typedef struct {
 void qsd_lanczos_default_params(qsd_lanczos_params *p);
 
 /* Lowest eigenvalue of the real symmetric H_S with a Lanczos solver on the
- * device, fully reorthogonalised: classical Gram-Schmidt twice, each
- * vector's second pass delayed to the next step, so that a step makes one
- * dot pass and one subtraction pass over the basis.
+ * device, fully reorthogonalised: per step the three-term recurrence, then
+ * one classical Gram-Schmidt pass of the residual against every earlier
+ * vector with FP64 dots (complete reorthogonalisation; the recurrence is the
+ * first pass for the two vectors whose coefficients cancel).  The workspace
+ * (the basis of max_steps + 1 vectors of D values and a few vectors more)
+ * comes from the context's pool (qsd_create).
  * *energy receives the Ritz value (FP64).  vec_out (optional, device double
  * [D]) receives the normalised Ritz vector.  info is optional.
  * Errors: QSD_ERR_NOT_HERMITIAN, QSD_ERR_COMPLEX_UNSUPPORTED,
