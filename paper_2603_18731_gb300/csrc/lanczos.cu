@@ -1251,7 +1251,15 @@ int lanczos_ground_state(qsd_ctx ctx, qsd_op op, qsd_sub sub, const qsd_lanczos_
     const bool graphs = p.use_graphs != 0;
     int applies = 0, total_steps = 0, restarts = 0;
     bool timeout = false;
-    // workspace from the context's pool: a repeated solve maps nothing
+    // workspace from the context's pool: a repeated solve maps nothing.  The
+    // guard, destroyed after every buffer below, synchronises the stream once
+    // their stream-ordered frees are enqueued: the pool then gives back what
+    // it holds above its release threshold within this call, not at some
+    // later caller's synchronisation.
+    struct SyncAtExit {
+        cudaStream_t s;
+        ~SyncAtExit() { cudaStreamSynchronize(s); }
+    } sync_at_exit{s};
     cudaMemPool_t pool = ctx->pool;
     DevBuf u;
     u.alloc_pool((size_t)D * 8, pool, s);
