@@ -430,7 +430,16 @@ def measure_rest(ctx, q, st, args, timer, sm_mhz, head_ms):
                             "applies": inf["applies"], "residual": inf["residual"],
                             "status": q.STATUS.get(inf["status"], inf["status"])}
         solve["product_ms_fp64_k1"] = variants["fp64_k1"]["ms"]
+        solve["fp64"]["over_products"] = solve_over_products(solve["fp64"], solve["product_ms_fp64_k1"])
     return variants, solve
+
+
+def solve_over_products(entry, product_ms):
+    """Warm solve time over the time of its products (applies x the timed
+    FP64 single-vector product): the eigensolver's overhead around H_S x."""
+    if not product_ms or not entry.get("applies"):
+        return None
+    return entry["warm_seconds"] * 1e3 / (entry["applies"] * product_ms)
 
 
 def workload_summary(st):

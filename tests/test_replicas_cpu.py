@@ -1,6 +1,7 @@
 """The multi-GPU path is replicas only: each rank runs the whole workload and
 the bench reports the units of all ranks over the slowest rank's time.  The
-aggregation is checked with two gloo ranks on the CPU."""
+aggregation is checked with two gloo ranks on the CPU, and so is the bench's
+other host-side arithmetic."""
 import os
 import socket
 
@@ -45,3 +46,10 @@ def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.whole_job_rate(10.0, 2.0, 1) == 5.0
+
+
+def test_solve_over_products():
+    import bench
+    assert abs(bench.solve_over_products({"warm_seconds": 6.46e-3, "applies": 41}, 0.0845) - 1.8646) < 1e-3
+    assert bench.solve_over_products({"warm_seconds": 1.0, "applies": 0}, 0.1) is None
+    assert bench.solve_over_products({"warm_seconds": 1.0, "applies": 3}, None) is None
